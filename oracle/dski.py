@@ -1,0 +1,195 @@
+"""D-SKI (Sec. 3.1): K^grad ~ [W; dW] K_UU [W; dW]^T, plus the noise diagonal.
+
+* U is a regular grid with m_k nodes per dimension from lo_k to hi_k (both
+  ends included), flattened in C order (last dimension fastest).
+* K_UU = s_f^2 K_1 (x) ... (x) K_d with K_k[a, b] = exp(-(u_a - u_b)^2 / 2 l_k^2):
+  the SE kernel of App. A is a product over dimensions, so on a tensor grid
+  it is a Kronecker product.
+* W holds tensor-product Keys weights w_i(u) = prod_k omega(t_ik - u_k);
+  dW_p differentiates them in dimension p only (omega'/h_p there).
+* K~ = B K_UU B^T + diag(noise) with B = [W; dW_1; ...; dW_d] (N x m,
+  N = n(d+1)), noise sigma_v^2 on value rows and sigma_g^2 on gradient rows.
+
+Test infrastructure only (see ``oracle/__init__``).
+"""
+from dataclasses import dataclass
+import itertools
+
+import numpy as np
+import scipy.sparse as sp
+
+from .keys import omega, domega
+
+
+@dataclass(frozen=True)
+class Grid:
+    m: tuple
+    lo: tuple
+    hi: tuple
+
+    @property
+    def d(self):
+        return len(self.m)
+
+    @property
+    def h(self):
+        return tuple((b - a) / (mk - 1) for a, b, mk in zip(self.lo, self.hi, self.m))
+
+    @property
+    def size(self):
+        return int(np.prod(self.m))
+
+    def nodes(self, k):
+        return self.lo[k] + np.arange(self.m[k]) * self.h[k]
+
+
+def kfactor(grid, k, ell):
+    """K_k[a, b] = exp(-(u_a - u_b)^2 / (2 l^2)) on dimension k of the grid."""
+    u = grid.nodes(k)
+    diff = u[:, None] - u[None, :]
+    return np.exp(-0.5 * diff**2 / ell**2)
+
+
+def kfactor_dlogell(grid, k, ell):
+    """d K_k / d log l = K_k * (u_a - u_b)^2 / l^2."""
+    u = grid.nodes(k)
+    diff = u[:, None] - u[None, :]
+    return np.exp(-0.5 * diff**2 / ell**2) * diff**2 / ell**2
+
+
+def kuu_dense(grid, lengthscale, outputscale):
+    """Dense K_UU = s_f^2 kron(K_1, ..., K_d) (small grids only)."""
+    out = np.array([[1.0]])
+    for k in range(grid.d):
+        out = np.kron(out, kfactor(grid, k, lengthscale[k]))
+    return outputscale**2 * out
+
+
+def kron_apply(factors, G):
+    """(A_1 (x) ... (x) A_d) G for G of shape (prod m_k, s), one mode at a time."""
+    m = [A.shape[0] for A in factors]
+    s = G.shape[1]
+    T = G.reshape(*m, s)
+    for k, A in enumerate(factors):
+        T = np.moveaxis(np.tensordot(A, T, axes=([1], [k])), 0, k)
+    return T.reshape(-1, s)
+
+
+def kuu_apply(grid, lengthscale, outputscale, G):
+    """K_UU G through the Kronecker factors (no dense K_UU)."""
+    facs = [kfactor(grid, k, lengthscale[k]) for k in range(grid.d)]
+    return outputscale**2 * kron_apply(facs, G)
+
+
+def stencils(X, grid):
+    """Per point and dimension: first node c_k - 1, weights and derivative
+    weights of the four stencil nodes (t = (x - lo)/h, c = floor(t))."""
+    X = np.asarray(X, np.float64)
+    n, d = X.shape
+    first = np.empty((n, d), np.int64)
+    w = np.empty((n, d, 4))
+    dw = np.empty((n, d, 4))
+    for k in range(d):
+        h = grid.h[k]
+        t = (X[:, k] - grid.lo[k]) / h
+        c = np.floor(t).astype(np.int64)
+        if np.any(c < 1) or np.any(c > grid.m[k] - 3):
+            raise ValueError("point outside the interpolation grid")
+        first[:, k] = c - 1
+        s = t[:, None] - (c[:, None] - 1 + np.arange(4)[None, :])
+        w[:, k, :] = omega(s)
+        dw[:, k, :] = domega(s) / h
+    return first, w, dw
+
+
+def interp_matrix(X, grid):
+    """Explicit sparse B = [W; dW_1; ...; dW_d] (N x m CSR)."""
+    first, w, dw = stencils(X, grid)
+    n, d = first.shape
+    strides = [int(np.prod(grid.m[k + 1:])) for k in range(d)]
+    rows, cols, vals = [], [], []
+    pts = np.arange(n)
+    for offs in itertools.product(range(4), repeat=d):
+        col = np.zeros(n, np.int64)
+        for k in range(d):
+            col += (first[:, k] + offs[k]) * strides[k]
+        wv = np.ones(n)
+        for k in range(d):
+            wv = wv * w[:, k, offs[k]]
+        rows.append(pts)
+        cols.append(col)
+        vals.append(wv)
+        for p in range(d):
+            gv = np.ones(n)
+            for k in range(d):
+                gv = gv * (dw[:, k, offs[k]] if k == p else w[:, k, offs[k]])
+            rows.append((p + 1) * n + pts)
+            cols.append(col)
+            vals.append(gv)
+    B = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(n * (d + 1), grid.size))
+    return B.tocsr()
+
+
+def noise_diag(n, d, noise_value, noise_grad):
+    """Diagonal of the noise term: sigma_v^2 on value rows, sigma_g^2 on gradient rows."""
+    return np.concatenate([np.full(n, float(noise_value)), np.full(n * d, float(noise_grad))])
+
+
+class DSKI:
+    """The D-SKI operator K~ = B K_UU B^T + diag(noise) for fixed data X."""
+
+    def __init__(self, X, grid, lengthscale, outputscale, noise_value, noise_grad):
+        self.X = np.asarray(X, np.float64)
+        self.n, self.d = self.X.shape
+        self.N = self.n * (self.d + 1)
+        self.grid = grid
+        self.ell = np.asarray(lengthscale, np.float64)
+        self.sf = float(outputscale)
+        self.B = interp_matrix(self.X, grid)
+        self.noise = noise_diag(self.n, self.d, noise_value, noise_grad)
+
+    def kgrad_mvm(self, V):
+        """K^grad_SKI V = B K_UU B^T V (no noise)."""
+        V = np.asarray(V, np.float64)
+        vec = V.ndim == 1
+        V2 = V.reshape(self.N, -1)
+        G = self.B.T @ V2
+        H = kuu_apply(self.grid, self.ell, self.sf, G)
+        out = self.B @ H
+        return out.ravel() if vec else out
+
+    def mvm(self, V):
+        """K~ V = B K_UU B^T V + noise * V (the D-SKI MVM of Sec. 3.1)."""
+        V = np.asarray(V, np.float64)
+        nz = self.noise if V.ndim == 1 else self.noise[:, None]
+        return self.kgrad_mvm(V) + nz * V
+
+    def dense_kgrad(self):
+        """Dense B K_UU B^T (small grids)."""
+        Bd = self.B.toarray()
+        return Bd @ kuu_dense(self.grid, self.ell, self.sf) @ Bd.T
+
+    def dense(self):
+        return self.dense_kgrad() + np.diag(self.noise)
+
+    def kgrad_diag(self):
+        """diag(B K_UU B^T): each row's stencil block of K_UU (Sec. 3.3)."""
+        B = self.B.tocsr()
+        out = np.empty(self.N)
+        facs = [kfactor(self.grid, k, self.ell[k]) for k in range(self.d)]
+        for i in range(self.N):
+            cols = B.indices[B.indptr[i]:B.indptr[i + 1]]
+            vals = B.data[B.indptr[i]:B.indptr[i + 1]]
+            idx = np.array(np.unravel_index(cols, self.grid.m))      # d x nnz
+            blk = np.ones((len(cols), len(cols)))
+            for k in range(self.d):
+                blk = blk * facs[k][np.ix_(idx[k], idx[k])]
+            out[i] = self.sf**2 * vals @ blk @ vals
+        return out
+
+    def kgrad_row(self, j):
+        """Row j of B K_UU B^T: B (K_UU B[j]^T) (Sec. 3.3)."""
+        bj = self.B.getrow(j).toarray().ravel()
+        h = kuu_apply(self.grid, self.ell, self.sf, bj[:, None])[:, 0]
+        return self.B @ h

@@ -1,0 +1,75 @@
+"""Log marginal likelihood (Eq. 1) and its hyperparameter gradient.
+
+With mu = 0 and N = n(d+1) observations (values and gradients):
+  L(theta) = -1/2 [ y^T alpha + log|K~| + N log(2 pi) ],  alpha = K~^{-1} y,
+  dL/dtheta = 1/2 alpha^T (dK~/dtheta) alpha - 1/2 tr(K~^{-1} dK~/dtheta).
+
+theta = (log l_1, ..., log l_d, log s_f, log sigma_n).  In D-SKI the
+interpolation matrix B does not depend on theta, so
+  dK~/dlog l_k  = B (s_f^2 K_1 (x) .. (x) dK_k/dlog l_k (x) .. (x) K_d) B^T,
+  dK_k/dlog l_k = K_k * (u_a - u_b)^2 / l_k^2,
+  dK~/dlog s_f  = 2 B K_UU B^T,
+  dK~/dlog sigma_n = 2 diag(noise)   (both noise levels scale with sigma_n^2).
+
+Test infrastructure only (see ``oracle/__init__``).
+"""
+import numpy as np
+
+from .dski import DSKI, kfactor, kfactor_dlogell, kron_apply
+from .solve import chol_solve, chol_logdet, pcg
+
+
+def dtheta_mvm(op: DSKI, i, V):
+    """(dK~/dtheta_i) V for theta index i (see the module docstring)."""
+    d = op.d
+    V = np.asarray(V, np.float64)
+    V2 = V.reshape(op.N, -1)
+    if i < d:
+        facs = [kfactor_dlogell(op.grid, k, op.ell[k]) if k == i else kfactor(op.grid, k, op.ell[k])
+                for k in range(d)]
+        out = op.B @ (op.sf**2 * kron_apply(facs, op.B.T @ V2))
+    elif i == d:
+        out = 2.0 * op.kgrad_mvm(V2)
+    else:
+        out = 2.0 * op.noise[:, None] * V2
+    return out.ravel() if V.ndim == 1 else out
+
+
+def mll_dense(op: DSKI, y):
+    """Eq. 1 by the direct (Cholesky) method."""
+    A = op.dense()
+    alpha = chol_solve(A, y)
+    return -0.5 * (y @ alpha + chol_logdet(A) + op.N * np.log(2.0 * np.pi))
+
+
+def mll_grad_dense(op: DSKI, y):
+    """Exact gradient of Eq. 1 with the trace taken through the dense inverse."""
+    A = op.dense()
+    alpha = chol_solve(A, y)
+    Ainv = chol_solve(A, np.eye(op.N))
+    g = []
+    for i in range(op.d + 2):
+        dK = dtheta_mvm(op, i, np.eye(op.N))
+        g.append(0.5 * alpha @ dK @ alpha - 0.5 * np.sum(Ainv * dK.T))
+    return np.array(g)
+
+
+def mll_grad_hutchinson(op: DSKI, y, precond, probes, rtol=1e-12, maxit=20000):
+    """Stochastic gradient with probes z_j = C w_j (E[z z^T] = M):
+    tr(K~^{-1} dK~) ~ mean_j (K~^{-1} z_j)^T dK~ (M^{-1} z_j).
+
+    Returns (data-fit part 1/2 alpha^T dK alpha, trace estimates, gradient).
+    """
+    run = pcg(op.mvm, y, precond.solve, rtol=rtol, maxit=maxit)
+    alpha = run["x"]
+    fit = np.array([0.5 * alpha @ dtheta_mvm(op, i, alpha) for i in range(op.d + 2)])
+    P = probes.shape[1]
+    tr = np.zeros(op.d + 2)
+    for j in range(P):
+        z = precond.sqrt_apply(probes[:, j])
+        u = pcg(op.mvm, z, precond.solve, rtol=rtol, maxit=maxit)["x"]
+        v = precond.solve(z)
+        for i in range(op.d + 2):
+            tr[i] += u @ dtheta_mvm(op, i, v)
+    tr /= P
+    return fit, tr, fit - 0.5 * tr

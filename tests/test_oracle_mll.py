@@ -1,0 +1,59 @@
+"""Pins of the marginal-likelihood oracle (Eq. 1): the value against SciPy's
+multivariate normal density, the exact gradient against central finite
+differences, and the Hutchinson gradient against the exact one with scaled
+basis probes (an exact trace)."""
+import numpy as np
+import scipy.stats as st
+
+from oracle.dski import DSKI, Grid
+from oracle.mll import mll_dense, mll_grad_dense, mll_grad_hutchinson
+from oracle.solve import pivoted_cholesky, QRPreconditioner
+
+
+def _make(theta, X, grid, rho):
+    d = X.shape[1]
+    ell = np.exp(theta[:d])
+    sf = np.exp(theta[d])
+    s2 = np.exp(2 * theta[d + 1])
+    return DSKI(X, grid, ell, sf, s2, rho * s2)
+
+
+def _setup(n=10, d=2, seed=0):
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(0, 1, (n, d))
+    grid = Grid(m=(10,) * d, lo=(-0.3,) * d, hi=(1.3,) * d)
+    theta = np.array([np.log(0.35), np.log(0.3), np.log(1.2), np.log(0.1)])[: d + 2] if d == 2 else \
+        np.array([np.log(0.35), np.log(0.4), np.log(0.3), np.log(1.2), np.log(0.1)])
+    y = rng.normal(size=n * (d + 1))
+    return X, grid, theta, y
+
+
+def test_mll_value_is_gaussian_log_density():
+    X, grid, theta, y = _setup()
+    op = _make(theta, X, grid, 2.0)
+    want = st.multivariate_normal(mean=np.zeros(op.N), cov=op.dense()).logpdf(y)
+    assert abs(mll_dense(op, y) - want) < 1e-9 * abs(want)
+
+
+def test_gradient_matches_central_differences():
+    for d in (2, 3):
+        X, grid, theta, y = _setup(n=8, d=d, seed=d)
+        g = mll_grad_dense(_make(theta, X, grid, 2.0), y)
+        h = 1e-4
+        for i in range(d + 2):
+            e = np.zeros_like(theta)
+            e[i] = h
+            fd = (mll_dense(_make(theta + e, X, grid, 2.0), y)
+                  - mll_dense(_make(theta - e, X, grid, 2.0), y)) / (2 * h)
+            assert abs(g[i] - fd) < 1e-6 * max(1.0, abs(fd)), (d, i, g[i], fd)
+
+
+def test_hutchinson_with_basis_probes_is_exact():
+    X, grid, theta, y = _setup(n=6, seed=4)
+    op = _make(theta, X, grid, 2.0)
+    L, _, _ = pivoted_cholesky(op.kgrad_diag(), op.kgrad_row, 5)
+    Pc = QRPreconditioner(L, op.noise)
+    W = np.sqrt(op.N) * np.eye(op.N)
+    _, _, g = mll_grad_hutchinson(op, y, Pc, W, rtol=1e-14)
+    ge = mll_grad_dense(op, y)
+    assert np.allclose(g, ge, rtol=1e-7, atol=1e-7)

@@ -1,0 +1,68 @@
+"""Pins of the SLQ oracle (Sec. 2): the Lanczos tridiagonal recovered from CG
+coefficients equals explicit Lanczos; with full depth and scaled basis probes
+the estimate is the exact log determinant; Rademacher estimates fall within
+a few standard errors; the probe generator is the SplitMix64 stream."""
+import numpy as np
+
+from oracle.dski import DSKI, Grid
+from oracle.solve import pivoted_cholesky, QRPreconditioner, pcg, chol_logdet
+from oracle.slq import lanczos_T_from_cg, lanczos_full, slq_logdet, quadrature_logdet_term
+from oracle.probes import splitmix64_stream, splitmix64_at, rademacher
+
+
+def _op(n, seed, m=12):
+    X = np.random.default_rng(seed).uniform(0, 1, (n, 2))
+    g = Grid(m=(m, m), lo=(-0.25, -0.25), hi=(1.25, 1.25))
+    return DSKI(X, g, [0.3, 0.35], 1.0, 1e-2, 3e-2)
+
+
+def test_T_from_cg_equals_explicit_lanczos():
+    op = _op(12, 0)
+    A = op.dense()
+    b = np.random.default_rng(1).normal(size=op.N)
+    k = 8
+    run = pcg(op.mvm, b, None, rtol=0.0, maxit=k, record=k)
+    d1, o1 = lanczos_T_from_cg(run["alphas"], run["betas"])
+    d2, o2 = lanczos_full(A, b, k)
+    assert np.allclose(d1, d2, rtol=1e-8)
+    assert np.allclose(o1, np.abs(o2), rtol=1e-8)
+
+
+def test_full_depth_basis_probes_give_exact_logdet():
+    op = _op(4, 2, m=8)               # N = 12
+    A = op.dense()
+    L, _, _ = pivoted_cholesky(op.kgrad_diag(), op.kgrad_row, 3)
+    Pc = QRPreconditioner(L, op.noise)
+    W = np.sqrt(op.N) * np.eye(op.N)   # (1/N) sum w w^T = I
+    est, _, _, _ = slq_logdet(op.mvm, Pc, W, depth=op.N, rtol=1e-14)
+    assert abs(est - chol_logdet(A)) < 1e-8 * abs(chol_logdet(A))
+
+
+def test_rademacher_estimate_within_standard_errors():
+    op = _op(30, 3)
+    A = op.dense()
+    L, _, _ = pivoted_cholesky(op.kgrad_diag(), op.kgrad_row, 10)
+    Pc = QRPreconditioner(L, op.noise)
+    W = rademacher(77, op.N, 24)
+    est, se, _, _ = slq_logdet(op.mvm, Pc, W, depth=30)
+    assert abs(est - chol_logdet(A)) < 4 * se + 1e-6 * abs(chol_logdet(A))
+
+
+def test_quadrature_of_diagonal_matrix():
+    # T diagonal (off = 0): e1^T log(T) e1 = log T[0, 0]
+    assert abs(quadrature_logdet_term(np.array([2.0, 5.0]), np.array([0.0]), 3.0) - 3 * np.log(2)) < 1e-14
+
+
+def test_splitmix_counter_equals_stream_and_rademacher_layout():
+    seed = 0x1234ABCD5678
+    s = splitmix64_stream(seed, 50)
+    assert all(splitmix64_at(seed, k + 1) == s[k] for k in range(50))
+    N, P = 7, 3
+    Z = rademacher(seed, N, P)
+    for j in range(P):
+        for e in range(N):
+            bit = splitmix64_at(seed, j * N + e + 1) >> 63
+            assert Z[e, j] == (1.0 if bit == 0 else -1.0)
+    big = rademacher(5, 4000, 5)
+    assert set(np.unique(big)) == {-1.0, 1.0}
+    assert abs(big.mean()) < 0.03
