@@ -1,0 +1,213 @@
+/*
+ * dski.h -- C ABI of the GB300 D-SKI library.
+ *
+ * D-SKI (Eriksson et al., "Scaling Gaussian Process Regression with
+ * Derivatives", NeurIPS 2018, Sec. 3.1) approximates the kernel matrix of a
+ * Gaussian process observed through values AND gradients at n points in d
+ * dimensions (the n(d+1) x n(d+1) matrix K^grad of Sec. 2) by
+ *
+ *     K~ = [W; dW_1; ...; dW_d] K_UU [W; dW_1; ...; dW_d]^T + diag(noise)
+ *
+ * where W holds cubic-convolution interpolation weights (Keys, a = -1/2) on a
+ * regular grid U, dW_p their derivatives in dimension p, and K_UU is the
+ * squared-exponential (SE) kernel of App. A on the grid, a Kronecker product
+ * of one m_k x m_k factor per dimension.  The library computes MVMs with K~
+ * (Sec. 3.1), builds the truncated pivoted-Cholesky preconditioner of
+ * Sec. 3.3, solves K~ x = b by preconditioned CG (Sec. 2), estimates
+ * log|K~| by stochastic Lanczos quadrature (Sec. 2) and differentiates the
+ * log marginal likelihood of Eq. 1 with respect to the hyperparameters.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - N = n (d + 1).  A length-N vector is in the block order of Sec. 3.1:
+ *   [values (n); d/dx_1 (n); ...; d/dx_d (n)], each block in the caller's
+ *   point order.  s right-hand sides are column-major N x s (column j starts
+ *   at element j*N).
+ * - Pointers named *_dev are device pointers owned by the caller; pointers
+ *   named *_host are host pointers owned by the caller.  The library never
+ *   frees caller memory and keeps no caller pointer after a call returns.
+ * - All device work is issued on the stream given to dski_create.  Calls
+ *   that return host results synchronise that stream before returning.
+ * - A handle is not thread-safe; distinct handles may be used concurrently.
+ * - Every int-returning call returns DSKI_OK (0) or a negative dski_status;
+ *   dski_last_error() then gives a message (thread-local, valid until the
+ *   next failing call on that thread).
+ */
+#ifndef DSKI_H
+#define DSKI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dski_handle_* dski_handle;
+typedef struct pivchol_* pivchol_handle;
+
+typedef enum {
+  DSKI_OK = 0,
+  DSKI_ERR_ARG = -1,            /* bad size, pointer or hyperparameter      */
+  DSKI_ERR_OUT_OF_GRID = -2,    /* a point lacks its full 4^d stencil       */
+  DSKI_ERR_CUDA = -3,           /* a CUDA runtime call failed               */
+  DSKI_ERR_NOT_CONVERGED = -4,  /* maxit reached; outputs hold best iterate */
+  DSKI_ERR_BREAKDOWN = -5,      /* NaN/Inf, p^T A p <= 0, non-PD r x r      */
+  DSKI_ERR_TIMEOUT = -6,        /* a device-side wait exceeded its budget   */
+  DSKI_ERR_ALLOC = -7           /* device allocation failed                 */
+} dski_status;
+
+/* Arithmetic of the MVM.  FP64: every step in double.  MIXED_3XTF32: FP32
+ * scatter/gather, Kronecker mode products on the tensor cores in TF32 with
+ * the three-product split (hi*hi + hi*lo + lo*hi) and FP32 accumulation.
+ * MIXED_TF32: as MIXED_3XTF32 with a single TF32 product.  In the mixed
+ * modes CG scalars, dot products, x and r stay FP64 (see dski_pcg_solve). */
+typedef enum { DSKI_FP64 = 0, DSKI_MIXED_3XTF32 = 1, DSKI_MIXED_TF32 = 2 } dski_precision;
+
+/* Problem statement of Sec. 2 / Sec. 3.1 / App. A.
+ *   n, d          points and dimensions, n >= 1, 1 <= d <= 3.
+ *   grid_m[d]     grid nodes per dimension, 4 <= m_k <= 1027; grid nodes are
+ *                 u_a = lo_k + a (hi_k - lo_k)/(m_k - 1), a = 0..m_k-1 (both
+ *                 end points included); the grid is flattened in C order.
+ *   grid_lo/hi[d] grid extent, lo_k < hi_k.  Every point needs
+ *                 1 <= floor((x_k - lo_k)/h_k) <= m_k - 3 in every dimension
+ *                 so that its four stencil nodes exist (else OUT_OF_GRID).
+ *   lengthscale[d] SE length scales l_k > 0 (ARD form of App. A).
+ *   outputscale   sigma_f > 0; K_UU = sigma_f^2 K_1 (x) ... (x) K_d with
+ *                 K_k[a,b] = exp(-(u_a - u_b)^2 / (2 l_k^2)).
+ *   noise_value   sigma^2 added on value rows (> 0).
+ *   noise_grad    sigma^2 added on gradient rows (> 0).  Sec. 2 uses one
+ *                 noise; the terrain experiment of Sec. 4 fits two.
+ *   prec          arithmetic of the MVM (dski_precision).
+ * The arrays are read during dski_create only. */
+typedef struct {
+  int n, d;
+  const int* grid_m;
+  const double* grid_lo;
+  const double* grid_hi;
+  const double* lengthscale;
+  double outputscale;
+  double noise_value, noise_grad;
+  dski_precision prec;
+} dski_params;
+
+/* Sec. 3.1: build the D-SKI operator for the points X_dev (device, n x d
+ * row-major FP64).  Computes each point's grid cell and cell fractions in
+ * FP64, sorts the points by cell (stable, deterministic), builds the cell
+ * index and the Kronecker factors.  The handle owns all of it and a
+ * workspace; X_dev is not referenced afterwards.  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).
+ * Errors: ARG, OUT_OF_GRID, ALLOC, CUDA.  On error *out is NULL. */
+int dski_create(dski_handle* out, const dski_params* params, const double* X_dev,
+                void* cuda_stream);
+
+/* Replace the hyperparameters (lengthscale[d], outputscale, both noises)
+ * of an existing handle; rebuilds the Kronecker factors.  Preconditioners
+ * built earlier keep the hyperparameters they were built with.
+ * Errors: ARG, CUDA. */
+int dski_set_hypers(dski_handle h, const double* lengthscale, double outputscale,
+                    double noise_value, double noise_grad);
+
+/* Sec. 3.1: out = K~ v for s >= 1 columns.  v_dev and out_dev are device
+ * N x s column-major, FP64 (double) in DSKI_FP64 mode and FP32 (float) in
+ * the mixed modes; they must not overlap.  The product runs as
+ * scatter (B^T v onto the grid) -> d Kronecker mode products -> gather
+ * (B h) plus the noise diagonal.  Asynchronous on the handle's stream.
+ * Errors: ARG, CUDA. */
+int dski_mvm(dski_handle h, const void* v_dev, void* out_dev, int s);
+
+/* Sec. 3.3: truncated pivoted Cholesky of the noise-free D-SKI matrix
+ * K^grad_SKI = B K_UU B^T, computed from its diagonal and pivot rows only:
+ * greedy pivot = largest residual diagonal (lowest block-order index on
+ * ties); stops at `rank` steps or when the residual trace drops below
+ * 1e-14 times the initial trace.  Then forms the preconditioner
+ * M = D + L L^T (D = noise diagonal) in the QR-stable form of Sec. 3.3,
+ * M^-1 b = D^-1/2 (y - Q1 (Q1^T y)), y = D^-1/2 b, with Q1 from two
+ * CholeskyQR passes in FP64 (stored FP32 in the mixed modes with an FP64
+ * r x r correction that keeps M^-1 symmetric positive definite).
+ * 1 <= rank <= 128.  *rank_achieved (host) receives the steps taken.
+ * The pivchol handle holds device memory until pivchol_destroy and is tied
+ * to the hyperparameters current at build time.
+ * Errors: ARG, BREAKDOWN, ALLOC, CUDA. */
+int pivchol_build(dski_handle h, int rank, pivchol_handle* out, int* rank_achieved);
+
+/* Sec. 2 / Sec. 3.3: solve K~ x = b for s columns by preconditioned CG.
+ *   pc       preconditioner from pivchol_build, or NULL for plain CG.
+ *   b_dev    device N x s FP64 right-hand sides (block order).
+ *   x_dev    device N x s FP64; on entry the initial guess, on exit the
+ *            solution.
+ *   rtol     stop when ||b - K~ x||_2 <= rtol ||b||_2 per column, the
+ *            residual recomputed in FP64.
+ *   maxit    iteration cap (MVMs of the inner loop).
+ *   iters_host[s], relres_host[s]  iterations and final true relative
+ *            residual per column (FP64 residual, even in the mixed modes).
+ * FP64 mode runs PCG entirely in double.  In the mixed modes the MVM runs
+ * in FP32 / (3x)TF32 while x, r, the dot products and the CG recurrences
+ * are FP64, and the residual is periodically replaced by the FP64 residual
+ * b - K~ x (reliable updates), so the FP64 tolerance is reachable.
+ * Errors: ARG, NOT_CONVERGED (outputs filled), BREAKDOWN, CUDA. */
+int dski_pcg_solve(dski_handle h, pivchol_handle pc, const double* b_dev, double* x_dev,
+                   int s, double rtol, int maxit, int* iters_host, double* relres_host);
+
+/* Sec. 2: stochastic Lanczos quadrature estimate of log|K~|.
+ * Probe j (0-based) is z_j = D^1/2 (w1_j + L' w2_j), where w = [w1; w2] is a
+ * Rademacher vector of length N + r and L' the preconditioner's low-rank
+ * factor scaled by D^-1/2, so E[z z^T] = M.  Entry e of w (block-order row
+ * for e < N, then the r extra rows) is +1 if the top bit of
+ * SplitMix64(seed)[j (N + r) + e + 1] is 0 and -1 otherwise (the k-th
+ * output of SplitMix64 is mix64(seed + k 0x9E3779B97F4A7C15)).  All probes
+ * run in one batched PCG; the first `depth` CG coefficients of each give the
+ * Lanczos tridiagonal T_j, and
+ *   log|K~| ~ log|M| + mean_j (z_j^T M^-1 z_j) e1^T log(T_j) e1.
+ * pc is required; 2 <= probes <= 256, 1 <= depth <= 128.
+ * logdet_host and stderr_host (standard error over probes) are host
+ * scalars.  Errors: ARG, BREAKDOWN, CUDA. */
+int dski_logdet_slq(dski_handle h, pivchol_handle pc, int probes, int depth, uint64_t seed,
+                    double* logdet_host, double* stderr_host);
+
+/* Eq. 1: log marginal likelihood L = -1/2 [y^T a + log|K~| + N log 2 pi],
+ * a = K~^-1 y, and its gradient with respect to
+ * theta = (log l_1, ..., log l_d, log sigma_f, log sigma_n) (both noises
+ * scale with sigma_n^2):
+ *   dL/dtheta_i = 1/2 a^T (dK~/dtheta_i) a - 1/2 tr(K~^-1 dK~/dtheta_i),
+ * the trace estimated with the probes of dski_logdet_slq
+ * (mean_j (K~^-1 z_j)^T dK~ (M^-1 z_j)).  The solve uses rtol 1e-8 (FP64
+ * residual).  y_dev: device length-N FP64.  mll_host: host scalar;
+ * grad_host: host array of d + 2.  Errors: ARG, NOT_CONVERGED, BREAKDOWN,
+ * CUDA. */
+int dski_mll_grad(dski_handle h, pivchol_handle pc, const double* y_dev, int probes,
+                  uint64_t seed, double* mll_host, double* grad_host);
+
+/* Profiling aid (the paper has no counterpart): per-stage device timers.
+ * Stages, in order: 0 permute (user block order <-> internal layout),
+ * 1 scatter, 2 Kronecker mode products, 3 gather (+ noise), 4 preconditioner
+ * apply, 5 CG vector work (dots, updates, residual refinement),
+ * 6 pivoted Cholesky build, 7 Lanczos / quadrature.
+ *   mode 1: reset and start recording.  Every stage launch issued on the
+ *           handle's stream is bracketed by a pair of CUDA events.
+ *   mode 0: stop; synchronise the stream; write, per stage, the summed
+ *           device milliseconds to ms_host[DSKI_NSTAGES] and the number of
+ *           kernels launched to launches_host[DSKI_NSTAGES] (either may be
+ *           NULL).  At most 2^18 event pairs are kept; launches beyond that
+ *           are counted but not timed (*truncated_host, may be NULL, = 1).
+ * Errors: ARG, CUDA. */
+#define DSKI_NSTAGES 8
+int dski_profile(dski_handle h, int mode, double* ms_host, long long* launches_host,
+                 int* truncated_host);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * handles).  A host-side counter, incremented at every launch site. */
+long long dski_launch_count(void);
+
+/* Release a handle / preconditioner (NULL is ignored).  Synchronises the
+ * handle's stream first. */
+void dski_destroy(dski_handle h);
+void pivchol_destroy(pivchol_handle pc);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* dski_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DSKI_H */

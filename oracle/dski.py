@@ -165,6 +165,21 @@ class DSKI:
         nz = self.noise if V.ndim == 1 else self.noise[:, None]
         return self.kgrad_mvm(V) + nz * V
 
+    def abs_mvm(self, V):
+        """|B| K_UU |B|^T |V| + noise * |V|: the same product with every term
+        replaced by its absolute value (K_UU >= 0 elementwise for the SE
+        kernel).  The standard rounding-error bound of a product evaluated
+        term by term in precision u is |fl(K~ v) - K~ v| <= gamma |B| K_UU
+        |B|^T |v| (Higham, Accuracy and Stability of Numerical Algorithms,
+        2nd ed., Sec. 3.5); this supplies the right-hand side."""
+        V = np.abs(np.asarray(V, np.float64))
+        vec = V.ndim == 1
+        V2 = V.reshape(self.N, -1)
+        Ba = abs(self.B)
+        out = Ba @ kuu_apply(self.grid, self.ell, self.sf, Ba.T @ V2)
+        out = out + self.noise[:, None] * V2
+        return out.ravel() if vec else out
+
     def dense_kgrad(self):
         """Dense B K_UU B^T (small grids)."""
         Bd = self.B.toarray()

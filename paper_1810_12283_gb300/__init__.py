@@ -1,0 +1,183 @@
+"""GB300 D-SKI: the derivative structured-kernel-interpolation MVM of
+Eriksson et al., "Scaling Gaussian Process Regression with Derivatives"
+(NeurIPS 2018, Sec. 3.1), with the pivoted-Cholesky-preconditioned CG,
+stochastic-Lanczos log determinant and marginal-likelihood gradient it drives
+(Sec. 2, Sec. 3.3, Eq. 1).
+
+This module is the thin Python binding of the C ABI declared in
+``include/dski.h``: it marshals torch CUDA tensors (device memory, streams)
+into the library's calls and nothing else.  Every step of the computation
+runs in the CUDA library ``libdski.so``; importing fails loudly when the
+library has not been built.
+"""
+import ctypes as C
+
+import torch
+
+from . import _lib
+from ._lib import DskiError, PREC
+
+__all__ = ["DSKI", "Preconditioner", "DskiError", "PREC", "mll_function", "launch_count"]
+
+
+def _stream_ptr(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+class Preconditioner:
+    """Truncated pivoted Cholesky preconditioner M = D + L L^T (Sec. 3.3)."""
+
+    def __init__(self, handle, ptr, rank):
+        self._owner = handle
+        self.ptr = ptr
+        self.rank = rank
+
+    def close(self):
+        if self.ptr:
+            _lib.load().pivchol_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class DSKI:
+    """D-SKI operator K~ = [W; dW] K_UU [W; dW]^T + diag(noise) on a regular grid.
+
+    X: (n, d) float64 CUDA tensor of points.  Vectors are length N = n(d+1)
+    in block order [values; d/dx_1; ...; d/dx_d] (columns of an (N, s)
+    tensor stored column-major, i.e. pass ``V.T.contiguous().T`` or an
+    (s, N) tensor's transpose -- the helpers below take (N,) or (s, N)).
+    """
+
+    def __init__(self, X, grid_m, grid_lo, grid_hi, lengthscale, outputscale=1.0,
+                 noise_value=1e-4, noise_grad=None, prec="fp64", stream=None):
+        lib = _lib.load()
+        if not (isinstance(X, torch.Tensor) and X.is_cuda):
+            raise TypeError("X must be a CUDA tensor")
+        X = X.to(torch.float64).contiguous()
+        n, d = X.shape
+        self.n, self.d, self.N = n, d, n * (d + 1)
+        self.prec = prec
+        self.dtype = torch.float64 if prec == "fp64" else torch.float32
+        self.device = X.device
+        self.stream = stream
+        ng = noise_value if noise_grad is None else noise_grad
+        self._m = (C.c_int * d)(*[int(v) for v in grid_m])
+        self._lo = (C.c_double * d)(*[float(v) for v in grid_lo])
+        self._hi = (C.c_double * d)(*[float(v) for v in grid_hi])
+        ell = list(lengthscale) if hasattr(lengthscale, "__len__") else [lengthscale] * d
+        self._ell = (C.c_double * d)(*[float(v) for v in ell])
+        p = _lib.DskiParams(n, d, self._m, self._lo, self._hi, self._ell, float(outputscale),
+                            float(noise_value), float(ng), PREC[prec])
+        h = C.c_void_p()
+        _lib.check(lib.dski_create(C.byref(h), C.byref(p), _dptr(X), _stream_ptr(stream)))
+        self.h = h
+
+    # -- helpers -------------------------------------------------------------
+    def _cols(self, v, dtype):
+        """(N,) or (s, N) -> contiguous (s, N) tensor of dtype on our device."""
+        if v.dim() == 1:
+            v = v[None, :]
+        if v.shape[-1] != self.N:
+            raise ValueError(f"expected trailing size N={self.N}, got {tuple(v.shape)}")
+        return v.to(device=self.device, dtype=dtype).contiguous()
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.load().dski_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- calls -----------------------------------------------------------------
+    def set_hypers(self, lengthscale, outputscale, noise_value, noise_grad=None):
+        ng = noise_value if noise_grad is None else noise_grad
+        ell = list(lengthscale) if hasattr(lengthscale, "__len__") else [lengthscale] * self.d
+        arr = (C.c_double * self.d)(*[float(v) for v in ell])
+        _lib.check(_lib.load().dski_set_hypers(self.h, arr, float(outputscale),
+                                               float(noise_value), float(ng)))
+
+    def mvm(self, v, out=None):
+        """K~ v for v of shape (N,) or (s, N) (each row one column of the C-ABI's N x s)."""
+        squeeze = v.dim() == 1
+        V = self._cols(v, self.dtype)
+        s = V.shape[0]
+        if out is None:
+            res = torch.empty_like(V)
+            _lib.check(_lib.load().dski_mvm(self.h, _dptr(V), _dptr(res), s))
+            return res[0] if squeeze else res
+        if (out.dtype != self.dtype or not out.is_contiguous() or out.numel() != V.numel()
+                or out.device != V.device):
+            raise ValueError("out must be a contiguous tensor of the operator's dtype and size")
+        _lib.check(_lib.load().dski_mvm(self.h, _dptr(V), _dptr(out), s))
+        return out
+
+    def pivchol(self, rank):
+        pc = C.c_void_p()
+        got = C.c_int()
+        _lib.check(_lib.load().pivchol_build(self.h, int(rank), C.byref(pc), C.byref(got)))
+        return Preconditioner(self, pc, got.value)
+
+    def solve(self, b, pc=None, rtol=1e-8, maxit=10000, x0=None, allow_not_converged=False):
+        """Solve K~ x = b.  Returns (x, iters list, relres list)."""
+        squeeze = b.dim() == 1
+        B = self._cols(b, torch.float64)
+        s = B.shape[0]
+        X = torch.zeros_like(B) if x0 is None else self._cols(x0, torch.float64).clone()
+        it = (C.c_int * s)()
+        rr = (C.c_double * s)()
+        allow = (-4,) if allow_not_converged else ()
+        _lib.check(_lib.load().dski_pcg_solve(self.h, pc.ptr if pc is not None else None,
+                                              _dptr(B), _dptr(X), s, float(rtol), int(maxit),
+                                              it, rr), allow)
+        return (X[0] if squeeze else X), list(it), list(rr)
+
+    def profile_start(self):
+        """Start the per-stage device timers (dski_profile mode 1)."""
+        _lib.check(_lib.load().dski_profile(self.h, 1, None, None, None))
+
+    def profile_stop(self):
+        """Stop the timers; returns {stage: (ms, launches)} and a truncated flag."""
+        ms = (C.c_double * _lib.NSTAGES)()
+        la = (C.c_longlong * _lib.NSTAGES)()
+        tr = C.c_int()
+        _lib.check(_lib.load().dski_profile(self.h, 0, ms, la, C.byref(tr)))
+        return {name: (ms[k], la[k]) for k, name in enumerate(_lib.STAGES)}, bool(tr.value)
+
+    def logdet(self, pc, probes=16, depth=30, seed=777):
+        ld = C.c_double()
+        se = C.c_double()
+        _lib.check(_lib.load().dski_logdet_slq(self.h, pc.ptr, int(probes), int(depth),
+                                               C.c_uint64(seed), C.byref(ld), C.byref(se)))
+        return ld.value, se.value
+
+    def mll_grad(self, y, pc, probes=16, seed=777):
+        Y = self._cols(y, torch.float64)
+        mll = C.c_double()
+        g = (C.c_double * (self.d + 2))()
+        _lib.check(_lib.load().dski_mll_grad(self.h, pc.ptr, _dptr(Y), int(probes),
+                                             C.c_uint64(seed), C.byref(mll), g))
+        return mll.value, list(g)
+
+
+def launch_count():
+    """Kernels the CUDA library has launched in this process."""
+    return int(_lib.load().dski_launch_count())
+
+
+def mll_function(*args, **kwargs):
+    from .autograd import mll_function as f
+    return f(*args, **kwargs)

@@ -1,0 +1,129 @@
+// Internal declarations of the D-SKI library (not part of the C ABI).
+//
+// Internal data layout (all device memory owned by the handle):
+//   * points are kept sorted by grid cell (stable, by original index within a
+//     cell); sorted position j <-> original point perm[j];
+//   * an internal vector row is e = j (d + 1) + c, c = 0 for the value and
+//     c = 1..d for d/dx_c ("point-interleaved"), s columns column-major
+//     (column q at q N).  Dot products are permutation invariant, so the
+//     solvers run entirely in this layout; only the C-ABI boundary permutes;
+//   * a grid vector is the C-order grid (last dimension fastest), s columns
+//     column-major (column q at q M).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/dski.h"
+
+#define DSKI_MAXD 3
+
+namespace dski {
+
+// ---------------------------------------------------------------- errors ---
+int set_error(int code, const char* fmt, ...);
+void clear_error();
+
+#define DSKI_TRY(expr)                      \
+  do {                                      \
+    int rc__ = (expr);                      \
+    if (rc__ != DSKI_OK) return rc__;       \
+  } while (0)
+
+#define DSKI_CUDA(call)                                                        \
+  do {                                                                         \
+    cudaError_t e__ = (call);                                                  \
+    if (e__ != cudaSuccess)                                                    \
+      return ::dski::set_error(DSKI_ERR_CUDA, "%s failed: %s (%s:%d)", #call,  \
+                               cudaGetErrorString(e__), __FILE__, __LINE__);   \
+  } while (0)
+
+#define DSKI_LAUNCHED() DSKI_CUDA(cudaGetLastError())
+
+// ------------------------------------------------------- stage profiling ---
+// Per-stage CUDA-event timers (off unless dski_profile switched them on) and
+// a process-wide count of the kernels this library launched.
+enum Stage { ST_PERMUTE = 0, ST_SCATTER, ST_KRON, ST_GATHER, ST_PRECOND, ST_PCGVEC,
+             ST_PIVCHOL, ST_LANCZOS, ST_COUNT };
+static_assert(ST_COUNT == DSKI_NSTAGES, "stage table out of sync with dski.h");
+
+struct Profiler;   // defined in capi.cu
+void count_launches(int k);   // adds to the process-wide launch counter
+void stage_begin(dski_handle h, int stage, cudaStream_t st);
+void stage_end(dski_handle h, int stage, cudaStream_t st, int launches);
+
+// Brackets the launches of one stage: stage_begin on construction,
+// stage_end (which also counts `launches` kernels) on destruction.
+struct StageScope {
+  dski_handle h;
+  int stage;
+  cudaStream_t st;
+  int launches;
+  StageScope(dski_handle h_, int stage_, cudaStream_t st_, int launches_ = 1)
+      : h(h_), stage(stage_), st(st_), launches(launches_) {
+    stage_begin(h, stage, st);
+  }
+  ~StageScope() { stage_end(h, stage, st, launches); }
+};
+
+// --------------------------------------------------------- device buffer ---
+// A grow-only device allocation owned by a handle.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  int ensure(size_t need);   // grows (never shrinks); DSKI_OK or ALLOC
+  void release();
+  template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+}  // namespace dski
+
+struct dski_handle_ {
+  int n = 0, d = 0, N = 0;
+  int m[DSKI_MAXD] = {1, 1, 1};     // grid nodes per dimension
+  int mc[DSKI_MAXD] = {1, 1, 1};    // cells per dimension (m_k - 3)
+  double lo[DSKI_MAXD] = {0, 0, 0}, hi[DSKI_MAXD] = {0, 0, 0}, h[DSKI_MAXD] = {1, 1, 1};
+  double ell[DSKI_MAXD] = {1, 1, 1};
+  double sf = 1.0, nv = 0.0, ng = 0.0;
+  int prec = DSKI_FP64;
+  cudaStream_t stream = nullptr;
+  int M = 0;        // grid size prod m_k
+  int ncell = 0;    // prod mc_k
+  int sm_count = 0;
+
+  // geometry (sorted order)
+  dski::DevBuf perm, inv_perm, cell, cell_start, frac64, frac32;
+  // Kronecker factors K_k (m_k x m_k, row-major, symmetric): FP64, FP32 and
+  // the TF32 hi/lo split of the FP64 value (hi = rna_tf32(K), lo = rna_tf32(K - hi)).
+  dski::DevBuf K64[DSKI_MAXD], K32[DSKI_MAXD], Khi[DSKI_MAXD], Klo[DSKI_MAXD];
+  // workspace
+  dski::DevBuf gridA, gridB, vin, vout, scratch;
+  // solver workspace: reduction partials, last-block tickets (zeroed at
+  // allocation), per-column scalar state and solver vectors
+  dski::DevBuf s_part, s_ticket, s_state, s_vec[10];
+  // stage timers (NULL unless profiling is on)
+  dski::Profiler* prof = nullptr;
+};
+
+namespace dski {
+
+// Geometry / factors (geom.cu)
+int build_geometry(dski_handle h, const double* X_dev);
+int build_factors(dski_handle h);
+
+// MVM pieces (mvm.cu).  `prec64` selects the FP64 operator (double vectors)
+// or the FP32 operator (float vectors, (3x)TF32 mode products per h->prec).
+int mvm_internal(dski_handle h, const void* vin, void* vout, int s, bool prec64);
+int permute_in(dski_handle h, const void* v_user, void* v_int, int s, bool f64, cudaStream_t st);
+int permute_out(dski_handle h, const void* v_int, void* v_user, int s, bool f64, cudaStream_t st);
+// grid-only pieces used by the adjoint: g = B^T v, and the Kronecker product
+// with one factor optionally replaced by dK_k/dlog l_k (which = k) or none (which = -1).
+int scatter_internal(dski_handle h, const void* vin, void* g, int s, bool prec64);
+int kron_internal(dski_handle h, void* g, void* tmp, int s, bool prec64, int dfactor,
+                  const void* dK, void** result);
+
+// internal vector length
+inline size_t nrows(dski_handle h) { return (size_t)h->N; }
+
+}  // namespace dski

@@ -1,0 +1,200 @@
+// Tall-skinny FP64 linear algebra on the internal layout, used by the
+// preconditioner build and apply of Sec. 3.3 and by the solvers:
+//   ts_tn   C = A^T (w .* B)         (N x p)^T (N x q) -> p x q, split over rows
+//   ts_nn   Y = alpha X + A C        (N x p)(p x q)    -> N x q, row-parallel
+//   col_dots, noise_diag, precond_apply.
+// All reductions are deterministic (fixed-order partial sums).
+#include "solve_internal.cuh"
+
+namespace dski {
+
+double* wbuf(DevBuf& b, size_t count) {
+  if (b.ensure(count * sizeof(double)) != DSKI_OK) {
+    set_error(DSKI_ERR_ALLOC, "solver workspace allocation failed (%zu doubles)", count);
+    return nullptr;
+  }
+  return b.as<double>();
+}
+
+namespace {
+
+constexpr int TN_TP = 32;     // output tile rows (columns of A)
+constexpr int TN_TQ = 8;      // output tile cols (columns of B)
+constexpr int TN_SUB = 64;    // rows staged per sub-chunk
+constexpr int TN_CHUNK = 2048;
+
+// partial[chunk][tp][tq] of A^T (w .* B) over one chunk of rows.
+__global__ void __launch_bounds__(256) k_ts_tn(const double* __restrict__ A, int p,
+                                               const double* __restrict__ B, int q,
+                                               const double* __restrict__ w, long long N,
+                                               double* __restrict__ part) {
+  __shared__ double As[TN_SUB][TN_TP + 1];
+  __shared__ double Bs[TN_SUB][TN_TQ + 1];
+  const int t0 = blockIdx.y * TN_TP, u0 = blockIdx.z * TN_TQ;
+  const long long r0 = (long long)blockIdx.x * TN_CHUNK;
+  const long long r1 = min(N, r0 + TN_CHUNK);
+  const int ti = threadIdx.x / TN_TQ, ui = threadIdx.x % TN_TQ;   // 32 x 8
+  double acc = 0.0;
+  for (long long rs = r0; rs < r1; rs += TN_SUB) {
+    for (int idx = threadIdx.x; idx < TN_SUB * TN_TP; idx += 256) {
+      const int rr = idx % TN_SUB, tt = idx / TN_SUB;
+      const long long row = rs + rr;
+      As[rr][tt] = (row < r1 && t0 + tt < p) ? A[(long long)(t0 + tt) * N + row] : 0.0;
+    }
+    for (int idx = threadIdx.x; idx < TN_SUB * TN_TQ; idx += 256) {
+      const int rr = idx % TN_SUB, uu = idx / TN_SUB;
+      const long long row = rs + rr;
+      double v = 0.0;
+      if (row < r1 && u0 + uu < q) {
+        v = B[(long long)(u0 + uu) * N + row];
+        if (w) v *= w[row];
+      }
+      Bs[rr][uu] = v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < TN_SUB; ++rr) acc = fma(As[rr][ti], Bs[rr][ui], acc);
+    __syncthreads();
+  }
+  const int t = t0 + ti, u = u0 + ui;
+  if (t < p && u < q) part[((long long)blockIdx.x * p + t) * q + u] = acc;
+}
+
+__global__ void k_sum_chunks(const double* __restrict__ part, int nchunk, int pq,
+                             double* __restrict__ out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= pq) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunk; ++c) s += part[(long long)c * pq + idx];
+  out[idx] = s;
+}
+
+// Y[:, u] = alpha X[:, u] + sum_t A[:, t] C[t, u]   (optionally times rowscale)
+template <int QB>
+__global__ void __launch_bounds__(256) k_ts_nn(const double* __restrict__ X, double alpha,
+                                               const double* __restrict__ A, int p,
+                                               const double* __restrict__ C, int q,
+                                               double* __restrict__ Y,
+                                               const double* __restrict__ rowscale,
+                                               long long N) {
+  extern __shared__ double Cs[];   // p x q
+  for (int i = threadIdx.x; i < p * q; i += blockDim.x) Cs[i] = C[i];
+  __syncthreads();
+  const int u0 = blockIdx.y * QB;
+  for (long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x; row < N;
+       row += (long long)gridDim.x * blockDim.x) {
+    double acc[QB];
+#pragma unroll
+    for (int u = 0; u < QB; ++u)
+      acc[u] = (X && u0 + u < q) ? alpha * X[(long long)(u0 + u) * N + row] : 0.0;
+    for (int t = 0; t < p; ++t) {
+      const double a = A[(long long)t * N + row];
+#pragma unroll
+      for (int u = 0; u < QB; ++u)
+        if (u0 + u < q) acc[u] = fma(a, Cs[t * q + u0 + u], acc[u]);
+    }
+    const double sc = rowscale ? rowscale[row] : 1.0;
+#pragma unroll
+    for (int u = 0; u < QB; ++u)
+      if (u0 + u < q) Y[(long long)(u0 + u) * N + row] = sc * acc[u];
+  }
+}
+
+__global__ void k_col_dots(const double* __restrict__ a, const double* __restrict__ b,
+                           long long N, int s, double* __restrict__ part,
+                           unsigned* __restrict__ ticket, double* __restrict__ out) {
+  __shared__ double sh[32];
+  const int q = blockIdx.y;
+  double v = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    v = fma(a[(long long)q * N + i], b[(long long)q * N + i], v);
+  v = block_sum(v, sh);
+  if (threadIdx.x == 0) part[(long long)q * gridDim.x + blockIdx.x] = v;
+  if (last_block(ticket, gridDim.x * gridDim.y)) {
+    for (int c = threadIdx.x; c < s; c += blockDim.x) {
+      double t = 0.0;
+      for (unsigned bx = 0; bx < gridDim.x; ++bx) t += part[(long long)c * gridDim.x + bx];
+      out[c] = t;
+    }
+  }
+}
+
+__global__ void k_noise_diag(int n, int d, double nv, double ng, double* __restrict__ D) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * (d + 1)) return;
+  D[e] = (e % (d + 1)) == 0 ? nv : ng;
+}
+
+}  // namespace
+
+int ts_tn(dski_handle h, const double* A, int p, const double* B, int q, const double* w,
+          double* C_dev) {
+  const long long N = h->N;
+  const int nchunk = (int)((N + TN_CHUNK - 1) / TN_CHUNK);
+  double* part = wbuf(h->s_part, (size_t)nchunk * p * q);
+  if (!part) return DSKI_ERR_ALLOC;
+  dim3 grd(nchunk, (p + TN_TP - 1) / TN_TP, (q + TN_TQ - 1) / TN_TQ);
+  {
+    StageScope sc(h, ST_PRECOND, h->stream, 2);
+    k_ts_tn<<<grd, 256, 0, h->stream>>>(A, p, B, q, w, N, part);
+    k_sum_chunks<<<(p * q + 255) / 256, 256, 0, h->stream>>>(part, nchunk, p * q, C_dev);
+  }
+  DSKI_LAUNCHED();
+  return DSKI_OK;
+}
+
+int ts_nn(dski_handle h, const double* X, double alpha, const double* A, int p,
+          const double* C, int q, double* Y, const double* rowscale) {
+  const long long N = h->N;
+  const size_t smem = (size_t)p * q * sizeof(double);
+  if (smem > 96 * 1024) return set_error(DSKI_ERR_ARG, "ts_nn: p*q too large (%d x %d)", p, q);
+  const int nbx = (int)std::min<long long>((N + 255) / 256, 4LL * h->sm_count);
+  StageScope sc(h, ST_PRECOND, h->stream);
+  if (q <= 4) {
+    dim3 grd(nbx, (q + 3) / 4);
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_ts_nn<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_ts_nn<4><<<grd, 256, smem, h->stream>>>(X, alpha, A, p, C, q, Y, rowscale, N);
+  } else {
+    dim3 grd(nbx, (q + 7) / 8);
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_ts_nn<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_ts_nn<8><<<grd, 256, smem, h->stream>>>(X, alpha, A, p, C, q, Y, rowscale, N);
+  }
+  DSKI_LAUNCHED();
+  return DSKI_OK;
+}
+
+static unsigned* tickets(dski_handle h, int count) {
+  // Tickets are zeroed once at allocation; every user leaves them at zero.
+  const size_t need = (size_t)count * sizeof(unsigned);
+  if (h->s_ticket.bytes < need || !h->s_ticket.ptr) {
+    h->s_ticket.release();
+    if (h->s_ticket.ensure(std::max<size_t>(need, 4096)) != DSKI_OK) return nullptr;
+    if (cudaMemsetAsync(h->s_ticket.ptr, 0, h->s_ticket.bytes, h->stream) != cudaSuccess)
+      return nullptr;
+  }
+  return h->s_ticket.as<unsigned>();
+}
+
+int col_dots(dski_handle h, const double* a, const double* b, int s, double* out_dev) {
+  const long long N = h->N;
+  const int nbx = (int)std::min<long long>((N + 1023) / 1024, 2LL * h->sm_count);
+  double* part = wbuf(h->s_part, (size_t)nbx * s);
+  unsigned* tk = tickets(h, 1);
+  if (!part || !tk) return set_error(DSKI_ERR_ALLOC, "col_dots: workspace allocation failed");
+  StageScope sc(h, ST_PCGVEC, h->stream);
+  k_col_dots<<<dim3(nbx, s), 256, 0, h->stream>>>(a, b, N, s, part, tk, out_dev);
+  DSKI_LAUNCHED();
+  return DSKI_OK;
+}
+
+int noise_diag(dski_handle h, double nv, double ng, double* D_dev) {
+  StageScope sc(h, ST_PCGVEC, h->stream);
+  k_noise_diag<<<(unsigned)((h->N + 255) / 256), 256, 0, h->stream>>>(h->n, h->d, nv, ng, D_dev);
+  DSKI_LAUNCHED();
+  return DSKI_OK;
+}
+
+}  // namespace dski

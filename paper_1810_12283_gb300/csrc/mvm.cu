@@ -1,0 +1,466 @@
+// The D-SKI MVM of Sec. 3.1:
+//   K~ v = B (K_UU (B^T v)) + noise .* v,   B = [W; dW_1; ...; dW_d],
+// in three stages on the sorted, point-interleaved internal layout:
+//   scatter  g = B^T v   (grid-node-owned pull over the 4^d neighbouring
+//                         cells: deterministic, no atomics)
+//   kron     h = s_f^2 (K_1 (x) ... (x) K_d) g  (d mode products)
+//   gather   out = B h + noise .* v   (point-owned, sum-factorised stencil)
+// The mode products here are the SIMT path (FP64 DFMA, or FP32 FFMA);
+// the tensor-core (3x)TF32 path lives in kron_tc.cu.
+#include <algorithm>
+
+#include "dski_internal.cuh"
+#include "keys.cuh"
+
+namespace dski {
+
+struct MvmGeo {
+  int d;
+  int m[DSKI_MAXD];
+  int mc[DSKI_MAXD];
+  double invh[DSKI_MAXD];
+};
+
+static MvmGeo make_geo(dski_handle h) {
+  MvmGeo g{};
+  g.d = h->d;
+  for (int k = 0; k < DSKI_MAXD; ++k) {
+    g.m[k] = k < h->d ? h->m[k] : 1;
+    g.mc[k] = k < h->d ? h->mc[k] : 1;
+    g.invh[k] = k < h->d ? 1.0 / h->h[k] : 1.0;
+  }
+  return g;
+}
+
+namespace {
+
+// ------------------------------------------------------------- scatter ----
+// Grid node u receives sum_i [w_i(u) v_i^0 + sum_p dw_{i,p}(u) v_i^p] over the
+// points i whose stencil covers u, i.e. whose cell (first stencil node) f
+// satisfies u - 3 <= f <= u per dimension.  The cells of the last dimension
+// are contiguous in sorted order, so each (f_0, .., f_{d-2}) gives one range.
+template <class T, int D, int CB>
+__global__ void __launch_bounds__(256) k_scatter(MvmGeo g, const int* __restrict__ cell_start,
+                                                 const int* __restrict__ cell,
+                                                 const T* __restrict__ frac,
+                                                 const T* __restrict__ v, T* __restrict__ grid,
+                                                 int s, long long N, long long M) {
+  const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= M) return;
+  const int q0 = blockIdx.y * CB;
+  int uc[3];
+  {
+    long long t = u;
+    for (int k = D - 1; k >= 0; --k) {
+      uc[k] = (int)(t % g.m[k]);
+      t /= g.m[k];
+    }
+  }
+  T acc[CB];
+#pragma unroll
+  for (int q = 0; q < CB; ++q) acc[q] = T(0);
+  const T ih0 = (T)g.invh[0];
+  const T ih1 = D > 1 ? (T)g.invh[1] : T(1);
+  const T ih2 = D > 2 ? (T)g.invh[2] : T(1);
+  const int L = D - 1;   // last (fastest) dimension
+  const int lo_l = max(0, uc[L] - 3), hi_l = min(uc[L], g.mc[L] - 1);
+  if (lo_l > hi_l) {
+#pragma unroll
+    for (int q = 0; q < CB; ++q)
+      if (q0 + q < s) grid[(long long)(q0 + q) * M + u] = T(0);
+    return;
+  }
+  const int lo0 = D > 1 ? max(0, uc[0] - 3) : 0, hi0 = D > 1 ? min(uc[0], g.mc[0] - 1) : 0;
+  const int lo1 = D > 2 ? max(0, uc[1] - 3) : 0, hi1 = D > 2 ? min(uc[1], g.mc[1] - 1) : 0;
+  for (int f0 = lo0; f0 <= hi0; ++f0) {
+    for (int f1 = lo1; f1 <= hi1; ++f1) {
+      long long rowbase;
+      if (D == 1) rowbase = 0;
+      else if (D == 2) rowbase = (long long)f0 * g.mc[1];
+      else rowbase = ((long long)f0 * g.mc[1] + f1) * g.mc[2];
+      const int js = cell_start[rowbase + lo_l];
+      const int je = cell_start[rowbase + hi_l + 1];
+      for (int j = js; j < je; ++j) {
+        const int fl = (int)(cell[j] - rowbase);
+        const int ol = uc[L] - fl;
+        T c[D + 1];
+        if (D == 1) {
+          T w0, dw0;
+          keys1<T>(frac[j], ol, w0, dw0);
+          c[0] = w0;
+          c[1] = dw0 * ih0;
+        } else if (D == 2) {
+          T w0, dw0, w1, dw1;
+          keys1<T>(frac[2 * (long long)j], uc[0] - f0, w0, dw0);
+          keys1<T>(frac[2 * (long long)j + 1], ol, w1, dw1);
+          c[0] = w0 * w1;
+          c[1] = dw0 * ih0 * w1;
+          c[D > 1 ? 2 : 0] = w0 * dw1 * ih1;
+        } else {
+          T w0, dw0, w1, dw1, w2, dw2;
+          keys1<T>(frac[3 * (long long)j], uc[0] - f0, w0, dw0);
+          keys1<T>(frac[3 * (long long)j + 1], uc[D > 2 ? 1 : 0] - f1, w1, dw1);
+          keys1<T>(frac[3 * (long long)j + 2], ol, w2, dw2);
+          const T w01 = w0 * w1;
+          c[0] = w01 * w2;
+          c[1] = dw0 * ih0 * w1 * w2;
+          c[D > 1 ? 2 : 0] = w0 * dw1 * ih1 * w2;
+          c[D > 2 ? 3 : 0] = w01 * dw2 * ih2;
+        }
+        const long long e = (long long)j * (D + 1);
+#pragma unroll
+        for (int q = 0; q < CB; ++q) {
+          if (q0 + q < s) {
+            const T* vq = v + (long long)(q0 + q) * N + e;
+            T a = acc[q];
+#pragma unroll
+            for (int cc = 0; cc <= D; ++cc) a += c[cc] * vq[cc];
+            acc[q] = a;
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < CB; ++q)
+    if (q0 + q < s) grid[(long long)(q0 + q) * M + u] = acc[q];
+}
+
+// -------------------------------------------------------------- gather ----
+// out_j^0 = sum_u w_j(u) h(u) + nv v_j^0,  out_j^p = sum_u dw_{j,p}(u) h(u) + ng v_j^p,
+// evaluated dimension by dimension over the 4^d stencil.
+template <class T, int D, int CB>
+__global__ void __launch_bounds__(256) k_gather(MvmGeo g, const int* __restrict__ cell,
+                                                const T* __restrict__ frac,
+                                                const T* __restrict__ grid,
+                                                const T* __restrict__ v, T* __restrict__ out,
+                                                int s, int n, long long N, long long M, T nv,
+                                                T ng) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int q0 = blockIdx.y * CB;
+  int f[3] = {0, 0, 0};
+  {
+    int t = cell[j];
+    for (int k = D - 1; k >= 0; --k) {
+      f[k] = t % g.mc[k];
+      t /= g.mc[k];
+    }
+  }
+  T w[D][4], dw[D][4];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    keys4<T>(frac[(long long)j * D + k], w[k], dw[k]);
+    const T ih = (T)g.invh[k];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) dw[k][o] *= ih;
+  }
+  long long base = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) base = base * g.m[k] + f[k];
+  const long long e = (long long)j * (D + 1);
+#pragma unroll
+  for (int q = 0; q < CB; ++q) {
+    if (q0 + q >= s) break;
+    const T* hq = grid + (long long)(q0 + q) * M + base;
+    T r[D + 1];
+#pragma unroll
+    for (int cc = 0; cc <= D; ++cc) r[cc] = T(0);
+    if (D == 1) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const T x = hq[a];
+        r[0] += w[0][a] * x;
+        r[1] += dw[0][a] * x;
+      }
+    } else if (D == 2) {
+      const int s1 = g.m[D > 1 ? 1 : 0];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        T rw = T(0), rd = T(0);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const T x = hq[(long long)a * s1 + b];
+          rw += w[D > 1 ? 1 : 0][b] * x;
+          rd += dw[D > 1 ? 1 : 0][b] * x;
+        }
+        r[0] += w[0][a] * rw;
+        r[1] += dw[0][a] * rw;
+        r[D > 1 ? 2 : 0] += w[0][a] * rd;
+      }
+    } else {
+      const long long s1 = (long long)g.m[1] * g.m[2];
+      const int s2 = g.m[2];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        T aw = T(0), ad1 = T(0), ad2 = T(0);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          T lw = T(0), ld = T(0);
+#pragma unroll
+          for (int c2 = 0; c2 < 4; ++c2) {
+            const T x = hq[a * s1 + (long long)b * s2 + c2];
+            lw += w[D > 2 ? 2 : 0][c2] * x;
+            ld += dw[D > 2 ? 2 : 0][c2] * x;
+          }
+          aw += w[D > 1 ? 1 : 0][b] * lw;
+          ad1 += dw[D > 1 ? 1 : 0][b] * lw;
+          ad2 += w[D > 1 ? 1 : 0][b] * ld;
+        }
+        r[0] += w[0][a] * aw;
+        r[1] += dw[0][a] * aw;
+        r[D > 1 ? 2 : 0] += w[0][a] * ad1;
+        r[D > 2 ? 3 : 0] += w[0][a] * ad2;
+      }
+    }
+    const T* vq = v + (long long)(q0 + q) * N + e;
+    T* oq = out + (long long)(q0 + q) * N + e;
+    oq[0] = r[0] + nv * vq[0];
+#pragma unroll
+    for (int cc = 1; cc <= D; ++cc) oq[cc] = r[cc] + ng * vq[cc];
+  }
+}
+
+// --------------------------------------------------- SIMT mode product ----
+// Y[q][j][r] = scale * sum_i X[q][r][i] K[j][i]  (K symmetric m x m,
+// X viewed as R x m with the contracted mode contiguous; the output has the
+// contracted mode first: one step of the cyclic mode rotation).
+template <class T, int TM, int TN>
+__global__ void __launch_bounds__(256) k_mode_simt(const T* __restrict__ X,
+                                                   const T* __restrict__ K, T* __restrict__ Y,
+                                                   int m, long long R, T scale) {
+  constexpr int BM = 16 * TM, BN = 16 * TN, BK = 16;
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int j0 = blockIdx.y * BM;
+  const long long r0 = (long long)blockIdx.x * BN;
+  const long long qoff = (long long)blockIdx.z * R * m;
+  const T* Xq = X + qoff;
+  T* Yq = Y + qoff;
+  T acc[TM][TN];
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TN; ++b) acc[a][b] = T(0);
+  for (int i0 = 0; i0 < m; i0 += BK) {
+    for (int idx = threadIdx.x; idx < BM * BK; idx += 256) {
+      const int jj = idx / BK, ii = idx % BK;
+      const int gj = j0 + jj, gi = i0 + ii;
+      As[ii][jj] = (gj < m && gi < m) ? K[(long long)gj * m + gi] : T(0);
+    }
+    for (int idx = threadIdx.x; idx < BN * BK; idx += 256) {
+      const int rr = idx / BK, ii = idx % BK;
+      const long long gr = r0 + rr;
+      const int gi = i0 + ii;
+      Bs[ii][rr] = (gr < R && gi < m) ? Xq[gr * m + gi] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ii = 0; ii < BK; ++ii) {
+      T a[TM], b[TN];
+#pragma unroll
+      for (int x = 0; x < TM; ++x) a[x] = As[ii][ty * TM + x];
+#pragma unroll
+      for (int y = 0; y < TN; ++y) b[y] = Bs[ii][tx * TN + y];
+#pragma unroll
+      for (int x = 0; x < TM; ++x)
+#pragma unroll
+        for (int y = 0; y < TN; ++y) acc[x][y] += a[x] * b[y];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int x = 0; x < TM; ++x) {
+    const int gj = j0 + ty * TM + x;
+    if (gj >= m) continue;
+#pragma unroll
+    for (int y = 0; y < TN; ++y) {
+      const long long gr = r0 + tx * TN + y;
+      if (gr < R) Yq[(long long)gj * R + gr] = scale * acc[x][y];
+    }
+  }
+}
+
+template <class T>
+__global__ void k_perm_in(const int* __restrict__ perm, const T* __restrict__ vu,
+                          T* __restrict__ vi, int n, int d, long long N, int s) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int i = perm[j];
+  for (int q = 0; q < s; ++q)
+    for (int c = 0; c <= d; ++c)
+      vi[q * N + (long long)j * (d + 1) + c] = vu[q * N + (long long)c * n + i];
+}
+
+template <class T>
+__global__ void k_perm_out(const int* __restrict__ perm, const T* __restrict__ vi,
+                           T* __restrict__ vu, int n, int d, long long N, int s) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int i = perm[j];
+  for (int q = 0; q < s; ++q)
+    for (int c = 0; c <= d; ++c)
+      vu[q * N + (long long)c * n + i] = vi[q * N + (long long)j * (d + 1) + c];
+}
+
+template <class T, int D, int CB>
+void launch_scatter(dski_handle h, const MvmGeo& g, const T* frac, const T* v, T* grid, int s,
+                    cudaStream_t st) {
+  dim3 grd((unsigned)((h->M + 255) / 256), (unsigned)((s + CB - 1) / CB));
+  StageScope sc(h, ST_SCATTER, st);
+  k_scatter<T, D, CB><<<grd, 256, 0, st>>>(g, h->cell_start.as<int>(), h->cell.as<int>(), frac,
+                                           v, grid, s, (long long)h->N, (long long)h->M);
+}
+
+template <class T, int D, int CB>
+void launch_gather(dski_handle h, const MvmGeo& g, const T* frac, const T* grid, const T* v,
+                   T* out, int s, cudaStream_t st) {
+  dim3 grd((unsigned)((h->n + 255) / 256), (unsigned)((s + CB - 1) / CB));
+  StageScope sc(h, ST_GATHER, st);
+  k_gather<T, D, CB><<<grd, 256, 0, st>>>(g, h->cell.as<int>(), frac, grid, v, out, s, h->n,
+                                          (long long)h->N, (long long)h->M, (T)h->nv, (T)h->ng);
+}
+
+template <class T, int D>
+void scatter_dispatch(dski_handle h, const MvmGeo& g, const T* frac, const T* v, T* grid, int s,
+                      cudaStream_t st) {
+  if (s == 1) launch_scatter<T, D, 1>(h, g, frac, v, grid, s, st);
+  else if (s <= 4) launch_scatter<T, D, 4>(h, g, frac, v, grid, s, st);
+  else launch_scatter<T, D, 8>(h, g, frac, v, grid, s, st);
+}
+
+template <class T, int D>
+void gather_dispatch(dski_handle h, const MvmGeo& g, const T* frac, const T* grid, const T* v,
+                     T* out, int s, cudaStream_t st) {
+  if (s == 1) launch_gather<T, D, 1>(h, g, frac, grid, v, out, s, st);
+  else if (s <= 4) launch_gather<T, D, 4>(h, g, frac, grid, v, out, s, st);
+  else launch_gather<T, D, 8>(h, g, frac, grid, v, out, s, st);
+}
+
+template <class T>
+void mode_simt(dski_handle h, const T* X, const T* K, T* Y, int m, long long R, int s, T scale,
+               int sms, cudaStream_t st) {
+  StageScope sc(h, ST_KRON, st);
+  auto ctas = [&](int b) { return ((R + b - 1) / b) * (long long)((m + b - 1) / b) * s; };
+  if (ctas(64) >= 2LL * sms) {
+    dim3 grd((unsigned)((R + 63) / 64), (unsigned)((m + 63) / 64), (unsigned)s);
+    k_mode_simt<T, 4, 4><<<grd, 256, 0, st>>>(X, K, Y, m, R, scale);
+  } else if (ctas(32) >= 2LL * sms) {
+    dim3 grd((unsigned)((R + 31) / 32), (unsigned)((m + 31) / 32), (unsigned)s);
+    k_mode_simt<T, 2, 2><<<grd, 256, 0, st>>>(X, K, Y, m, R, scale);
+  } else {
+    dim3 grd((unsigned)((R + 15) / 16), (unsigned)((m + 15) / 16), (unsigned)s);
+    k_mode_simt<T, 1, 1><<<grd, 256, 0, st>>>(X, K, Y, m, R, scale);
+  }
+}
+
+}  // namespace
+
+int scatter_internal(dski_handle h, const void* vin, void* g, int s, bool prec64) {
+  const MvmGeo geo = make_geo(h);
+  cudaStream_t st = h->stream;
+  if (prec64) {
+    const double* fr = h->frac64.as<double>();
+    switch (h->d) {
+      case 1: scatter_dispatch<double, 1>(h, geo, fr, (const double*)vin, (double*)g, s, st); break;
+      case 2: scatter_dispatch<double, 2>(h, geo, fr, (const double*)vin, (double*)g, s, st); break;
+      default: scatter_dispatch<double, 3>(h, geo, fr, (const double*)vin, (double*)g, s, st); break;
+    }
+  } else {
+    const float* fr = h->frac32.as<float>();
+    switch (h->d) {
+      case 1: scatter_dispatch<float, 1>(h, geo, fr, (const float*)vin, (float*)g, s, st); break;
+      case 2: scatter_dispatch<float, 2>(h, geo, fr, (const float*)vin, (float*)g, s, st); break;
+      default: scatter_dispatch<float, 3>(h, geo, fr, (const float*)vin, (float*)g, s, st); break;
+    }
+  }
+  DSKI_LAUNCHED();
+  return DSKI_OK;
+}
+
+// d mode products g -> result (ping-pong between g and tmp).  Factor k is
+// K_k, except k == dfactor which uses dK (same precision as the path).
+int kron_internal(dski_handle h, void* g, void* tmp, int s, bool prec64, int dfactor,
+                  const void* dK, void** result) {
+  cudaStream_t st = h->stream;
+  void* cur = g;
+  void* nxt = tmp;
+  for (int t = 0; t < h->d; ++t) {
+    const int k = h->d - 1 - t;
+    const long long R = h->M / h->m[k];
+    const bool last = t == h->d - 1;
+    const double scale = last ? h->sf * h->sf : 1.0;
+    if (prec64) {
+      const double* K = k == dfactor ? (const double*)dK : h->K64[k].as<double>();
+      mode_simt<double>(h, (const double*)cur, K, (double*)nxt, h->m[k], R, s, scale, h->sm_count,
+                        st);
+    } else {
+      const float* K = k == dfactor ? (const float*)dK : h->K32[k].as<float>();
+      mode_simt<float>(h, (const float*)cur, K, (float*)nxt, h->m[k], R, s, (float)scale,
+                       h->sm_count, st);
+    }
+    DSKI_LAUNCHED();
+    std::swap(cur, nxt);
+  }
+  *result = cur;
+  return DSKI_OK;
+}
+
+int mvm_internal(dski_handle h, const void* vin, void* vout, int s, bool prec64) {
+  const size_t es = prec64 ? 8 : 4;
+  const size_t gbytes = (size_t)h->M * s * es;
+  if (h->gridA.ensure(gbytes) || h->gridB.ensure(gbytes))
+    return set_error(DSKI_ERR_ALLOC, "grid workspace allocation failed (%zu bytes)", gbytes);
+  DSKI_TRY(scatter_internal(h, vin, h->gridA.ptr, s, prec64));
+  void* res = nullptr;
+  DSKI_TRY(kron_internal(h, h->gridA.ptr, h->gridB.ptr, s, prec64, -1, nullptr, &res));
+  const MvmGeo geo = make_geo(h);
+  cudaStream_t st = h->stream;
+  if (prec64) {
+    const double* fr = h->frac64.as<double>();
+    switch (h->d) {
+      case 1: gather_dispatch<double, 1>(h, geo, fr, (const double*)res, (const double*)vin, (double*)vout, s, st); break;
+      case 2: gather_dispatch<double, 2>(h, geo, fr, (const double*)res, (const double*)vin, (double*)vout, s, st); break;
+      default: gather_dispatch<double, 3>(h, geo, fr, (const double*)res, (const double*)vin, (double*)vout, s, st); break;
+    }
+  } else {
+    const float* fr = h->frac32.as<float>();
+    switch (h->d) {
+      case 1: gather_dispatch<float, 1>(h, geo, fr, (const float*)res, (const float*)vin, (float*)vout, s, st); break;
+      case 2: gather_dispatch<float, 2>(h, geo, fr, (const float*)res, (const float*)vin, (float*)vout, s, st); break;
+      default: gather_dispatch<float, 3>(h, geo, fr, (const float*)res, (const float*)vin, (float*)vout, s, st); break;
+    }
+  }
+  DSKI_LAUNCHED();
+  return DSKI_OK;
+}
+
+int permute_in(dski_handle h, const void* v_user, void* v_int, int s, bool f64, cudaStream_t st) {
+  const unsigned nb = (unsigned)((h->n + 255) / 256);
+  StageScope sc(h, ST_PERMUTE, st);
+  if (f64)
+    k_perm_in<double><<<nb, 256, 0, st>>>(h->perm.as<int>(), (const double*)v_user,
+                                          (double*)v_int, h->n, h->d, h->N, s);
+  else
+    k_perm_in<float><<<nb, 256, 0, st>>>(h->perm.as<int>(), (const float*)v_user, (float*)v_int,
+                                         h->n, h->d, h->N, s);
+  DSKI_LAUNCHED();
+  return DSKI_OK;
+}
+
+int permute_out(dski_handle h, const void* v_int, void* v_user, int s, bool f64,
+                cudaStream_t st) {
+  const unsigned nb = (unsigned)((h->n + 255) / 256);
+  StageScope sc(h, ST_PERMUTE, st);
+  if (f64)
+    k_perm_out<double><<<nb, 256, 0, st>>>(h->perm.as<int>(), (const double*)v_int,
+                                           (double*)v_user, h->n, h->d, h->N, s);
+  else
+    k_perm_out<float><<<nb, 256, 0, st>>>(h->perm.as<int>(), (const float*)v_int,
+                                          (float*)v_user, h->n, h->d, h->N, s);
+  DSKI_LAUNCHED();
+  return DSKI_OK;
+}
+
+}  // namespace dski

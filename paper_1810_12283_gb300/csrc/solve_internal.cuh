@@ -1,0 +1,93 @@
+// Internal declarations of the solvers (Sec. 2, Sec. 3.3, Eq. 1).
+//
+// All solver vectors live in the handle's internal layout (points sorted by
+// grid cell, rows point-interleaved: row e = j (d + 1) + c) as FP64 N x s
+// column-major arrays.  Dot products and norms are permutation invariant, so
+// only the C-ABI boundary permutes.
+//
+// Reductions are deterministic: each block writes a partial sum, and the
+// last block to finish (an atomic ticket after a memory fence) adds the
+// partials in block order.
+#pragma once
+
+#include <vector>
+
+#include "dski_internal.cuh"
+
+// Preconditioner of Sec. 3.3 in the handle's internal layout:
+//   M = D + L L^T,  Lt = D^-1/2 L,  [Lt; I] = [Q1; Q2] R  (CholeskyQR2, FP64),
+//   M^-1 b = D^-1/2 (y - Q1 Q1^T y),  y = D^-1/2 b.
+struct pivchol_ {
+  dski_handle h = nullptr;
+  int N = 0;
+  int rank = 0;           // columns of L / Q1 actually built
+  double nv = 0, ng = 0;  // noise diagonal at build time
+  double logdetM = 0;     // log|M| = sum log D + 2 sum log diag(R)
+  dski::DevBuf L;         // N x rank FP64, col-major
+  dski::DevBuf Q1;        // N x rank FP64, col-major
+  std::vector<int> piv;   // internal row of pivot k
+};
+
+namespace dski {
+
+constexpr int RED_THREADS = 256;
+
+// ---- device reduction helpers (header-only, used by several .cu files) ----
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block; the result is valid in thread 0.  `sh` holds >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    t = lane < nw ? sh[lane] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;
+}
+
+// True in every thread of the last block (of nblocks) to reach this point.
+// Must be called by all threads of every block, after the block's partial
+// results are written.  The last block resets the ticket for the next use.
+__device__ __forceinline__ bool last_block(unsigned* ticket, unsigned nblocks) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned t = atomicAdd(ticket, 1u);
+    is_last = (t == nblocks - 1);
+    if (is_last) *ticket = 0u;
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last;
+}
+
+// ---- host-side building blocks (pcg.cu) ----
+// Column dots: out[q] = sum_i a[q N + i] b[q N + i] for q < s (FP64, deterministic).
+int col_dots(dski_handle h, const double* a, const double* b, int s, double* out_dev);
+// Tall-skinny products over N rows, col-major operands:
+//   C (p x q) = A^T B   (A: N x p, B: N x q), optional row scaling w (B rows times w)
+int ts_tn(dski_handle h, const double* A, int p, const double* B, int q, const double* w,
+          double* C_dev);
+//   Y (N x q) = alpha X + A C   (A: N x p, C: p x q, row-major p x q), optional row scale
+int ts_nn(dski_handle h, const double* X, double alpha, const double* A, int p,
+          const double* C, int q, double* Y, const double* rowscale);
+// Noise diagonal of the internal layout: D[e] = nv (value rows) or ng.
+int noise_diag(dski_handle h, double nv, double ng, double* D_dev);
+// M^-1 for s columns: Z = D^-1/2 (Y - Q1 Q1^T Y), Y = D^-1/2 R.
+int precond_apply(dski_handle h, pivchol_handle pc, const double* R, double* Z, int s);
+
+// Ensure `count` doubles in b; returns the pointer or NULL (error set).
+double* wbuf(DevBuf& b, size_t count);
+
+}  // namespace dski

@@ -91,3 +91,16 @@ def test_converges_to_exact_dse_under_refinement():
     assert rate_v > 2.6, (rate_v, errs_v)
     assert rate_g > 1.7, (rate_g, errs_g)
     assert errs_v[-1] < 1e-5
+
+
+def test_abs_mvm_bounds_the_product():
+    """abs_mvm is |B| K_UU |B|^T |v| + noise |v| (dense brute force) and
+    dominates |K~ v| entrywise."""
+    g = Grid(m=(9, 11), lo=(-0.3, -0.3), hi=(1.3, 1.3))
+    X = _pts(30, 2, 8)
+    op = DSKI(X, g, [0.3, 0.4], 1.2, 1e-3, 2e-3)
+    v = np.random.default_rng(9).normal(size=op.N)
+    Ba = np.abs(op.B.toarray())
+    want = Ba @ kuu_dense(g, op.ell, op.sf) @ Ba.T @ np.abs(v) + op.noise * np.abs(v)
+    assert np.allclose(op.abs_mvm(v), want, rtol=1e-13, atol=0)
+    assert np.all(op.abs_mvm(v) >= np.abs(op.mvm(v)) * (1 - 1e-13))
