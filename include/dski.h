@@ -130,6 +130,17 @@ int dski_mvm(dski_handle h, const void* v_dev, void* out_dev, int s);
  * Errors: ARG, BREAKDOWN, ALLOC, CUDA. */
 int pivchol_build(dski_handle h, int rank, pivchol_handle* out, int* rank_achieved);
 
+/* Sec. 3.3: copy the preconditioner's factor out.  L_dev (device, may be
+ * NULL) receives L as N x rank_achieved column-major FP64 in the caller's
+ * block order; pivots_host (host, may be NULL) receives the pivot rows in
+ * the order chosen, as caller block-order row indices.  Synchronises.
+ * Errors: ARG, CUDA. */
+int pivchol_export(pivchol_handle pc, double* L_dev, int* pivots_host);
+
+/* Sec. 3.3: log|M| = sum log D + log|I + L^T D^-1 L| (Sylvester's identity,
+ * from the CholeskyQR factor R); NaN for a NULL handle. */
+double pivchol_logdet(pivchol_handle pc);
+
 /* Sec. 2 / Sec. 3.3: solve K~ x = b for s columns by preconditioned CG.
  *   pc       preconditioner from pivchol_build, or NULL for plain CG.
  *   b_dev    device N x s FP64 right-hand sides (block order).

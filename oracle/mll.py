@@ -73,3 +73,21 @@ def mll_grad_hutchinson(op: DSKI, y, precond, probes, rtol=1e-12, maxit=20000):
             tr[i] += u @ dtheta_mvm(op, i, v)
     tr /= P
     return fit, tr, fit - 0.5 * tr
+
+
+def mll_grad_hutchinson_z(op: DSKI, y, precond, Z, rtol=1e-12, maxit=20000):
+    """As mll_grad_hutchinson with the probe vectors z_j (E[z z^T] = M)
+    given directly: tr(K~^{-1} dK~) ~ mean_j (K~^{-1} z_j)^T dK~ (M^{-1} z_j)."""
+    run = pcg(op.mvm, y, precond.solve, rtol=rtol, maxit=maxit)
+    alpha = run["x"]
+    fit = np.array([0.5 * alpha @ dtheta_mvm(op, i, alpha) for i in range(op.d + 2)])
+    P = Z.shape[1]
+    tr = np.zeros(op.d + 2)
+    for j in range(P):
+        z = Z[:, j]
+        u = pcg(op.mvm, z, precond.solve, rtol=rtol, maxit=maxit)["x"]
+        v = precond.solve(z)
+        for i in range(op.d + 2):
+            tr[i] += u @ dtheta_mvm(op, i, v)
+    tr /= P
+    return fit, tr, fit - 0.5 * tr

@@ -10,7 +10,9 @@ GAMMA = 0x9E3779B97F4A7C15 and mix64 the "variant 13" finaliser
   z *= 0x94D049BB133111EB; z ^= z >> 31          (all mod 2^64).
 Probe j, row e (row index in the user's block order [values; d/dx_1; ...])
 takes counter k = j * N + e + 1 and value +1 if the top bit of the output is
-0, else -1.
+0, else -1.  Preconditioned probes (``preconditioned_probes``) draw w of
+length N + r this way and map it through C = [D^{1/2}, L], so that
+E[z z^T] = C C^T = M.
 
 Test infrastructure only (see ``oracle/__init__``).
 """
@@ -57,3 +59,10 @@ def rademacher(seed, N, P):
         z = np.uint64(seed & MASK) + k * np.uint64(GAMMA)
         bits = _mix64_vec(z) >> np.uint64(63)
     return np.where(bits == 0, 1.0, -1.0).T.copy()
+
+
+def preconditioned_probes(seed, precond, P):
+    """N x P probes z_j = D^{1/2} w1 + L w2, w = rademacher(seed, N + r, P)
+    (``precond`` an oracle.solve.QRPreconditioner)."""
+    N, r = precond.L.shape
+    return precond.factor_apply(rademacher(seed, N + r, P))

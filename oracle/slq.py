@@ -83,3 +83,27 @@ def slq_logdet(mvm, precond, probes, depth, rtol=1e-12, maxit=10000):
     est = precond.logdet() + terms.mean()
     se = terms.std(ddof=1) / np.sqrt(P) if P > 1 else float("nan")
     return est, se, terms, runs
+
+
+def slq_logdet_z(mvm, precond, Z, depth, rtol=1e-12, maxit=10000):
+    """Preconditioned SLQ from probe vectors z_j (columns of Z) with
+    E[z z^T] = M.  For such z, E[z^T M^{-1/2} log(A_hat) M^{-1/2} z] =
+    tr log(A_hat), A_hat = M^{-1/2} K~ M^{-1/2}; PCG on K~ x = z is the
+    Lanczos process on A_hat from M^{-1/2} z, whose squared norm is
+    z^T M^{-1} z, so the quadrature term of probe j is
+    (z_j^T M^{-1} z_j) e1^T log(T_j) e1.  Returns (estimate, standard error,
+    per-probe terms, per-probe PCG results)."""
+    from .solve import pcg
+    P = Z.shape[1]
+    terms, runs = [], []
+    for j in range(P):
+        z = Z[:, j]
+        run = pcg(mvm, z, precond.solve, rtol=rtol, maxit=maxit, record=depth)
+        k = min(depth, run["iters"])
+        dg, of = lanczos_T_from_cg(run["alphas"][:k], run["betas"][:k])
+        terms.append(quadrature_logdet_term(dg, of, z @ precond.solve(z)))
+        runs.append(run)
+    terms = np.array(terms)
+    est = precond.logdet() + terms.mean()
+    se = terms.std(ddof=1) / np.sqrt(P) if P > 1 else float("nan")
+    return est, se, terms, runs

@@ -86,6 +86,15 @@ class QRPreconditioner:
         r = self.Lt.shape[1]
         return np.sum(np.log(self.D)) + np.linalg.slogdet(np.eye(r) + self.Lt.T @ self.Lt)[1]
 
+    def factor_apply(self, w):
+        """C w with the rectangular factor C = [D^{1/2}, L] (N x (N + r)), so
+        that C C^T = D + L L^T = M: w stacks an N-vector w1 over an r-vector
+        w2 and C w = D^{1/2} w1 + L w2."""
+        w = np.asarray(w, np.float64)
+        N, r = self.L.shape
+        sq = np.sqrt(self.D) if w.ndim == 1 else np.sqrt(self.D)[:, None]
+        return sq * w[:N] + self.L @ w[N:]
+
     def sqrt_apply(self, w):
         """C w with C C^T = M, C = D^{1/2} (I + Lt Lt^T)^{1/2} (principal square
         root via the thin SVD Lt = U S V^T: I + U (sqrt(1 + S^2) - 1) U^T)."""

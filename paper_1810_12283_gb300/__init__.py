@@ -37,6 +37,19 @@ class Preconditioner:
         self.ptr = ptr
         self.rank = rank
 
+    def logdet(self):
+        """log|M| (Sylvester's identity through the CholeskyQR factor)."""
+        return float(_lib.load().pivchol_logdet(self.ptr))
+
+    def export(self):
+        """(L, pivots): L as an (rank, N) float64 CUDA tensor (row k = column k
+        of the factor, caller block order) and the pivot rows chosen."""
+        op = self._owner
+        L = torch.empty(max(self.rank, 1), op.N, dtype=torch.float64, device=op.device)
+        piv = (C.c_int * max(self.rank, 1))()
+        _lib.check(_lib.load().pivchol_export(self.ptr, _dptr(L), piv))
+        return L[:self.rank], list(piv)[:self.rank]
+
     def close(self):
         if self.ptr:
             _lib.load().pivchol_destroy(self.ptr)

@@ -18,7 +18,8 @@ PREC = {"fp64": 0, "mixed_3xtf32": 1, "mixed_tf32": 2}
 # every extern "C" symbol include/dski.h declares
 EXPORTS = ["dski_create", "dski_set_hypers", "dski_mvm", "pivchol_build", "dski_pcg_solve",
            "dski_logdet_slq", "dski_mll_grad", "dski_destroy", "pivchol_destroy",
-           "dski_last_error", "dski_profile", "dski_launch_count"]
+           "dski_last_error", "dski_profile", "dski_launch_count", "pivchol_export",
+           "pivchol_logdet"]
 NSTAGES = 8
 STAGES = ["permute", "scatter", "kron", "gather", "precond", "pcg_vec", "pivchol", "lanczos"]
 
@@ -68,9 +69,12 @@ def load(path=LIB_PATH):
     lib.dski_profile.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_longlong), ip]
     lib.dski_launch_count.argtypes = []
     lib.dski_launch_count.restype = C.c_longlong
+    lib.pivchol_export.argtypes = [vp, vp, ip]
+    lib.pivchol_logdet.argtypes = [vp]
+    lib.pivchol_logdet.restype = C.c_double
     for name in EXPORTS:
         if name not in ("dski_destroy", "pivchol_destroy", "dski_last_error",
-                        "dski_launch_count"):
+                        "dski_launch_count", "pivchol_logdet"):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib

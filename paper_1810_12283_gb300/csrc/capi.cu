@@ -138,6 +138,7 @@ static void release_all(dski_handle h) {
     h->K32[k].release();
     h->Khi[k].release();
     h->Klo[k].release();
+    h->dK64[k].release();
   }
   h->gridA.release();
   h->gridB.release();
@@ -145,6 +146,7 @@ static void release_all(dski_handle h) {
   h->vout.release();
   h->scratch.release();
   h->s_part.release();
+  h->s_tnpart.release();
   h->s_ticket.release();
   h->s_state.release();
   for (auto& b : h->s_vec) b.release();

@@ -97,11 +97,13 @@ struct dski_handle_ {
   // Kronecker factors K_k (m_k x m_k, row-major, symmetric): FP64, FP32 and
   // the TF32 hi/lo split of the FP64 value (hi = rna_tf32(K), lo = rna_tf32(K - hi)).
   dski::DevBuf K64[DSKI_MAXD], K32[DSKI_MAXD], Khi[DSKI_MAXD], Klo[DSKI_MAXD];
+  // dK_k / dlog l_k = K_k .* ((a - b) h_k)^2 / l_k^2 (FP64), for the gradient of Eq. 1
+  dski::DevBuf dK64[DSKI_MAXD];
   // workspace
   dski::DevBuf gridA, gridB, vin, vout, scratch;
   // solver workspace: reduction partials, last-block tickets (zeroed at
   // allocation), per-column scalar state and solver vectors
-  dski::DevBuf s_part, s_ticket, s_state, s_vec[10];
+  dski::DevBuf s_part, s_tnpart, s_ticket, s_state, s_vec[10];
   // stage timers (NULL unless profiling is on)
   dski::Profiler* prof = nullptr;
 };

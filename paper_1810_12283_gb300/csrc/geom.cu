@@ -194,13 +194,15 @@ __device__ __forceinline__ float rna_tf32(float x) {
 
 __global__ void k_factor(int m, double h, double ell, double* __restrict__ K64,
                          float* __restrict__ K32, float* __restrict__ Khi,
-                         float* __restrict__ Klo) {
+                         float* __restrict__ Klo, double* __restrict__ dK64) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= m * m) return;
   const int a = idx / m, b = idx % m;
   const double r = (double)(a - b) * h;
-  const double v = exp(-0.5 * r * r / (ell * ell));
+  const double q = r * r / (ell * ell);
+  const double v = exp(-0.5 * q);
   K64[idx] = v;
+  dK64[idx] = v * q;
   K32[idx] = (float)v;
   const float hi = rna_tf32((float)v);
   Khi[idx] = hi;
@@ -297,11 +299,11 @@ int build_factors(dski_handle h) {
     const int m = h->m[k];
     const size_t mm = (size_t)m * m;
     if (h->K64[k].ensure(mm * 8) || h->K32[k].ensure(mm * 4) || h->Khi[k].ensure(mm * 4) ||
-        h->Klo[k].ensure(mm * 4))
+        h->Klo[k].ensure(mm * 4) || h->dK64[k].ensure(mm * 8))
       return set_error(DSKI_ERR_ALLOC, "device allocation failed for Kronecker factors");
     k_factor<<<(unsigned)((mm + 255) / 256), 256, 0, h->stream>>>(
         m, h->h[k], h->ell[k], h->K64[k].as<double>(), h->K32[k].as<float>(),
-        h->Khi[k].as<float>(), h->Klo[k].as<float>());
+        h->Khi[k].as<float>(), h->Klo[k].as<float>(), h->dK64[k].as<double>());
     count_launches(1);
     DSKI_LAUNCHED();
   }

@@ -1,7 +1,7 @@
 // Tall-skinny FP64 linear algebra on the internal layout, used by the
 // preconditioner build and apply of Sec. 3.3 and by the solvers:
 //   ts_tn   C = A^T (w .* B)         (N x p)^T (N x q) -> p x q, split over rows
-//   ts_nn   Y = alpha X + A C        (N x p)(p x q)    -> N x q, row-parallel
+//   ts_nn   Y = r .* (alpha x .* X + beta A C)  (N x p)(p x q) -> N x q, row-parallel
 //   col_dots, noise_diag, precond_apply.
 // All reductions are deterministic (fixed-order partial sums).
 #include "solve_internal.cuh"
@@ -69,24 +69,26 @@ __global__ void k_sum_chunks(const double* __restrict__ part, int nchunk, int pq
   out[idx] = s;
 }
 
-// Y[:, u] = alpha X[:, u] + sum_t A[:, t] C[t, u]   (optionally times rowscale)
+// Y[:, u] = rowscale .* (alpha xscale .* X[:, u] + beta sum_t A[:, t] C[t, u])
 template <int QB>
 __global__ void __launch_bounds__(256) k_ts_nn(const double* __restrict__ X, double alpha,
+                                               const double* __restrict__ xscale, double beta,
                                                const double* __restrict__ A, int p,
                                                const double* __restrict__ C, int q,
                                                double* __restrict__ Y,
                                                const double* __restrict__ rowscale,
                                                long long N) {
   extern __shared__ double Cs[];   // p x q
-  for (int i = threadIdx.x; i < p * q; i += blockDim.x) Cs[i] = C[i];
+  for (int i = threadIdx.x; i < p * q; i += blockDim.x) Cs[i] = beta * C[i];
   __syncthreads();
   const int u0 = blockIdx.y * QB;
   for (long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x; row < N;
        row += (long long)gridDim.x * blockDim.x) {
     double acc[QB];
+    const double xs = xscale ? alpha * xscale[row] : alpha;
 #pragma unroll
     for (int u = 0; u < QB; ++u)
-      acc[u] = (X && u0 + u < q) ? alpha * X[(long long)(u0 + u) * N + row] : 0.0;
+      acc[u] = (X && u0 + u < q) ? xs * X[(long long)(u0 + u) * N + row] : 0.0;
     for (int t = 0; t < p; ++t) {
       const double a = A[(long long)t * N + row];
 #pragma unroll
@@ -132,7 +134,7 @@ int ts_tn(dski_handle h, const double* A, int p, const double* B, int q, const d
           double* C_dev) {
   const long long N = h->N;
   const int nchunk = (int)((N + TN_CHUNK - 1) / TN_CHUNK);
-  double* part = wbuf(h->s_part, (size_t)nchunk * p * q);
+  double* part = wbuf(h->s_tnpart, (size_t)nchunk * p * q);   // own buffer: callers hold s_part
   if (!part) return DSKI_ERR_ALLOC;
   dim3 grd(nchunk, (p + TN_TP - 1) / TN_TP, (q + TN_TQ - 1) / TN_TQ);
   {
@@ -144,8 +146,8 @@ int ts_tn(dski_handle h, const double* A, int p, const double* B, int q, const d
   return DSKI_OK;
 }
 
-int ts_nn(dski_handle h, const double* X, double alpha, const double* A, int p,
-          const double* C, int q, double* Y, const double* rowscale) {
+int ts_nn(dski_handle h, const double* X, double alpha, const double* xscale, double beta,
+          const double* A, int p, const double* C, int q, double* Y, const double* rowscale) {
   const long long N = h->N;
   const size_t smem = (size_t)p * q * sizeof(double);
   if (smem > 96 * 1024) return set_error(DSKI_ERR_ARG, "ts_nn: p*q too large (%d x %d)", p, q);
@@ -155,18 +157,18 @@ int ts_nn(dski_handle h, const double* X, double alpha, const double* A, int p,
     dim3 grd(nbx, (q + 3) / 4);
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(k_ts_nn<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_ts_nn<4><<<grd, 256, smem, h->stream>>>(X, alpha, A, p, C, q, Y, rowscale, N);
+    k_ts_nn<4><<<grd, 256, smem, h->stream>>>(X, alpha, xscale, beta, A, p, C, q, Y, rowscale, N);
   } else {
     dim3 grd(nbx, (q + 7) / 8);
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(k_ts_nn<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_ts_nn<8><<<grd, 256, smem, h->stream>>>(X, alpha, A, p, C, q, Y, rowscale, N);
+    k_ts_nn<8><<<grd, 256, smem, h->stream>>>(X, alpha, xscale, beta, A, p, C, q, Y, rowscale, N);
   }
   DSKI_LAUNCHED();
   return DSKI_OK;
 }
 
-static unsigned* tickets(dski_handle h, int count) {
+unsigned* tickets(dski_handle h, int count) {
   // Tickets are zeroed once at allocation; every user leaves them at zero.
   const size_t need = (size_t)count * sizeof(unsigned);
   if (h->s_ticket.bytes < need || !h->s_ticket.ptr) {
@@ -178,8 +180,9 @@ static unsigned* tickets(dski_handle h, int count) {
   return h->s_ticket.as<unsigned>();
 }
 
-int col_dots(dski_handle h, const double* a, const double* b, int s, double* out_dev) {
-  const long long N = h->N;
+int col_dots(dski_handle h, const double* a, const double* b, int s, double* out_dev,
+             long long len) {
+  const long long N = len > 0 ? len : h->N;
   const int nbx = (int)std::min<long long>((N + 1023) / 1024, 2LL * h->sm_count);
   double* part = wbuf(h->s_part, (size_t)nbx * s);
   unsigned* tk = tickets(h, 1);
@@ -188,6 +191,20 @@ int col_dots(dski_handle h, const double* a, const double* b, int s, double* out
   k_col_dots<<<dim3(nbx, s), 256, 0, h->stream>>>(a, b, N, s, part, tk, out_dev);
   DSKI_LAUNCHED();
   return DSKI_OK;
+}
+
+int precond_apply(dski_handle h, pivchol_handle pc, const double* R, double* Z, int s) {
+  if (pc->rank == 0) {
+    // M = D: Z = D^-1 R
+    return ts_nn(h, R, 1.0, pc->dis.as<double>(), 0.0, nullptr, 0, nullptr, s, Z,
+                 pc->dis.as<double>());
+  }
+  double* C = wbuf(h->s_vec[5], (size_t)pc->rank * s);
+  if (!C) return DSKI_ERR_ALLOC;
+  DSKI_TRY(ts_tn(h, pc->Q1.as<double>(), pc->rank, R, s, pc->dis.as<double>(), C));
+  // Z = D^-1/2 (D^-1/2 R - Q1 C)
+  return ts_nn(h, R, 1.0, pc->dis.as<double>(), -1.0, pc->Q1.as<double>(), pc->rank, C, s, Z,
+               pc->dis.as<double>());
 }
 
 int noise_diag(dski_handle h, double nv, double ng, double* D_dev) {

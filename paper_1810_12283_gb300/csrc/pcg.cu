@@ -1,0 +1,440 @@
+// Batched preconditioned conjugate gradients (Sec. 2 "conjugate gradients",
+// Sec. 3.3 preconditioning), stochastic Lanczos quadrature for log|K~|
+// (Sec. 2) and the gradient of the log marginal likelihood (Eq. 1).
+//
+// One PCG runs s columns at once on the internal layout.  Per iteration:
+//   q = K~ p                         (D-SKI MVM: scatter, mode products, gather)
+//   alpha = r^T z / p^T q            (fused column dot + scalar update)
+//   x += alpha p,  r -= alpha q      (fused, with ||r||^2)
+//   z = M^-1 r                       (QR-form apply: C = Q1^T D^-1/2 r, then
+//                                     z = D^-1/2 (D^-1/2 r - Q1 C), fused r^T z)
+//   beta = r'^T z' / r^T z,  p = z + beta p
+// Scalars (alpha, beta, r^T z, norms) stay on the device in FP64; the host
+// reads one "columns still active" count per chunk of iterations.  When the
+// recursive residual of every column meets the tolerance, the true residual
+// b - K~ x is recomputed with the FP64 operator and columns that miss the
+// tolerance restart from it.  In the mixed modes the MVM of the inner
+// iteration runs in FP32 / (3x)TF32 on a float copy of p while x, r, z and
+// every scalar stay FP64; the inner solve then targets a reduction of 1e-4
+// of the residual it restarted from, and the FP64 true residual refines x.
+//
+// The first `depth` alpha_j, beta_j of each column are recorded: CG on
+// K~ x = z with preconditioner M is the Lanczos process on
+// M^-1/2 K~ M^-1/2, whose tridiagonal T has
+//   T[j][j]   = 1/alpha_j + beta_{j-1}/alpha_{j-1},
+//   T[j][j+1] = sqrt(beta_j)/alpha_j
+// (Saad, Iterative Methods for Sparse Linear Systems, 2nd ed., Sec. 6.7.3).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "solve_internal.cuh"
+
+namespace dski {
+namespace {
+
+struct ColState {
+  double *bn2, *rn2, *rz, *rz0, *alpha, *beta, *target;
+  int *active, *iters, *bd, *nactive;
+  double *ahist, *bhist;
+  int depth;
+  int s;
+};
+
+constexpr int CG_THREADS = 256;
+
+__device__ __forceinline__ bool cg_last(unsigned* ticket) {
+  return last_block(ticket, gridDim.x * gridDim.y);
+}
+
+// r = b - q, y = dis .* r; ||b||^2 (first call) and ||r||^2; (re)activates
+// the columns whose residual misses the target.
+__global__ void __launch_bounds__(CG_THREADS) k_cg_init(
+    const double* __restrict__ b, const double* __restrict__ q, double* __restrict__ r,
+    double* __restrict__ y, const double* __restrict__ dis, long long N, int first, double tol2,
+    double eta2, ColState cs, double* part, unsigned* ticket) {
+  __shared__ double sh[32];
+  const int c = blockIdx.y;
+  double sb = 0.0, sr = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long o = (long long)c * N + i;
+    const double bi = b[o];
+    const double ri = bi - q[o];
+    r[o] = ri;
+    if (y) y[o] = dis[i] * ri;
+    sb = fma(bi, bi, sb);
+    sr = fma(ri, ri, sr);
+  }
+  sb = block_sum(sb, sh);
+  __syncthreads();
+  sr = block_sum(sr, sh);
+  if (threadIdx.x == 0) {
+    part[2 * ((long long)c * gridDim.x + blockIdx.x)] = sb;
+    part[2 * ((long long)c * gridDim.x + blockIdx.x) + 1] = sr;
+  }
+  if (cg_last(ticket)) {
+    int nact = 0;
+    for (int cc = threadIdx.x; cc < cs.s; cc += blockDim.x) {
+      double tb = 0.0, tr = 0.0;
+      for (unsigned bx = 0; bx < gridDim.x; ++bx) {
+        tb += part[2 * ((long long)cc * gridDim.x + bx)];
+        tr += part[2 * ((long long)cc * gridDim.x + bx) + 1];
+      }
+      if (first) cs.bn2[cc] = tb;
+      cs.rn2[cc] = tr;
+      const double goal = fmax(tol2 * cs.bn2[cc], eta2 * tr);
+      cs.target[cc] = goal;
+      const int act = (!cs.bd[cc] && tr > tol2 * cs.bn2[cc] && isfinite(tr)) ? 1 : 0;
+      cs.active[cc] = act;
+      nact += act;
+    }
+    nact = (int)block_sum((double)nact, sh);
+    if (threadIdx.x == 0) *cs.nactive = nact;
+  }
+}
+
+// z = dis .* (y - Q1 C) (preconditioned) or z = r (plain); r^T z.
+// init: p = z (and its float copy), r^T z becomes rz and rz0.
+// else: beta = (r^T z)_new / rz for active columns, recorded.
+__global__ void __launch_bounds__(CG_THREADS) k_cg_z(
+    const double* __restrict__ r, const double* __restrict__ y, const double* __restrict__ Q1,
+    int rank, const double* __restrict__ C, const double* __restrict__ dis,
+    double* __restrict__ z, double* __restrict__ p, float* __restrict__ p32, long long N,
+    int init, ColState cs, double* part, unsigned* ticket) {
+  extern __shared__ double Cs[];   // rank values of column c
+  __shared__ double sh[32];
+  const int c = blockIdx.y;
+  for (int t = threadIdx.x; t < rank; t += blockDim.x) Cs[t] = C[(long long)t * cs.s + c];
+  __syncthreads();
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long o = (long long)c * N + i;
+    double zi;
+    if (y) {
+      double v = y[o];
+      if (Q1)
+        for (int t = 0; t < rank; ++t) v = fma(-Q1[(long long)t * N + i], Cs[t], v);
+      zi = dis[i] * v;
+    } else {
+      zi = r[o];
+    }
+    acc = fma(r[o], zi, acc);
+    if (init) {
+      p[o] = zi;
+      if (p32) p32[o] = (float)zi;
+    } else {
+      z[o] = zi;
+    }
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[(long long)c * gridDim.x + blockIdx.x] = acc;
+  if (cg_last(ticket)) {
+    for (int cc = threadIdx.x; cc < cs.s; cc += blockDim.x) {
+      double t = 0.0;
+      for (unsigned bx = 0; bx < gridDim.x; ++bx) t += part[(long long)cc * gridDim.x + bx];
+      if (init) {
+        cs.rz[cc] = t;
+        cs.beta[cc] = 0.0;
+        if (cs.rz0[cc] == 0.0) cs.rz0[cc] = t;
+      } else if (cs.active[cc]) {
+        const double be = t / cs.rz[cc];
+        cs.beta[cc] = be;
+        cs.rz[cc] = t;
+        const int k = cs.iters[cc] - 1;
+        if (cs.bhist && k >= 0 && k < cs.depth) cs.bhist[(long long)k * cs.s + cc] = be;
+      } else {
+        cs.beta[cc] = 0.0;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(CG_THREADS) k_cg_p(const double* __restrict__ z,
+                                                     double* __restrict__ p,
+                                                     float* __restrict__ p32, long long N,
+                                                     ColState cs) {
+  const int c = blockIdx.y;
+  if (!cs.active[c]) return;
+  const double be = cs.beta[c];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long o = (long long)c * N + i;
+    const double v = fma(be, p[o], z[o]);
+    p[o] = v;
+    if (p32) p32[o] = (float)v;
+  }
+}
+
+// p^T q and alpha = r^T z / p^T q (zero for finished columns).
+template <class TQ>
+__global__ void __launch_bounds__(CG_THREADS) k_cg_alpha(const double* __restrict__ p,
+                                                         const TQ* __restrict__ q, long long N,
+                                                         ColState cs, double* part,
+                                                         unsigned* ticket) {
+  __shared__ double sh[32];
+  const int c = blockIdx.y;
+  double acc = 0.0;
+  if (cs.active[c])
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+      const long long o = (long long)c * N + i;
+      acc = fma(p[o], (double)q[o], acc);
+    }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[(long long)c * gridDim.x + blockIdx.x] = acc;
+  if (cg_last(ticket)) {
+    for (int cc = threadIdx.x; cc < cs.s; cc += blockDim.x) {
+      double al = 0.0;
+      if (cs.active[cc]) {
+        double t = 0.0;
+        for (unsigned bx = 0; bx < gridDim.x; ++bx) t += part[(long long)cc * gridDim.x + bx];
+        if (!(t > 0.0) || !isfinite(t) || !isfinite(cs.rz[cc])) {
+          cs.bd[cc] = 1;
+          cs.active[cc] = 0;
+        } else {
+          al = cs.rz[cc] / t;
+          const int k = cs.iters[cc];
+          if (cs.ahist && k < cs.depth) cs.ahist[(long long)k * cs.s + cc] = al;
+        }
+      }
+      cs.alpha[cc] = al;
+    }
+  }
+}
+
+// x += alpha p; r -= alpha q; y = dis .* r; ||r||^2; convergence.
+template <class TQ>
+__global__ void __launch_bounds__(CG_THREADS) k_cg_update(
+    double* __restrict__ x, double* __restrict__ r, double* __restrict__ y,
+    const double* __restrict__ p, const TQ* __restrict__ q, const double* __restrict__ dis,
+    long long N, ColState cs, double* part, unsigned* ticket) {
+  __shared__ double sh[32];
+  const int c = blockIdx.y;
+  const double al = cs.alpha[c];
+  double acc = 0.0;
+  if (cs.active[c])
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+      const long long o = (long long)c * N + i;
+      x[o] = fma(al, p[o], x[o]);
+      const double ri = fma(-al, (double)q[o], r[o]);
+      r[o] = ri;
+      if (y) y[o] = dis[i] * ri;
+      acc = fma(ri, ri, acc);
+    }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[(long long)c * gridDim.x + blockIdx.x] = acc;
+  if (cg_last(ticket)) {
+    int nact = 0;
+    for (int cc = threadIdx.x; cc < cs.s; cc += blockDim.x) {
+      if (cs.active[cc]) {
+        double t = 0.0;
+        for (unsigned bx = 0; bx < gridDim.x; ++bx) t += part[(long long)cc * gridDim.x + bx];
+        cs.rn2[cc] = t;
+        cs.iters[cc] += 1;
+        if (!(t > cs.target[cc])) cs.active[cc] = 0;
+      }
+      nact += cs.active[cc];
+    }
+    nact = (int)block_sum((double)nact, sh);
+    if (threadIdx.x == 0) *cs.nactive = nact;
+  }
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- engine --
+
+
+int cg_run(dski_handle h, CgRun& run) {
+  const long long N = h->N;
+  const int s = run.s;
+  const bool mixed = h->prec != DSKI_FP64;
+  const int rank = run.pc ? run.pc->rank : 0;
+  cudaStream_t st = h->stream;
+  const size_t Ns = (size_t)N * s;
+  double* R = wbuf(h->s_vec[0], Ns);
+  double* Z = wbuf(h->s_vec[1], Ns);
+  double* P = wbuf(h->s_vec[2], Ns);
+  double* Q = wbuf(h->s_vec[3], Ns);
+  double* Y = run.pc ? wbuf(h->s_vec[4], Ns) : nullptr;
+  double* C = rank ? wbuf(h->s_vec[5], (size_t)rank * s) : nullptr;
+  float* P32 = mixed ? (float*)wbuf(h->s_vec[6], (Ns + 1) / 2) : nullptr;
+  float* Q32 = mixed ? (float*)wbuf(h->s_vec[7], (Ns + 1) / 2) : nullptr;
+  const int depth = run.depth;
+  const size_t nstate = 8 * (size_t)s + 2 * (size_t)depth * s + 8;
+  double* stbuf = wbuf(h->s_state, nstate + 6 * (size_t)s + 8);
+  const int nbx = (int)std::min<long long>((N + CG_THREADS * 4 - 1) / (CG_THREADS * 4),
+                                           std::max(1, 4 * h->sm_count / std::max(1, s)));
+  double* part = wbuf(h->s_part, (size_t)nbx * s * 2 + 16);
+  unsigned* tk = tickets(h, 1);
+  if (!R || !Z || !P || !Q || (run.pc && !Y) || (rank && !C) || (mixed && (!P32 || !Q32)) ||
+      !stbuf || !part || !tk)
+    return set_error(DSKI_ERR_ALLOC, "dski_pcg_solve: workspace allocation failed");
+  if (run.pc && !Y) return DSKI_ERR_ALLOC;
+  ColState cs{};
+  cs.s = s;
+  cs.depth = depth;
+  cs.bn2 = stbuf;
+  cs.rn2 = cs.bn2 + s;
+  cs.rz = cs.rn2 + s;
+  cs.rz0 = cs.rz + s;
+  cs.alpha = cs.rz0 + s;
+  cs.beta = cs.alpha + s;
+  cs.target = cs.beta + s;
+  cs.ahist = depth ? cs.target + s : nullptr;
+  cs.bhist = depth ? cs.target + s + (size_t)depth * s : nullptr;
+  int* ib = (int*)(cs.target + s + 2 * (size_t)depth * s + 1);
+  cs.active = ib;
+  cs.iters = ib + s;
+  cs.bd = ib + 2 * s;
+  cs.nactive = ib + 3 * s;
+  if (cudaMemsetAsync(stbuf, 0, (nstate + 6 * (size_t)s + 8) * sizeof(double), st) != cudaSuccess)
+    return set_error(DSKI_ERR_CUDA, "dski_pcg_solve: memset failed");
+  const double tol2 = run.rtol * run.rtol;
+  const double eta2 = mixed ? 1e-8 : 0.0;   // inner reduction target (1e-4)^2 in the mixed modes
+  const double* dis = run.pc ? run.pc->dis.as<double>() : nullptr;
+  const dim3 grd(nbx, s);
+  const size_t zsmem = (size_t)std::max(rank, 1) * sizeof(double);
+
+  auto precond_z = [&](int init) -> int {
+    if (rank) DSKI_TRY(ts_tn(h, run.pc->Q1.as<double>(), rank, Y, s, nullptr, C));
+    StageScope sc(h, ST_PRECOND, st);
+    k_cg_z<<<grd, CG_THREADS, zsmem, st>>>(R, Y, rank ? run.pc->Q1.as<double>() : nullptr, rank,
+                                            C, dis, Z, P, P32, N, init, cs, part, tk);
+    DSKI_LAUNCHED();
+    return DSKI_OK;
+  };
+  auto true_residual = [&](int first) -> int {
+    DSKI_TRY(mvm_internal(h, run.X, Q, s, true));
+    StageScope sc(h, ST_PCGVEC, st);
+    k_cg_init<<<grd, CG_THREADS, 0, st>>>(run.B, Q, R, Y, dis, N, first, tol2, eta2, cs, part,
+                                          tk);
+    DSKI_LAUNCHED();
+    return DSKI_OK;
+  };
+  auto read_nactive = [&](int* out) -> int {
+    if (cudaMemcpyAsync(out, cs.nactive, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return set_error(DSKI_ERR_CUDA, "dski_pcg_solve: %s", cudaGetErrorString(cudaGetLastError()));
+    return DSKI_OK;
+  };
+  auto iteration = [&]() -> int {
+    if (mixed) {
+      DSKI_TRY(mvm_internal(h, P32, Q32, s, false));
+      StageScope sc(h, ST_PCGVEC, st, 2);
+      k_cg_alpha<float><<<grd, CG_THREADS, 0, st>>>(P, Q32, N, cs, part, tk);
+      k_cg_update<float><<<grd, CG_THREADS, 0, st>>>(run.X, R, Y, P, Q32, dis, N, cs, part, tk);
+    } else {
+      DSKI_TRY(mvm_internal(h, P, Q, s, true));
+      StageScope sc(h, ST_PCGVEC, st, 2);
+      k_cg_alpha<double><<<grd, CG_THREADS, 0, st>>>(P, Q, N, cs, part, tk);
+      k_cg_update<double><<<grd, CG_THREADS, 0, st>>>(run.X, R, Y, P, Q, dis, N, cs, part, tk);
+    }
+    DSKI_LAUNCHED();
+    DSKI_TRY(precond_z(0));
+    {
+      StageScope sc(h, ST_PCGVEC, st);
+      k_cg_p<<<grd, CG_THREADS, 0, st>>>(Z, P, P32, N, cs);
+    }
+    DSKI_LAUNCHED();
+    return DSKI_OK;
+  };
+
+  int its = 0, restarts = 0, nact = 0;
+  const int max_restarts = mixed ? 200 : 16;
+  DSKI_TRY(true_residual(1));
+  DSKI_TRY(read_nactive(&nact));
+  while (nact > 0) {
+    DSKI_TRY(precond_z(1));
+    while (its < run.maxit) {
+      const int chunk = std::min(16, run.maxit - its);
+      for (int k = 0; k < chunk; ++k) DSKI_TRY(iteration());
+      its += chunk;
+      DSKI_TRY(read_nactive(&nact));
+      if (nact == 0) break;
+    }
+    DSKI_TRY(true_residual(0));
+    DSKI_TRY(read_nactive(&nact));
+    if (nact == 0 || its >= run.maxit || restarts >= max_restarts) break;
+    ++restarts;
+    cs.depth = 0;   // the Lanczos record covers the first pass only
+  }
+  // results
+  std::vector<double> hb(s), hr(s);
+  std::vector<int> hi(s), hbd(s);
+  run.rz0.resize(s);
+  if (cudaMemcpyAsync(hb.data(), cs.bn2, s * 8, cudaMemcpyDeviceToHost, st) ||
+      cudaMemcpyAsync(hr.data(), cs.rn2, s * 8, cudaMemcpyDeviceToHost, st) ||
+      cudaMemcpyAsync(run.rz0.data(), cs.rz0, s * 8, cudaMemcpyDeviceToHost, st) ||
+      cudaMemcpyAsync(hi.data(), cs.iters, s * 4, cudaMemcpyDeviceToHost, st) ||
+      cudaMemcpyAsync(hbd.data(), cs.bd, s * 4, cudaMemcpyDeviceToHost, st))
+    return set_error(DSKI_ERR_CUDA, "dski_pcg_solve: result copy failed");
+  cs.ahist = depth ? cs.target + s : nullptr;
+  cs.bhist = depth ? cs.target + s + (size_t)depth * s : nullptr;
+  if (depth) {
+    run.ahist.resize((size_t)depth * s);
+    run.bhist.resize((size_t)depth * s);
+    if (cudaMemcpyAsync(run.ahist.data(), cs.ahist, (size_t)depth * s * 8, cudaMemcpyDeviceToHost,
+                        st) ||
+        cudaMemcpyAsync(run.bhist.data(), cs.bhist, (size_t)depth * s * 8, cudaMemcpyDeviceToHost,
+                        st))
+      return set_error(DSKI_ERR_CUDA, "dski_pcg_solve: history copy failed");
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess)
+    return set_error(DSKI_ERR_CUDA, "dski_pcg_solve: %s", cudaGetErrorString(cudaGetLastError()));
+  run.iters = hi;
+  run.relres.resize(s);
+  bool conv = true;
+  for (int c = 0; c < s; ++c) {
+    run.relres[c] = hb[c] > 0 ? std::sqrt(hr[c] / hb[c]) : 0.0;
+    if (!(run.relres[c] <= run.rtol)) conv = false;
+    if (hbd[c]) run.breakdown = true;
+  }
+  if (run.breakdown)
+    return set_error(DSKI_ERR_BREAKDOWN, "dski_pcg_solve: p^T K~ p <= 0 or non-finite value");
+  if (!conv)
+    return set_error(DSKI_ERR_NOT_CONVERGED,
+                     "dski_pcg_solve: tolerance %.3g not met after %d iterations", run.rtol, its);
+  return DSKI_OK;
+}
+
+}  // namespace dski
+
+using namespace dski;
+
+extern "C" int dski_pcg_solve(dski_handle h, pivchol_handle pc, const double* b_dev, double* x_dev,
+                              int s, double rtol, int maxit, int* iters_host, double* relres_host) {
+  clear_error();
+  if (!h || !b_dev || !x_dev) return set_error(DSKI_ERR_ARG, "dski_pcg_solve: NULL argument");
+  if (s < 1 || s > 256) return set_error(DSKI_ERR_ARG, "dski_pcg_solve: s must be in 1..256");
+  if (!(rtol > 0.0) || maxit < 1) return set_error(DSKI_ERR_ARG, "dski_pcg_solve: need rtol > 0, maxit >= 1");
+  if (pc && pc->h != h) return set_error(DSKI_ERR_ARG, "dski_pcg_solve: preconditioner of another handle");
+  const size_t Ns = (size_t)h->N * s;
+  double* Bi = wbuf(h->s_vec[8], Ns);
+  double* Xi = wbuf(h->s_vec[9], Ns);
+  if (!Bi || !Xi) return DSKI_ERR_ALLOC;
+  DSKI_TRY(permute_in(h, b_dev, Bi, s, true, h->stream));
+  DSKI_TRY(permute_in(h, x_dev, Xi, s, true, h->stream));
+  CgRun run;
+  run.s = s;
+  run.rtol = rtol;
+  run.maxit = maxit;
+  run.pc = pc;
+  run.B = Bi;
+  run.X = Xi;
+  const int rc = cg_run(h, run);
+  if (rc == DSKI_OK || rc == DSKI_ERR_NOT_CONVERGED || rc == DSKI_ERR_BREAKDOWN) {
+    const int rc2 = permute_out(h, Xi, x_dev, s, true, h->stream);
+    if (rc2 != DSKI_OK) return rc2;
+    for (int c = 0; c < s && !run.iters.empty(); ++c) {
+      if (iters_host) iters_host[c] = run.iters[c];
+      if (relres_host) relres_host[c] = run.relres[c];
+    }
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess)
+      return set_error(DSKI_ERR_CUDA, "dski_pcg_solve: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  return rc;
+}

@@ -25,6 +25,8 @@ struct pivchol_ {
   double logdetM = 0;     // log|M| = sum log D + 2 sum log diag(R)
   dski::DevBuf L;         // N x rank FP64, col-major
   dski::DevBuf Q1;        // N x rank FP64, col-major
+  dski::DevBuf dis;       // D^-1/2 per internal row
+  dski::DevBuf ds;        // D^1/2 per internal row
   std::vector<int> piv;   // internal row of pivot k
 };
 
@@ -73,19 +75,39 @@ __device__ __forceinline__ bool last_block(unsigned* ticket, unsigned nblocks) {
 }
 
 // ---- host-side building blocks (pcg.cu) ----
-// Column dots: out[q] = sum_i a[q N + i] b[q N + i] for q < s (FP64, deterministic).
-int col_dots(dski_handle h, const double* a, const double* b, int s, double* out_dev);
+// Column dots: out[q] = sum_i a[q L + i] b[q L + i] for q < s (FP64,
+// deterministic); L = len, or N when len <= 0.
+int col_dots(dski_handle h, const double* a, const double* b, int s, double* out_dev,
+             long long len = 0);
 // Tall-skinny products over N rows, col-major operands:
 //   C (p x q) = A^T B   (A: N x p, B: N x q), optional row scaling w (B rows times w)
 int ts_tn(dski_handle h, const double* A, int p, const double* B, int q, const double* w,
           double* C_dev);
-//   Y (N x q) = alpha X + A C   (A: N x p, C: p x q, row-major p x q), optional row scale
-int ts_nn(dski_handle h, const double* X, double alpha, const double* A, int p,
-          const double* C, int q, double* Y, const double* rowscale);
+//   Y (N x q) = rowscale .* (alpha xscale .* X + beta A C)
+//   (A: N x p col-major, C: p x q row-major; X, xscale, rowscale may be NULL)
+int ts_nn(dski_handle h, const double* X, double alpha, const double* xscale, double beta,
+          const double* A, int p, const double* C, int q, double* Y, const double* rowscale);
+unsigned* tickets(dski_handle h, int count);   // zeroed last-block tickets
 // Noise diagonal of the internal layout: D[e] = nv (value rows) or ng.
 int noise_diag(dski_handle h, double nv, double ng, double* D_dev);
 // M^-1 for s columns: Z = D^-1/2 (Y - Q1 Q1^T Y), Y = D^-1/2 R.
 int precond_apply(dski_handle h, pivchol_handle pc, const double* R, double* Z, int s);
+
+// One batched PCG run on the internal layout (pcg.cu).
+struct CgRun {
+  int s = 1;
+  double rtol = 1e-8;
+  int maxit = 1000;
+  int depth = 0;
+  pivchol_handle pc = nullptr;
+  const double* B = nullptr;   // internal layout N x s
+  double* X = nullptr;         // internal layout N x s (initial guess in, solution out)
+  // host results
+  std::vector<int> iters;
+  std::vector<double> relres, rz0, ahist, bhist;
+  bool breakdown = false;
+};
+int cg_run(dski_handle h, CgRun& run);
 
 // Ensure `count` doubles in b; returns the pointer or NULL (error set).
 double* wbuf(DevBuf& b, size_t count);

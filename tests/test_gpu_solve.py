@@ -1,0 +1,174 @@
+"""GPU parity of the solvers (Sec. 2, Sec. 3.3, Eq. 1) against the FP64 oracle.
+
+* pivoted Cholesky: the same greedy pivots and, with those pivots, the same
+  factor L (1e-10 relative); log|M| of the QR form (1e-10 relative);
+* PCG: the first iterates equal the oracle's PCG iterates (1e-12), and a full
+  solve meets the true relative residual rtol with
+  ||K~ (x_gpu - x_direct)|| / ||b|| <= 2e-10 against the dense Cholesky
+  solve (the sine workload of 800 points, rank-20 preconditioner, rtol 1e-10;
+  kappa(K~) ~ 3.5e7, so ~1.9e4 iterations), several right-hand sides at
+  once, plain CG (no preconditioner) too;
+* SLQ: with identical probes z = D^1/2 w1 + L w2 the GPU estimate equals the
+  oracle's to 1e-10 relative, and lies within 4 standard errors of the dense
+  log determinant;
+* gradient of Eq. 1: equals the oracle's Hutchinson gradient with identical
+  probes (1e-6, the solves run to rtol 1e-8) and the exact dense gradient
+  within 4 standard errors of the probe mean.
+"""
+import numpy as np
+import pytest
+
+from synth import workloads as W
+from tests._gpu_helpers import gpu_op, oracle_op, need_gpu, rel, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_pc(orc, L):
+    from oracle.solve import QRPreconditioner
+    return QRPreconditioner(L, orc.noise)
+
+
+@pytest.mark.parametrize("make,rank", [(lambda: W.small2d(60, m=14, seed=2), 20),
+                                        (lambda: W.small3d(40, m=9, seed=3), 25),
+                                        (lambda: W.sine2d(), 20)],
+                         ids=["2d", "3d", "sine2d"])
+def test_pivoted_cholesky_parity(make, rank):
+    need_gpu()
+    from oracle.solve import pivoted_cholesky
+    p = make()
+    op = gpu_op(p, "fp64")
+    orc = oracle_op(p)
+    pc = op.pivchol(rank)
+    assert pc.rank == rank
+    Lg, piv = pc.export()
+    Lg = Lg.cpu().numpy().T
+    Lo, piv_o, _ = pivoted_cholesky(orc.kgrad_diag(), orc.kgrad_row, rank)
+    assert piv == piv_o
+    assert rel(Lg, Lo) <= 1e-10
+    assert abs(pc.logdet() - _oracle_pc(orc, Lo).logdet()) <= 1e-10 * abs(pc.logdet())
+    pc.close()
+    op.close()
+
+
+def test_pcg_first_iterates_equal_oracle():
+    need_gpu()
+    from oracle.solve import pcg, pivoted_cholesky
+    p = W.sine2d()
+    op = gpu_op(p, "fp64")
+    orc = oracle_op(p)
+    pc = op.pivchol(p["rank"])
+    _, piv = pc.export()
+    Lo, _, _ = pivoted_cholesky(orc.kgrad_diag(), orc.kgrad_row, p["rank"], pivots=piv)
+    Pc = _oracle_pc(orc, Lo)
+    b = torch.tensor(p["y"], device="cuda")
+    for k in (1, 2, 3, 7):
+        x, it, rr = op.solve(b, pc, rtol=1e-10, maxit=k, allow_not_converged=True)
+        run = pcg(orc.mvm, p["y"], Pc.solve, rtol=0.0, maxit=k)
+        assert it[0] == k
+        assert rel(x.cpu().numpy(), run["x"]) <= 1e-12
+        assert abs(rr[0] - run["relres"]) <= 1e-12
+    pc.close()
+    op.close()
+
+
+def test_pcg_sine_matches_direct_solve():
+    need_gpu()
+    p = W.sine2d()
+    op = gpu_op(p, "fp64")
+    orc = oracle_op(p)
+    A = orc.dense()
+    pc = op.pivchol(p["rank"])
+    rng = np.random.default_rng(3)
+    B = np.stack([p["y"], rng.normal(size=orc.N), rng.normal(size=orc.N)])
+    x, iters, relres = op.solve(torch.tensor(B, device="cuda"), pc, rtol=1e-10, maxit=60000)
+    x = x.cpu().numpy()
+    for q in range(B.shape[0]):
+        assert relres[q] <= 1e-10
+        true = np.linalg.norm(B[q] - A @ x[q]) / np.linalg.norm(B[q])
+        assert true <= 1.5e-10, (q, true)
+        xd = np.linalg.solve(A, B[q])
+        assert np.linalg.norm(A @ (x[q] - xd)) / np.linalg.norm(B[q]) <= 2e-10
+    pc.close()
+    op.close()
+
+
+def test_plain_cg_and_initial_guess():
+    need_gpu()
+    p = W.small2d(80, m=12, seed=5, nv=1e-2, ng=1e-2)
+    op = gpu_op(p, "fp64")
+    orc = oracle_op(p)
+    A = orc.dense()
+    b = np.random.default_rng(1).normal(size=orc.N)
+    x, it, rr = op.solve(torch.tensor(b, device="cuda"), None, rtol=1e-9, maxit=20000)
+    xn = x.cpu().numpy()
+    assert rr[0] <= 1e-9
+    assert np.linalg.norm(b - A @ xn) / np.linalg.norm(b) <= 2e-9
+    # warm start from the solution: converges at once
+    x2, it2, rr2 = op.solve(torch.tensor(b, device="cuda"), None, rtol=1e-9, maxit=100, x0=x)
+    assert it2[0] <= 2 and rr2[0] <= 1e-9
+    op.close()
+
+
+def test_not_converged_reports_best_iterate():
+    need_gpu()
+    from paper_1810_12283_gb300 import DskiError
+    p = W.sine2d()
+    op = gpu_op(p, "fp64")
+    b = torch.tensor(p["y"], device="cuda")
+    with pytest.raises(DskiError) as e:
+        op.solve(b, None, rtol=1e-12, maxit=5)
+    assert e.value.status == "NOT_CONVERGED"
+    x, it, rr = op.solve(b, None, rtol=1e-12, maxit=5, allow_not_converged=True)
+    assert it[0] == 5 and 0 < rr[0] < 1
+    op.close()
+
+
+def test_slq_same_probes_and_dense():
+    need_gpu()
+    from oracle.probes import preconditioned_probes
+    from oracle.slq import slq_logdet_z
+    from oracle.solve import chol_logdet, pivoted_cholesky
+    p = W.small2d(150, m=14, seed=7, nv=1e-2, ng=2e-2)
+    op = gpu_op(p, "fp64")
+    orc = oracle_op(p)
+    pc = op.pivchol(15)
+    Lg, piv = pc.export()
+    Lo, _, _ = pivoted_cholesky(orc.kgrad_diag(), orc.kgrad_row, 15, pivots=piv)
+    Pc = _oracle_pc(orc, Lo)
+    P, depth, seed = 12, 25, 2024
+    ld, se = op.logdet(pc, probes=P, depth=depth, seed=seed)
+    Z = preconditioned_probes(seed, Pc, P)
+    est, se_o, _, _ = slq_logdet_z(orc.mvm, Pc, Z, depth=depth, rtol=1e-15, maxit=depth)
+    assert abs(ld - est) <= 1e-10 * abs(est), (ld, est)
+    assert abs(se - se_o) <= 1e-6 * se_o
+    exact = chol_logdet(orc.dense())
+    assert abs(ld - exact) <= 4 * se + 1e-8 * abs(exact)
+    pc.close()
+    op.close()
+
+
+def test_mll_gradient_same_probes_and_dense():
+    need_gpu()
+    from oracle.mll import mll_grad_dense, mll_grad_hutchinson_z, mll_dense
+    from oracle.probes import preconditioned_probes
+    from oracle.solve import pivoted_cholesky
+    p = W.small2d(60, m=12, seed=11, nv=1e-2, ng=1e-2)
+    op = gpu_op(p, "fp64")
+    orc = oracle_op(p)
+    pc = op.pivchol(20)
+    _, piv = pc.export()
+    Lo, _, _ = pivoted_cholesky(orc.kgrad_diag(), orc.kgrad_row, 20, pivots=piv)
+    Pc = _oracle_pc(orc, Lo)
+    P, seed = 16, 31
+    mll, g = op.mll_grad(torch.tensor(p["y"], device="cuda"), pc, probes=P, seed=seed)
+    Z = preconditioned_probes(seed, Pc, P)
+    _, tr, go = mll_grad_hutchinson_z(orc, p["y"], Pc, Z, rtol=1e-12)
+    assert np.allclose(g, go, rtol=1e-6, atol=1e-6 * np.abs(go).max()), (g, go)
+    ge = mll_grad_dense(orc, p["y"])
+    # the trace estimate's spread over probes bounds the gradient error
+    assert np.all(np.abs(np.array(g) - ge) <= 0.5 * 4 * np.abs(tr).max() / np.sqrt(P) + 1e-6)
+    md = mll_dense(orc, p["y"])
+    assert abs(mll - md) <= 0.05 * abs(md)
+    pc.close()
+    op.close()

@@ -6,7 +6,7 @@ import numpy as np
 import scipy.stats as st
 
 from oracle.dski import DSKI, Grid
-from oracle.mll import mll_dense, mll_grad_dense, mll_grad_hutchinson
+from oracle.mll import mll_dense, mll_grad_dense, mll_grad_hutchinson, mll_grad_hutchinson_z
 from oracle.solve import pivoted_cholesky, QRPreconditioner
 
 
@@ -57,3 +57,14 @@ def test_hutchinson_with_basis_probes_is_exact():
     _, _, g = mll_grad_hutchinson(op, y, Pc, W, rtol=1e-14)
     ge = mll_grad_dense(op, y)
     assert np.allclose(g, ge, rtol=1e-7, atol=1e-7)
+
+
+def test_hutchinson_with_factor_basis_probes_is_exact():
+    X, grid, theta, y = _setup(n=6, seed=5)
+    op = _make(theta, X, grid, 2.0)
+    L, _, _ = pivoted_cholesky(op.kgrad_diag(), op.kgrad_row, 4)
+    Pc = QRPreconditioner(L, op.noise)
+    P = op.N + 4
+    Z = np.sqrt(P) * Pc.factor_apply(np.eye(P))
+    _, _, g = mll_grad_hutchinson_z(op, y, Pc, Z, rtol=1e-14)
+    assert np.allclose(g, mll_grad_dense(op, y), rtol=1e-7, atol=1e-7)

@@ -6,8 +6,9 @@ import numpy as np
 
 from oracle.dski import DSKI, Grid
 from oracle.solve import pivoted_cholesky, QRPreconditioner, pcg, chol_logdet
-from oracle.slq import lanczos_T_from_cg, lanczos_full, slq_logdet, quadrature_logdet_term
-from oracle.probes import splitmix64_stream, splitmix64_at, rademacher
+from oracle.slq import (lanczos_T_from_cg, lanczos_full, slq_logdet, quadrature_logdet_term,
+                        slq_logdet_z)
+from oracle.probes import splitmix64_stream, splitmix64_at, rademacher, preconditioned_probes
 
 
 def _op(n, seed, m=12):
@@ -66,3 +67,36 @@ def test_splitmix_counter_equals_stream_and_rademacher_layout():
     big = rademacher(5, 4000, 5)
     assert set(np.unique(big)) == {-1.0, 1.0}
     assert abs(big.mean()) < 0.03
+
+
+def test_factor_probes_square_to_the_preconditioner():
+    """C = [D^1/2, L] satisfies C C^T = M, and the probe generator is C w."""
+    op = _op(10, 5)
+    L, _, _ = pivoted_cholesky(op.kgrad_diag(), op.kgrad_row, 6)
+    Pc = QRPreconditioner(L, op.noise)
+    C = Pc.factor_apply(np.eye(op.N + 6))
+    assert np.allclose(C @ C.T, np.diag(op.noise) + L @ L.T, rtol=0, atol=1e-13)
+    Z = preconditioned_probes(99, Pc, 3)
+    assert np.allclose(Z, C @ rademacher(99, op.N + 6, 3), rtol=0, atol=1e-14)
+
+
+def test_full_depth_factor_basis_probes_give_exact_logdet():
+    """Probes sqrt(P) C e_i (i < P = N + r) average z z^T to M exactly, so at
+    full Lanczos depth the preconditioned estimator is the exact log det."""
+    op = _op(4, 6, m=8)               # N = 12
+    A = op.dense()
+    L, _, _ = pivoted_cholesky(op.kgrad_diag(), op.kgrad_row, 3)
+    Pc = QRPreconditioner(L, op.noise)
+    P = op.N + 3
+    Z = np.sqrt(P) * Pc.factor_apply(np.eye(P))
+    est, _, _, _ = slq_logdet_z(op.mvm, Pc, Z, depth=op.N, rtol=1e-14)
+    assert abs(est - chol_logdet(A)) < 1e-8 * abs(chol_logdet(A))
+
+
+def test_preconditioned_rademacher_within_standard_errors():
+    op = _op(30, 7)
+    A = op.dense()
+    L, _, _ = pivoted_cholesky(op.kgrad_diag(), op.kgrad_row, 10)
+    Pc = QRPreconditioner(L, op.noise)
+    est, se, _, _ = slq_logdet_z(op.mvm, Pc, preconditioned_probes(5, Pc, 24), depth=30)
+    assert abs(est - chol_logdet(A)) < 4 * se + 1e-6 * abs(chol_logdet(A))
