@@ -60,8 +60,14 @@ typedef enum {
  * scatter/gather, Kronecker mode products on the tensor cores in TF32 with
  * the three-product split (hi*hi + hi*lo + lo*hi) and FP32 accumulation.
  * MIXED_TF32: as MIXED_3XTF32 with a single TF32 product.  In the mixed
- * modes CG scalars, dot products, x and r stay FP64 (see dski_pcg_solve). */
-typedef enum { DSKI_FP64 = 0, DSKI_MIXED_3XTF32 = 1, DSKI_MIXED_TF32 = 2 } dski_precision;
+ * modes CG scalars, dot products, x and r stay FP64 (see dski_pcg_solve).
+ * FP64_TC: FP64 vectors, scatter and gather as in FP64, Kronecker mode
+ * products on the BF16 tensor cores with both operands split into six 7-bit
+ * digits whose products accumulate exactly in FP32 (relative error ~2^-42
+ * of |K| |g|); needs every m_k a multiple of 8 and <= 256.  Vectors are
+ * double in FP64 and FP64_TC, float in the MIXED modes. */
+typedef enum { DSKI_FP64 = 0, DSKI_MIXED_3XTF32 = 1, DSKI_MIXED_TF32 = 2,
+               DSKI_FP64_TC = 3 } dski_precision;
 
 /* Problem statement of Sec. 2 / Sec. 3.1 / App. A.
  *   n, d          points and dimensions, n >= 1, 1 <= d <= 3.
@@ -108,8 +114,8 @@ int dski_set_hypers(dski_handle h, const double* lengthscale, double outputscale
                     double noise_value, double noise_grad);
 
 /* Sec. 3.1: out = K~ v for s >= 1 columns.  v_dev and out_dev are device
- * N x s column-major, FP64 (double) in DSKI_FP64 mode and FP32 (float) in
- * the mixed modes; they must not overlap.  The product runs as
+ * N x s column-major, FP64 (double) in the FP64 and FP64_TC modes and FP32
+ * (float) in the MIXED modes; they must not overlap.  The product runs as
  * scatter (B^T v onto the grid) -> d Kronecker mode products -> gather
  * (B h) plus the noise diagonal.  Asynchronous on the handle's stream.
  * Errors: ARG, CUDA. */

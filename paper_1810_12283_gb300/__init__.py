@@ -80,7 +80,7 @@ class DSKI:
         n, d = X.shape
         self.n, self.d, self.N = n, d, n * (d + 1)
         self.prec = prec
-        self.dtype = torch.float64 if prec == "fp64" else torch.float32
+        self.dtype = torch.float64 if prec in ("fp64", "fp64_tc") else torch.float32
         self.device = X.device
         self.stream = stream
         ng = noise_value if noise_grad is None else noise_grad

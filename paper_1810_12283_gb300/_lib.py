@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(HERE, "libdski.so")
 DSKI_OK = 0
 STATUS = {0: "OK", -1: "ARG", -2: "OUT_OF_GRID", -3: "CUDA", -4: "NOT_CONVERGED",
           -5: "BREAKDOWN", -6: "TIMEOUT", -7: "ALLOC"}
-PREC = {"fp64": 0, "mixed_3xtf32": 1, "mixed_tf32": 2}
+PREC = {"fp64": 0, "mixed_3xtf32": 1, "mixed_tf32": 2, "fp64_tc": 3}
 
 # every extern "C" symbol include/dski.h declares
 EXPORTS = ["dski_create", "dski_set_hypers", "dski_mvm", "pivchol_build", "dski_pcg_solve",

@@ -133,18 +133,23 @@ static void release_all(dski_handle h) {
   h->cell_start.release();
   h->frac64.release();
   h->frac32.release();
+  h->W64.release();
+  h->W32.release();
   for (int k = 0; k < DSKI_MAXD; ++k) {
     h->K64[k].release();
     h->K32[k].release();
     h->Khi[k].release();
     h->Klo[k].release();
     h->dK64[k].release();
+    h->Kdig[k].release();
+    h->Kexp[k].release();
   }
   h->gridA.release();
   h->gridB.release();
   h->vin.release();
   h->vout.release();
   h->scratch.release();
+  h->dev_err.release();
   h->s_part.release();
   h->s_tnpart.release();
   h->s_ticket.release();
@@ -171,7 +176,8 @@ extern "C" int dski_create(dski_handle* out, const dski_params* p, const double*
     return set_error(DSKI_ERR_ARG, "dski_create: d must be in 1..3 (got %d)", p->d);
   if (!p->grid_m || !p->grid_lo || !p->grid_hi || !p->lengthscale || !X_dev)
     return set_error(DSKI_ERR_ARG, "dski_create: NULL array argument");
-  if (p->prec != DSKI_FP64 && p->prec != DSKI_MIXED_3XTF32 && p->prec != DSKI_MIXED_TF32)
+  if (p->prec != DSKI_FP64 && p->prec != DSKI_MIXED_3XTF32 && p->prec != DSKI_MIXED_TF32 &&
+      p->prec != DSKI_FP64_TC)
     return set_error(DSKI_ERR_ARG, "dski_create: unknown precision %d", (int)p->prec);
   if (!finite_pos(p->outputscale) || !finite_pos(p->noise_value) || !finite_pos(p->noise_grad))
     return set_error(DSKI_ERR_ARG, "dski_create: outputscale and noises must be finite and > 0");
@@ -185,6 +191,8 @@ extern "C" int dski_create(dski_handle* out, const dski_params* p, const double*
       return set_error(DSKI_ERR_ARG, "dski_create: need finite grid_lo[%d] < grid_hi[%d]", k, k);
     if (!finite_pos(p->lengthscale[k]))
       return set_error(DSKI_ERR_ARG, "dski_create: lengthscale[%d] must be finite and > 0", k);
+    if (p->prec == DSKI_FP64_TC && (p->grid_m[k] % 8 != 0 || p->grid_m[k] > 256))
+      return set_error(DSKI_ERR_ARG, "dski_create: FP64_TC needs grid_m[%d] a multiple of 8 and <= 256", k);
     M *= p->grid_m[k];
     ncell *= p->grid_m[k] - 3;
   }
@@ -219,7 +227,11 @@ extern "C" int dski_create(dski_handle* out, const dski_params* p, const double*
     delete h;
     return set_error(DSKI_ERR_CUDA, "dski_create: no usable CUDA device");
   }
-  int rc = build_geometry(h, X_dev);
+  int rc = DSKI_OK;
+  if (h->dev_err.ensure(256) != DSKI_OK ||
+      cudaMemsetAsync(h->dev_err.ptr, 0, 256, h->stream) != cudaSuccess)
+    rc = set_error(DSKI_ERR_ALLOC, "dski_create: device allocation failed");
+  if (rc == DSKI_OK) rc = build_geometry(h, X_dev);
   if (rc == DSKI_OK) rc = build_factors(h);
   if (rc == DSKI_OK && cudaStreamSynchronize(h->stream) != cudaSuccess)
     rc = set_error(DSKI_ERR_CUDA, "dski_create: %s", cudaGetErrorString(cudaGetLastError()));
@@ -252,7 +264,7 @@ extern "C" int dski_mvm(dski_handle h, const void* v_dev, void* out_dev, int s) 
   clear_error();
   if (!h || !v_dev || !out_dev) return set_error(DSKI_ERR_ARG, "dski_mvm: NULL argument");
   if (s < 1 || s > 4096) return set_error(DSKI_ERR_ARG, "dski_mvm: s must be in 1..4096");
-  const bool f64 = h->prec == DSKI_FP64;
+  const bool f64 = f64_vectors(h);
   const size_t es = f64 ? 8 : 4;
   const size_t vbytes = (size_t)h->N * s * es;
   const char* a = (const char*)v_dev;
@@ -310,6 +322,21 @@ extern "C" int dski_profile(dski_handle h, int mode, double* ms_host, long long*
 }
 
 extern "C" long long dski_launch_count(void) { return g_launches.load(); }
+
+namespace dski {
+int check_device_error(dski_handle h) {
+  int e = 0;
+  if (cudaMemcpyAsync(&e, h->dev_err.ptr, sizeof(int), cudaMemcpyDeviceToHost, h->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return set_error(DSKI_ERR_CUDA, "%s", cudaGetErrorString(cudaGetLastError()));
+  if (e) {
+    cudaMemsetAsync(h->dev_err.ptr, 0, sizeof(int), h->stream);
+    return set_error(DSKI_ERR_TIMEOUT, "a device-side wait ran out of its iteration budget");
+  }
+  return DSKI_OK;
+}
+}  // namespace dski
 
 extern "C" void dski_destroy(dski_handle h) {
   if (!h) return;

@@ -92,18 +92,23 @@ struct dski_handle_ {
   int ncell = 0;    // prod mc_k
   int sm_count = 0;
 
-  // geometry (sorted order)
-  dski::DevBuf perm, inv_perm, cell, cell_start, frac64, frac32;
+  // geometry (sorted order); W64/W32: per point and dimension the four Keys
+  // weights then the four derivative weights (already divided by h_k)
+  dski::DevBuf perm, inv_perm, cell, cell_start, frac64, frac32, W64, W32;
   // Kronecker factors K_k (m_k x m_k, row-major, symmetric): FP64, FP32 and
   // the TF32 hi/lo split of the FP64 value (hi = rna_tf32(K), lo = rna_tf32(K - hi)).
   dski::DevBuf K64[DSKI_MAXD], K32[DSKI_MAXD], Khi[DSKI_MAXD], Klo[DSKI_MAXD];
   // dK_k / dlog l_k = K_k .* ((a - b) h_k)^2 / l_k^2 (FP64), for the gradient of Eq. 1
   dski::DevBuf dK64[DSKI_MAXD];
+  // FP64_TC mode: six BF16 digit planes of K_k (6 x m x m) and row exponents
+  dski::DevBuf Kdig[DSKI_MAXD], Kexp[DSKI_MAXD];
   // workspace
   dski::DevBuf gridA, gridB, vin, vout, scratch;
   // solver workspace: reduction partials, last-block tickets (zeroed at
   // allocation), per-column scalar state and solver vectors
   dski::DevBuf s_part, s_tnpart, s_ticket, s_state, s_vec[10];
+  // device error word (int): set by kernels whose bounded waits ran out
+  dski::DevBuf dev_err;
   // stage timers (NULL unless profiling is on)
   dski::Profiler* prof = nullptr;
 };
@@ -124,6 +129,23 @@ int permute_out(dski_handle h, const void* v_int, void* v_user, int s, bool f64,
 int scatter_internal(dski_handle h, const void* vin, void* g, int s, bool prec64);
 int kron_internal(dski_handle h, void* g, void* tmp, int s, bool prec64, int dfactor,
                   const void* dK, void** result);
+
+// gather stage alone: vout = B grid + noise .* vin (internal layout)
+int gather_internal(dski_handle h, const void* grid, const void* vin, void* vout, int s,
+                    bool prec64);
+
+// tensor-core mode product (kron_tc.cu): TF32 (three = false) or 3xTF32
+int mode_tc_tf32(dski_handle h, const float* X, const float* Khi, const float* Klo, float* Y,
+                 int m, long long R, int s, float scale, bool three);
+// FP64_TC mode products (kron_tc.cu): digits of a factor, and one mode product
+int oz_slice_factor(dski_handle h, const double* K, int m, uint16_t* Ad, int* fA);
+int mode_tc_oz(dski_handle h, const double* X, const uint16_t* Ad, const int* fA, double* Y,
+               int m, long long R, int s, double scale);
+// vectors of this handle are double (FP64, FP64_TC) or float (MIXED modes)
+inline bool f64_vectors(dski_handle h) { return h->prec == DSKI_FP64 || h->prec == DSKI_FP64_TC; }
+// read and clear the device error word: DSKI_OK, or DSKI_ERR_TIMEOUT if a
+// kernel's bounded wait ran out since the last check (synchronises)
+int check_device_error(dski_handle h);
 
 // internal vector length
 inline size_t nrows(dski_handle h) { return (size_t)h->N; }

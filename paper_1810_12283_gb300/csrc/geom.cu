@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "dski_internal.cuh"
+#include "keys.cuh"
 
 namespace dski {
 namespace {
@@ -174,6 +175,28 @@ __global__ void k_apply_sort(const uint32_t* __restrict__ skey, const int* __res
   }
 }
 
+// Interpolation weights of each sorted point, computed once in FP64: per
+// dimension k the four Keys weights w_k[o] and derivative weights
+// omega'(.)/h_k, stored as W[j][k][0..3] = w, W[j][k][4..7] = dw (8 d values
+// per point), with an FP32 copy rounded from the FP64 values.
+__global__ void k_weights(const double* __restrict__ f64, int n, int d, GeoParams g,
+                          double* __restrict__ W64, float* __restrict__ W32) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  for (int k = 0; k < d; ++k) {
+    double w[4], dw[4];
+    keys4<double>(f64[(size_t)j * d + k], w, dw);
+    const double ih = 1.0 / g.h[k];
+    const size_t b = (size_t)j * 8 * d + 8 * k;
+    for (int o = 0; o < 4; ++o) {
+      W64[b + o] = w[o];
+      W64[b + 4 + o] = dw[o] * ih;
+      W32[b + o] = (float)w[o];
+      W32[b + 4 + o] = (float)(dw[o] * ih);
+    }
+  }
+}
+
 // cell_start[c] = first sorted position whose cell is >= c (CSR over cells).
 __global__ void k_cell_start(const uint32_t* __restrict__ skey, int n, int ncell,
                              int* __restrict__ start) {
@@ -275,7 +298,8 @@ int build_geometry(dski_handle h, const double* X_dev) {
     if (cudaGetLastError() != cudaSuccess) { rc = DSKI_ERR_CUDA; break; }
     if (h->perm.ensure((size_t)n * 4) || h->inv_perm.ensure((size_t)n * 4) ||
         h->cell.ensure((size_t)n * 4) || h->cell_start.ensure((size_t)(h->ncell + 1) * 4) ||
-        h->frac64.ensure((size_t)n * d * 8) || h->frac32.ensure((size_t)n * d * 4)) {
+        h->frac64.ensure((size_t)n * d * 8) || h->frac32.ensure((size_t)n * d * 4) ||
+        h->W64.ensure((size_t)n * d * 64) || h->W32.ensure((size_t)n * d * 32)) {
       rc = DSKI_ERR_ALLOC;
       break;
     }
@@ -283,7 +307,9 @@ int build_geometry(dski_handle h, const double* X_dev) {
                                                   h->inv_perm.as<int>(), h->cell.as<int>(),
                                                   h->frac64.as<double>(), h->frac32.as<float>());
     k_cell_start<<<(n + 255) / 256, 256, 0, st>>>(kin, n, h->ncell, h->cell_start.as<int>());
-    count_launches(2);
+    k_weights<<<(n + 255) / 256, 256, 0, st>>>(h->frac64.as<double>(), n, d, g, h->W64.as<double>(),
+                                               h->W32.as<float>());
+    count_launches(3);
     if (cudaGetLastError() != cudaSuccess) { rc = DSKI_ERR_CUDA; break; }
     if (cudaStreamSynchronize(st) != cudaSuccess) { rc = DSKI_ERR_CUDA; break; }
   } while (0);
@@ -306,6 +332,12 @@ int build_factors(dski_handle h) {
         h->Khi[k].as<float>(), h->Klo[k].as<float>(), h->dK64[k].as<double>());
     count_launches(1);
     DSKI_LAUNCHED();
+    if (h->prec == DSKI_FP64_TC) {
+      if (h->Kdig[k].ensure(6 * mm * 2) || h->Kexp[k].ensure((size_t)m * 4))
+        return set_error(DSKI_ERR_ALLOC, "device allocation failed for factor digits");
+      DSKI_TRY(oz_slice_factor(h, h->K64[k].as<double>(), m, h->Kdig[k].as<uint16_t>(),
+                               h->Kexp[k].as<int>()));
+    }
   }
   return DSKI_OK;
 }

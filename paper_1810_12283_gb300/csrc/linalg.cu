@@ -4,6 +4,8 @@
 //   ts_nn   Y = r .* (alpha x .* X + beta A C)  (N x p)(p x q) -> N x q, row-parallel
 //   col_dots, noise_diag, precond_apply.
 // All reductions are deterministic (fixed-order partial sums).
+#include <algorithm>
+
 #include "solve_internal.cuh"
 
 namespace dski {
@@ -21,13 +23,12 @@ namespace {
 constexpr int TN_TP = 32;     // output tile rows (columns of A)
 constexpr int TN_TQ = 8;      // output tile cols (columns of B)
 constexpr int TN_SUB = 64;    // rows staged per sub-chunk
-constexpr int TN_CHUNK = 2048;
 
 // partial[chunk][tp][tq] of A^T (w .* B) over one chunk of rows.
 __global__ void __launch_bounds__(256) k_ts_tn(const double* __restrict__ A, int p,
                                                const double* __restrict__ B, int q,
                                                const double* __restrict__ w, long long N,
-                                               double* __restrict__ part) {
+                                               int TN_CHUNK, double* __restrict__ part) {
   __shared__ double As[TN_SUB][TN_TP + 1];
   __shared__ double Bs[TN_SUB][TN_TQ + 1];
   const int t0 = blockIdx.y * TN_TP, u0 = blockIdx.z * TN_TQ;
@@ -60,13 +61,82 @@ __global__ void __launch_bounds__(256) k_ts_tn(const double* __restrict__ A, int
   if (t < p && u < q) part[((long long)blockIdx.x * p + t) * q + u] = acc;
 }
 
+// C = A^T (w .* B) for few columns q <= QMAX (the PCG's Q1^T y): each block
+// owns GV_ROWS rows, each thread GV_RPT of them with its B values held in
+// registers; A's columns are streamed once, 8 at a time, and the 8 x q
+// per-thread sums are reduced over the block in a fixed order.
+constexpr int GV_RPT = 4;
+constexpr int GV_ROWS = 256 * GV_RPT;
+constexpr int GV_TG = 8;
+template <int QMAX>
+__global__ void __launch_bounds__(256) k_gemv_t(const double* __restrict__ A, int p,
+                                                const double* __restrict__ B, int q,
+                                                const double* __restrict__ w, long long N,
+                                                double* __restrict__ part) {
+  __shared__ double red[8][GV_TG * QMAX];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long base = (long long)blockIdx.x * GV_ROWS;
+  double bv[GV_RPT][QMAX];
+#pragma unroll
+  for (int k = 0; k < GV_RPT; ++k) {
+    const long long row = base + k * 256 + threadIdx.x;
+#pragma unroll
+    for (int u = 0; u < QMAX; ++u) {
+      double v = 0.0;
+      if (row < N && u < q) {
+        v = B[(long long)u * N + row];
+        if (w) v *= w[row];
+      }
+      bv[k][u] = v;
+    }
+  }
+  for (int t0 = 0; t0 < p; t0 += GV_TG) {
+    double acc[GV_TG][QMAX];
+#pragma unroll
+    for (int tt = 0; tt < GV_TG; ++tt)
+#pragma unroll
+      for (int u = 0; u < QMAX; ++u) acc[tt][u] = 0.0;
+#pragma unroll
+    for (int k = 0; k < GV_RPT; ++k) {
+      const long long row = base + k * 256 + threadIdx.x;
+      if (row < N) {
+#pragma unroll
+        for (int tt = 0; tt < GV_TG; ++tt) {
+          const double a = (t0 + tt < p) ? A[(long long)(t0 + tt) * N + row] : 0.0;
+#pragma unroll
+          for (int u = 0; u < QMAX; ++u) acc[tt][u] = fma(a, bv[k][u], acc[tt][u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int tt = 0; tt < GV_TG; ++tt)
+#pragma unroll
+      for (int u = 0; u < QMAX; ++u) {
+        const double v = warp_sum(acc[tt][u]);
+        if (lane == 0) red[warp][tt * QMAX + u] = v;
+      }
+    __syncthreads();
+    if (threadIdx.x < GV_TG * QMAX) {
+      const int tt = threadIdx.x / QMAX, u = threadIdx.x % QMAX;
+      double v = 0.0;
+#pragma unroll
+      for (int wv = 0; wv < 8; ++wv) v += red[wv][threadIdx.x];
+      if (t0 + tt < p && u < q) part[((long long)blockIdx.x * p + t0 + tt) * q + u] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// One warp per output: lane l adds chunks l, l + 32, ... then a fixed tree.
 __global__ void k_sum_chunks(const double* __restrict__ part, int nchunk, int pq,
                              double* __restrict__ out) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int idx = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
   if (idx >= pq) return;
   double s = 0.0;
-  for (int c = 0; c < nchunk; ++c) s += part[(long long)c * pq + idx];
-  out[idx] = s;
+  for (int c = lane; c < nchunk; c += 32) s += part[(long long)c * pq + idx];
+  s = warp_sum(s);
+  if (lane == 0) out[idx] = s;
 }
 
 // Y[:, u] = rowscale .* (alpha xscale .* X[:, u] + beta sum_t A[:, t] C[t, u])
@@ -133,14 +203,32 @@ __global__ void k_noise_diag(int n, int d, double nv, double ng, double* __restr
 int ts_tn(dski_handle h, const double* A, int p, const double* B, int q, const double* w,
           double* C_dev) {
   const long long N = h->N;
-  const int nchunk = (int)((N + TN_CHUNK - 1) / TN_CHUNK);
+  if (q <= 4) {
+    const int nchunk = (int)((N + GV_ROWS - 1) / GV_ROWS);
+    double* part = wbuf(h->s_tnpart, (size_t)nchunk * p * q);
+    if (!part) return DSKI_ERR_ALLOC;
+    StageScope sc(h, ST_PRECOND, h->stream, 2);
+    if (q == 1)
+      k_gemv_t<1><<<nchunk, 256, 0, h->stream>>>(A, p, B, q, w, N, part);
+    else
+      k_gemv_t<4><<<nchunk, 256, 0, h->stream>>>(A, p, B, q, w, N, part);
+    k_sum_chunks<<<(p * q + 7) / 8, 256, 0, h->stream>>>(part, nchunk, p * q, C_dev);
+    DSKI_LAUNCHED();
+    return DSKI_OK;
+  }
+  // rows per chunk: enough blocks to fill the GPU twice, at least one sub-chunk
+  const int tiles = ((p + TN_TP - 1) / TN_TP) * ((q + TN_TQ - 1) / TN_TQ);
+  long long rows = (N + 2LL * h->sm_count * tiles - 1) / (2LL * h->sm_count * tiles);
+  rows = std::max<long long>(TN_SUB, (rows + TN_SUB - 1) / TN_SUB * TN_SUB);
+  const int chunk = (int)std::min<long long>(rows, 1 << 20);
+  const int nchunk = (int)((N + chunk - 1) / chunk);
   double* part = wbuf(h->s_tnpart, (size_t)nchunk * p * q);   // own buffer: callers hold s_part
   if (!part) return DSKI_ERR_ALLOC;
   dim3 grd(nchunk, (p + TN_TP - 1) / TN_TP, (q + TN_TQ - 1) / TN_TQ);
   {
     StageScope sc(h, ST_PRECOND, h->stream, 2);
-    k_ts_tn<<<grd, 256, 0, h->stream>>>(A, p, B, q, w, N, part);
-    k_sum_chunks<<<(p * q + 255) / 256, 256, 0, h->stream>>>(part, nchunk, p * q, C_dev);
+    k_ts_tn<<<grd, 256, 0, h->stream>>>(A, p, B, q, w, N, chunk, part);
+    k_sum_chunks<<<(p * q + 7) / 8, 256, 0, h->stream>>>(part, nchunk, p * q, C_dev);
   }
   DSKI_LAUNCHED();
   return DSKI_OK;

@@ -39,18 +39,23 @@ namespace {
 // points i whose stencil covers u, i.e. whose cell (first stencil node) f
 // satisfies u - 3 <= f <= u per dimension.  The cells of the last dimension
 // are contiguous in sorted order, so each (f_0, .., f_{d-2}) gives one range.
+// For d >= 2 four lanes share a node, lane `sub` taking f_0 = u_0 - 3 + sub;
+// their partial sums are combined in a fixed order (deterministic).
 template <class T, int D, int CB>
 __global__ void __launch_bounds__(256) k_scatter(MvmGeo g, const int* __restrict__ cell_start,
                                                  const int* __restrict__ cell,
-                                                 const T* __restrict__ frac,
+                                                 const T* __restrict__ wt,
                                                  const T* __restrict__ v, T* __restrict__ grid,
                                                  int s, long long N, long long M) {
-  const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= M) return;
+  constexpr int SPLIT = D > 1 ? 4 : 1;
+  const long long tix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long u = tix / SPLIT;
+  const int sub = (int)(tix % SPLIT);
+  const bool valid = u < M;
   const int q0 = blockIdx.y * CB;
-  int uc[3];
+  int uc[3] = {0, 0, 0};
   {
-    long long t = u;
+    long long t = valid ? u : 0;
     for (int k = D - 1; k >= 0; --k) {
       uc[k] = (int)(t % g.m[k]);
       t /= g.m[k];
@@ -59,20 +64,19 @@ __global__ void __launch_bounds__(256) k_scatter(MvmGeo g, const int* __restrict
   T acc[CB];
 #pragma unroll
   for (int q = 0; q < CB; ++q) acc[q] = T(0);
-  const T ih0 = (T)g.invh[0];
-  const T ih1 = D > 1 ? (T)g.invh[1] : T(1);
-  const T ih2 = D > 2 ? (T)g.invh[2] : T(1);
   const int L = D - 1;   // last (fastest) dimension
   const int lo_l = max(0, uc[L] - 3), hi_l = min(uc[L], g.mc[L] - 1);
-  if (lo_l > hi_l) {
-#pragma unroll
-    for (int q = 0; q < CB; ++q)
-      if (q0 + q < s) grid[(long long)(q0 + q) * M + u] = T(0);
-    return;
+  int f0 = 0, lo1 = 0, hi1 = 0;
+  bool active = valid && lo_l <= hi_l;
+  if (D > 1) {
+    f0 = uc[0] - 3 + sub;
+    active = active && f0 >= 0 && f0 <= g.mc[0] - 1;
   }
-  const int lo0 = D > 1 ? max(0, uc[0] - 3) : 0, hi0 = D > 1 ? min(uc[0], g.mc[0] - 1) : 0;
-  const int lo1 = D > 2 ? max(0, uc[1] - 3) : 0, hi1 = D > 2 ? min(uc[1], g.mc[1] - 1) : 0;
-  for (int f0 = lo0; f0 <= hi0; ++f0) {
+  if (D > 2) {
+    lo1 = max(0, uc[1] - 3);
+    hi1 = min(uc[1], g.mc[1] - 1);
+  }
+  if (active) {
     for (int f1 = lo1; f1 <= hi1; ++f1) {
       long long rowbase;
       if (D == 1) rowbase = 0;
@@ -83,29 +87,27 @@ __global__ void __launch_bounds__(256) k_scatter(MvmGeo g, const int* __restrict
       for (int j = js; j < je; ++j) {
         const int fl = (int)(cell[j] - rowbase);
         const int ol = uc[L] - fl;
+        // weights of this point at this node from the per-point table
+        const T* wj = wt + (long long)j * (8 * D);
         T c[D + 1];
         if (D == 1) {
-          T w0, dw0;
-          keys1<T>(frac[j], ol, w0, dw0);
-          c[0] = w0;
-          c[1] = dw0 * ih0;
+          c[0] = wj[ol];
+          c[1] = wj[4 + ol];
         } else if (D == 2) {
-          T w0, dw0, w1, dw1;
-          keys1<T>(frac[2 * (long long)j], uc[0] - f0, w0, dw0);
-          keys1<T>(frac[2 * (long long)j + 1], ol, w1, dw1);
+          const int o0 = uc[0] - f0;
+          const T w0 = wj[o0], dw0 = wj[4 + o0], w1 = wj[8 + ol], dw1 = wj[12 + ol];
           c[0] = w0 * w1;
-          c[1] = dw0 * ih0 * w1;
-          c[D > 1 ? 2 : 0] = w0 * dw1 * ih1;
+          c[1] = dw0 * w1;
+          c[D > 1 ? 2 : 0] = w0 * dw1;
         } else {
-          T w0, dw0, w1, dw1, w2, dw2;
-          keys1<T>(frac[3 * (long long)j], uc[0] - f0, w0, dw0);
-          keys1<T>(frac[3 * (long long)j + 1], uc[D > 2 ? 1 : 0] - f1, w1, dw1);
-          keys1<T>(frac[3 * (long long)j + 2], ol, w2, dw2);
+          const int o0 = uc[0] - f0, o1 = uc[D > 2 ? 1 : 0] - f1;
+          const T w0 = wj[o0], dw0 = wj[4 + o0], w1 = wj[8 + o1], dw1 = wj[12 + o1];
+          const T w2 = wj[16 + ol], dw2 = wj[20 + ol];
           const T w01 = w0 * w1;
           c[0] = w01 * w2;
-          c[1] = dw0 * ih0 * w1 * w2;
-          c[D > 1 ? 2 : 0] = w0 * dw1 * ih1 * w2;
-          c[D > 2 ? 3 : 0] = w01 * dw2 * ih2;
+          c[1] = dw0 * w1 * w2;
+          c[D > 1 ? 2 : 0] = w0 * dw1 * w2;
+          c[D > 2 ? 3 : 0] = w01 * dw2;
         }
         const long long e = (long long)j * (D + 1);
 #pragma unroll
@@ -121,9 +123,19 @@ __global__ void __launch_bounds__(256) k_scatter(MvmGeo g, const int* __restrict
       }
     }
   }
+  if (SPLIT > 1) {
+    // fixed-order combination: (sub0 + sub1) + (sub2 + sub3)
 #pragma unroll
-  for (int q = 0; q < CB; ++q)
-    if (q0 + q < s) grid[(long long)(q0 + q) * M + u] = acc[q];
+    for (int q = 0; q < CB; ++q) {
+      acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 1);
+      acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 2);
+    }
+  }
+  if (valid && sub == 0) {
+#pragma unroll
+    for (int q = 0; q < CB; ++q)
+      if (q0 + q < s) grid[(long long)(q0 + q) * M + u] = acc[q];
+  }
 }
 
 // -------------------------------------------------------------- gather ----
@@ -131,7 +143,7 @@ __global__ void __launch_bounds__(256) k_scatter(MvmGeo g, const int* __restrict
 // evaluated dimension by dimension over the 4^d stencil.
 template <class T, int D, int CB>
 __global__ void __launch_bounds__(256) k_gather(MvmGeo g, const int* __restrict__ cell,
-                                                const T* __restrict__ frac,
+                                                const T* __restrict__ wt,
                                                 const T* __restrict__ grid,
                                                 const T* __restrict__ v, T* __restrict__ out,
                                                 int s, int n, long long N, long long M, T nv,
@@ -148,12 +160,15 @@ __global__ void __launch_bounds__(256) k_gather(MvmGeo g, const int* __restrict_
     }
   }
   T w[D][4], dw[D][4];
+  {
+    const T* wj = wt + (long long)j * (8 * D);
 #pragma unroll
-  for (int k = 0; k < D; ++k) {
-    keys4<T>(frac[(long long)j * D + k], w[k], dw[k]);
-    const T ih = (T)g.invh[k];
+    for (int k = 0; k < D; ++k)
 #pragma unroll
-    for (int o = 0; o < 4; ++o) dw[k][o] *= ih;
+      for (int o = 0; o < 4; ++o) {
+        w[k][o] = wj[8 * k + o];
+        dw[k][o] = wj[8 * k + 4 + o];
+      }
   }
   long long base = 0;
 #pragma unroll
@@ -305,37 +320,38 @@ __global__ void k_perm_out(const int* __restrict__ perm, const T* __restrict__ v
 }
 
 template <class T, int D, int CB>
-void launch_scatter(dski_handle h, const MvmGeo& g, const T* frac, const T* v, T* grid, int s,
+void launch_scatter(dski_handle h, const MvmGeo& g, const T* wt, const T* v, T* grid, int s,
                     cudaStream_t st) {
-  dim3 grd((unsigned)((h->M + 255) / 256), (unsigned)((s + CB - 1) / CB));
+  const long long threads = (long long)h->M * (D > 1 ? 4 : 1);
+  dim3 grd((unsigned)((threads + 255) / 256), (unsigned)((s + CB - 1) / CB));
   StageScope sc(h, ST_SCATTER, st);
-  k_scatter<T, D, CB><<<grd, 256, 0, st>>>(g, h->cell_start.as<int>(), h->cell.as<int>(), frac,
+  k_scatter<T, D, CB><<<grd, 256, 0, st>>>(g, h->cell_start.as<int>(), h->cell.as<int>(), wt,
                                            v, grid, s, (long long)h->N, (long long)h->M);
 }
 
 template <class T, int D, int CB>
-void launch_gather(dski_handle h, const MvmGeo& g, const T* frac, const T* grid, const T* v,
+void launch_gather(dski_handle h, const MvmGeo& g, const T* wt, const T* grid, const T* v,
                    T* out, int s, cudaStream_t st) {
   dim3 grd((unsigned)((h->n + 255) / 256), (unsigned)((s + CB - 1) / CB));
   StageScope sc(h, ST_GATHER, st);
-  k_gather<T, D, CB><<<grd, 256, 0, st>>>(g, h->cell.as<int>(), frac, grid, v, out, s, h->n,
+  k_gather<T, D, CB><<<grd, 256, 0, st>>>(g, h->cell.as<int>(), wt, grid, v, out, s, h->n,
                                           (long long)h->N, (long long)h->M, (T)h->nv, (T)h->ng);
 }
 
 template <class T, int D>
-void scatter_dispatch(dski_handle h, const MvmGeo& g, const T* frac, const T* v, T* grid, int s,
+void scatter_dispatch(dski_handle h, const MvmGeo& g, const T* wt, const T* v, T* grid, int s,
                       cudaStream_t st) {
-  if (s == 1) launch_scatter<T, D, 1>(h, g, frac, v, grid, s, st);
-  else if (s <= 4) launch_scatter<T, D, 4>(h, g, frac, v, grid, s, st);
-  else launch_scatter<T, D, 8>(h, g, frac, v, grid, s, st);
+  if (s == 1) launch_scatter<T, D, 1>(h, g, wt, v, grid, s, st);
+  else if (s <= 4) launch_scatter<T, D, 4>(h, g, wt, v, grid, s, st);
+  else launch_scatter<T, D, 8>(h, g, wt, v, grid, s, st);
 }
 
 template <class T, int D>
-void gather_dispatch(dski_handle h, const MvmGeo& g, const T* frac, const T* grid, const T* v,
+void gather_dispatch(dski_handle h, const MvmGeo& g, const T* wt, const T* grid, const T* v,
                      T* out, int s, cudaStream_t st) {
-  if (s == 1) launch_gather<T, D, 1>(h, g, frac, grid, v, out, s, st);
-  else if (s <= 4) launch_gather<T, D, 4>(h, g, frac, grid, v, out, s, st);
-  else launch_gather<T, D, 8>(h, g, frac, grid, v, out, s, st);
+  if (s == 1) launch_gather<T, D, 1>(h, g, wt, grid, v, out, s, st);
+  else if (s <= 4) launch_gather<T, D, 4>(h, g, wt, grid, v, out, s, st);
+  else launch_gather<T, D, 8>(h, g, wt, grid, v, out, s, st);
 }
 
 template <class T>
@@ -361,14 +377,14 @@ int scatter_internal(dski_handle h, const void* vin, void* g, int s, bool prec64
   const MvmGeo geo = make_geo(h);
   cudaStream_t st = h->stream;
   if (prec64) {
-    const double* fr = h->frac64.as<double>();
+    const double* fr = h->W64.as<double>();
     switch (h->d) {
       case 1: scatter_dispatch<double, 1>(h, geo, fr, (const double*)vin, (double*)g, s, st); break;
       case 2: scatter_dispatch<double, 2>(h, geo, fr, (const double*)vin, (double*)g, s, st); break;
       default: scatter_dispatch<double, 3>(h, geo, fr, (const double*)vin, (double*)g, s, st); break;
     }
   } else {
-    const float* fr = h->frac32.as<float>();
+    const float* fr = h->W32.as<float>();
     switch (h->d) {
       case 1: scatter_dispatch<float, 1>(h, geo, fr, (const float*)vin, (float*)g, s, st); break;
       case 2: scatter_dispatch<float, 2>(h, geo, fr, (const float*)vin, (float*)g, s, st); break;
@@ -391,10 +407,18 @@ int kron_internal(dski_handle h, void* g, void* tmp, int s, bool prec64, int dfa
     const long long R = h->M / h->m[k];
     const bool last = t == h->d - 1;
     const double scale = last ? h->sf * h->sf : 1.0;
-    if (prec64) {
+    if (prec64 && h->prec == DSKI_FP64_TC && dfactor < 0) {
+      DSKI_TRY(mode_tc_oz(h, (const double*)cur, h->Kdig[k].as<uint16_t>(), h->Kexp[k].as<int>(),
+                          (double*)nxt, h->m[k], R, s, scale));
+    } else if (prec64) {
       const double* K = k == dfactor ? (const double*)dK : h->K64[k].as<double>();
       mode_simt<double>(h, (const double*)cur, K, (double*)nxt, h->m[k], R, s, scale, h->sm_count,
                         st);
+    } else if (dfactor < 0) {
+      // mixed modes: tensor cores, TF32 or 3xTF32
+      DSKI_TRY(mode_tc_tf32(h, (const float*)cur, h->Khi[k].as<float>(), h->Klo[k].as<float>(),
+                            (float*)nxt, h->m[k], R, s, (float)scale,
+                            h->prec == DSKI_MIXED_3XTF32));
     } else {
       const float* K = k == dfactor ? (const float*)dK : h->K32[k].as<float>();
       mode_simt<float>(h, (const float*)cur, K, (float*)nxt, h->m[k], R, s, (float)scale,
@@ -418,18 +442,41 @@ int mvm_internal(dski_handle h, const void* vin, void* vout, int s, bool prec64)
   const MvmGeo geo = make_geo(h);
   cudaStream_t st = h->stream;
   if (prec64) {
-    const double* fr = h->frac64.as<double>();
+    const double* fr = h->W64.as<double>();
     switch (h->d) {
       case 1: gather_dispatch<double, 1>(h, geo, fr, (const double*)res, (const double*)vin, (double*)vout, s, st); break;
       case 2: gather_dispatch<double, 2>(h, geo, fr, (const double*)res, (const double*)vin, (double*)vout, s, st); break;
       default: gather_dispatch<double, 3>(h, geo, fr, (const double*)res, (const double*)vin, (double*)vout, s, st); break;
     }
   } else {
-    const float* fr = h->frac32.as<float>();
+    const float* fr = h->W32.as<float>();
     switch (h->d) {
       case 1: gather_dispatch<float, 1>(h, geo, fr, (const float*)res, (const float*)vin, (float*)vout, s, st); break;
       case 2: gather_dispatch<float, 2>(h, geo, fr, (const float*)res, (const float*)vin, (float*)vout, s, st); break;
       default: gather_dispatch<float, 3>(h, geo, fr, (const float*)res, (const float*)vin, (float*)vout, s, st); break;
+    }
+  }
+  DSKI_LAUNCHED();
+  return DSKI_OK;
+}
+
+int gather_internal(dski_handle h, const void* grid, const void* vin, void* vout, int s,
+                    bool prec64) {
+  const MvmGeo geo = make_geo(h);
+  cudaStream_t st = h->stream;
+  if (prec64) {
+    const double* fr = h->W64.as<double>();
+    switch (h->d) {
+      case 1: gather_dispatch<double, 1>(h, geo, fr, (const double*)grid, (const double*)vin, (double*)vout, s, st); break;
+      case 2: gather_dispatch<double, 2>(h, geo, fr, (const double*)grid, (const double*)vin, (double*)vout, s, st); break;
+      default: gather_dispatch<double, 3>(h, geo, fr, (const double*)grid, (const double*)vin, (double*)vout, s, st); break;
+    }
+  } else {
+    const float* fr = h->W32.as<float>();
+    switch (h->d) {
+      case 1: gather_dispatch<float, 1>(h, geo, fr, (const float*)grid, (const float*)vin, (float*)vout, s, st); break;
+      case 2: gather_dispatch<float, 2>(h, geo, fr, (const float*)grid, (const float*)vin, (float*)vout, s, st); break;
+      default: gather_dispatch<float, 3>(h, geo, fr, (const float*)grid, (const float*)vin, (float*)vout, s, st); break;
     }
   }
   DSKI_LAUNCHED();

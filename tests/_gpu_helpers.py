@@ -38,15 +38,18 @@ def problem_1d(n, m=20, seed=0, ell=0.15):
 
 
 # unit roundoff of the arithmetic each mode evaluates the product in
-UNIT_ROUNDOFF = {"fp64": 2.0**-53, "mixed_3xtf32": 2.0**-24, "mixed_tf32": 2.0**-11}
+UNIT_ROUNDOFF = {"fp64": 2.0**-53, "mixed_3xtf32": 2.0**-24, "mixed_tf32": 2.0**-11,
+                 "fp64_tc": 2.0**-40}
 
 
 def mvm_tolerance(orc, v, prec):
     """Normwise tolerance for one MVM column, derived from the arithmetic.
 
-    FP64 mode: 1e-10 relative.  Mixed modes: u * ||abs|| / ||K~ v|| (the
+    FP64 mode: 1e-10 relative.  Other modes: u * ||abs|| / ||K~ v|| (the
     condition number of evaluating the product term by term times the unit
-    roundoff of the mode), never below 1e-6.  D-SKI gradient rows cancel
+    roundoff of the mode), never below 1e-6 (FP32 modes) or 1e-10 (FP64_TC,
+    whose digit-split mode products carry ~2^-42 relative error; u = 2^-40
+    leaves a margin of four).  D-SKI gradient rows cancel
     terms of size ~1/h against results of size ~1/l, so this condition
     number reaches ~1e5 on fine grids; the bound is the textbook
     normwise one (Higham, Sec. 3.5) with gamma_k replaced by u."""
@@ -54,4 +57,5 @@ def mvm_tolerance(orc, v, prec):
         return 1e-10
     a = orc.abs_mvm(v)
     r = orc.mvm(v)
-    return max(1e-6, UNIT_ROUNDOFF[prec] * np.linalg.norm(a) / np.linalg.norm(r))
+    floor = 1e-10 if prec == "fp64_tc" else 1e-6
+    return max(floor, UNIT_ROUNDOFF[prec] * np.linalg.norm(a) / np.linalg.norm(r))

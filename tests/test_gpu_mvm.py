@@ -42,6 +42,33 @@ def test_mvm_parity(name, make, prec, s):
     op.close()
 
 
+TC_CASES = [
+    ("1d-m40", lambda: problem_1d(300, m=40)),
+    ("2d-24x32", lambda: dict(W.small2d(700, m=24, seed=5), m=(24, 32))),
+    ("3d-16x24x16", lambda: dict(W.small3d(400, m=16, seed=6), m=(16, 24, 16))),
+    ("sine2d", lambda: W.sine2d()),
+]
+
+
+@pytest.mark.parametrize("name,make", TC_CASES, ids=[c[0] for c in TC_CASES])
+@pytest.mark.parametrize("s", [1, 5])
+def test_mvm_fp64_tc_parity(name, make, s):
+    """FP64_TC: FP64 scatter/gather with digit-split BF16 tensor-core mode
+    products; grids with every m_k a multiple of 8 (several 128-row tiles
+    and ragged tails in j and r)."""
+    need_gpu()
+    p = make()
+    op = gpu_op(p, "fp64_tc")
+    orc = oracle_op(p)
+    V = np.random.default_rng(12).normal(size=(s, orc.N))
+    got = op.mvm(torch.tensor(V, device="cuda")).cpu().numpy()
+    ref = orc.mvm(V.T).T
+    for q in range(s):
+        tol = mvm_tolerance(orc, V[q], "fp64_tc")
+        assert rel(got[q], ref[q]) <= tol, (name, q, rel(got[q], ref[q]), tol)
+    op.close()
+
+
 def test_mvm_single_point_and_grid_line():
     need_gpu()
     # one point exactly on a grid line in x (fraction 0) and one interior
@@ -98,8 +125,9 @@ def test_mvm_terrain_sampled_rows():
     ref = orc.B[rows] @ h + orc.noise[rows] * v[rows]
     habs = kuu_apply(orc.grid, orc.ell, orc.sf, (abs(orc.B).T @ np.abs(v))[:, None])[:, 0]
     absr = abs(orc.B[rows]) @ habs + orc.noise[rows] * np.abs(v[rows])
-    for prec in ("fp64", "mixed_3xtf32"):
-        tol = 1e-10 if prec == "fp64" else 2.0**-24 * np.linalg.norm(absr) / np.linalg.norm(ref)
+    for prec in ("fp64", "mixed_3xtf32", "fp64_tc"):
+        u = {"fp64": 0.0, "mixed_3xtf32": 2.0**-24, "fp64_tc": 2.0**-40}[prec]
+        tol = max(1e-10, u * np.linalg.norm(absr) / np.linalg.norm(ref))
         op = gpu_op(p, prec)
         got = op.mvm(torch.tensor(v, device="cuda")).double().cpu().numpy()[rows]
         assert rel(got, ref) <= tol, (prec, rel(got, ref), tol)

@@ -9,8 +9,12 @@
   kappa(K~) ~ 3.5e7, so ~1.9e4 iterations), several right-hand sides at
   once, plain CG (no preconditioner) too;
 * SLQ: with identical probes z = D^1/2 w1 + L w2 the GPU estimate equals the
-  oracle's to 1e-10 relative, and lies within 4 standard errors of the dense
-  log determinant;
+  oracle's to 1e-10 relative at a Lanczos depth (12) where the process is
+  still stable in floating point -- past it, two FP64 evaluation orders of
+  the same operator already differ by ~5e-5 relative (loss of orthogonality
+  once Ritz values converge), so at depth 25 the two must agree within 5% of
+  the standard error and lie within 4 standard errors of the dense log
+  determinant;
 * gradient of Eq. 1: equals the oracle's Hutchinson gradient with identical
   probes (1e-6, the solves run to rtol 1e-8) and the exact dense gradient
   within 4 standard errors of the probe mean.
@@ -79,16 +83,20 @@ def test_pcg_sine_matches_direct_solve():
     orc = oracle_op(p)
     A = orc.dense()
     pc = op.pivchol(p["rank"])
+    # the target at rtol 1e-10; two random right-hand sides at 1e-6 (for a
+    # random b, x is dominated by the smallest eigenvalues: the attainable
+    # FP64 residual is ~u kappa ~ 4e-9 and CG needs ~1e5 steps near it)
     rng = np.random.default_rng(3)
-    B = np.stack([p["y"], rng.normal(size=orc.N), rng.normal(size=orc.N)])
-    x, iters, relres = op.solve(torch.tensor(B, device="cuda"), pc, rtol=1e-10, maxit=60000)
-    x = x.cpu().numpy()
-    for q in range(B.shape[0]):
-        assert relres[q] <= 1e-10
-        true = np.linalg.norm(B[q] - A @ x[q]) / np.linalg.norm(B[q])
-        assert true <= 1.5e-10, (q, true)
-        xd = np.linalg.solve(A, B[q])
-        assert np.linalg.norm(A @ (x[q] - xd)) / np.linalg.norm(B[q]) <= 2e-10
+    for B, rtol in ((p["y"][None, :], 1e-10),
+                    (np.stack([rng.normal(size=orc.N), rng.normal(size=orc.N)]), 1e-6)):
+        x, iters, relres = op.solve(torch.tensor(B, device="cuda"), pc, rtol=rtol, maxit=60000)
+        x = x.cpu().numpy()
+        for q in range(B.shape[0]):
+            assert relres[q] <= rtol
+            true = np.linalg.norm(B[q] - A @ x[q]) / np.linalg.norm(B[q])
+            assert true <= 1.5 * rtol, (q, true)
+            xd = np.linalg.solve(A, B[q])
+            assert np.linalg.norm(A @ (x[q] - xd)) / np.linalg.norm(B[q]) <= 2 * rtol
     pc.close()
     op.close()
 
@@ -136,12 +144,17 @@ def test_slq_same_probes_and_dense():
     Lg, piv = pc.export()
     Lo, _, _ = pivoted_cholesky(orc.kgrad_diag(), orc.kgrad_row, 15, pivots=piv)
     Pc = _oracle_pc(orc, Lo)
-    P, depth, seed = 12, 25, 2024
-    ld, se = op.logdet(pc, probes=P, depth=depth, seed=seed)
+    P, seed = 12, 2024
     Z = preconditioned_probes(seed, Pc, P)
-    est, se_o, _, _ = slq_logdet_z(orc.mvm, Pc, Z, depth=depth, rtol=1e-15, maxit=depth)
+    ld, se = op.logdet(pc, probes=P, depth=12, seed=seed)
+    est, se_o, _, _ = slq_logdet_z(orc.mvm, Pc, Z, depth=12, rtol=1e-15, maxit=12)
     assert abs(ld - est) <= 1e-10 * abs(est), (ld, est)
-    assert abs(se - se_o) <= 1e-6 * se_o
+    assert abs(se - se_o) <= 1e-8 * se_o
+    ld, se = op.logdet(pc, probes=P, depth=25, seed=seed)
+    est, se_o, _, _ = slq_logdet_z(orc.mvm, Pc, Z, depth=25, rtol=1e-15, maxit=25)
+    # past the stable depth the two agree only up to the rounding-driven
+    # divergence of the Lanczos process, far below the statistical error
+    assert abs(ld - est) <= 0.05 * se_o, (ld, est, se_o)
     exact = chol_logdet(orc.dense())
     assert abs(ld - exact) <= 4 * se + 1e-8 * abs(exact)
     pc.close()
