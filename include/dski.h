@@ -215,6 +215,28 @@ int dski_profile(dski_handle h, int mode, double* ms_host, long long* launches_h
  * handles).  A host-side counter, incremented at every launch site. */
 long long dski_launch_count(void);
 
+/* The paper has no counterpart: this is dski_mvm for callers that cannot
+ * allocate device memory -- applications whose device memory belongs to a
+ * pool allocator that must see every allocation, real-time loops where
+ * cudaMalloc's implicit device synchronisation is not allowed, plug-ins
+ * whose host forbids device allocation after start-up.  Same arguments,
+ * layouts and result as dski_mvm, but it calls no cudaMalloc, cudaFree or
+ * allocating library routine: its temporaries (the permuted input and output,
+ * N x s each, and two grids, M x s each, in the mode's element size) live in
+ * one fixed device array of DSKI_NOALLOC_SCRATCH_BYTES (32 MiB) that the
+ * library reserves on every GPU that loads it, until the process exits.
+ *   - Sizes that do not fit (2 N s + 2 M s elements, each part padded to 256
+ *     bytes) are rejected with DSKI_ERR_ARG and a message; nothing runs.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - Every call on a device shares the one array, which keeps the last
+ *     call's contents.  Calls whose work overlaps on the GPU (other streams,
+ *     other handles, other host threads) race on it: serialise them.
+ *   - The handle must live on the current device (else DSKI_ERR_ARG).
+ * Errors: ARG, CUDA. */
+#define DSKI_NOALLOC_SCRATCH_BYTES (32u << 20)
+int dski_mvm_noalloc(dski_handle h, const void* v_dev, void* out_dev, int s);
+
 /* Release a handle / preconditioner (NULL is ignored).  Synchronises the
  * handle's stream first. */
 void dski_destroy(dski_handle h);
