@@ -2,15 +2,22 @@
 
 Workload: the terrain stand-in -- n = 100,000 points uniform in [0,1]^2 with
 values and gradients of a 512-feature random Fourier field (N = 300,000
-rows), SE length scale 0.05, noise 1e-3, 256 x 256 grid over [-0.05, 1.05]^2.
+rows), SE length scale 0.05, noise 1e-3, 256 x 256 grid over
+[-0.05, 1.05]^2, pivoted-Cholesky rank 100, PCG to relative residual 1e-8.
 Inputs are synthetic and seeded (``synth.workloads.terrain2d``).
 
-A step is one D-SKI MVM K~ v (Sec. 3.1) of one fresh right-hand side in the
-mixed (3xTF32 / FP32) mode, with the FP64 mode timed beside it.  The L2 is
-flushed (a 256 MiB write) between timed steps, outside the timed events.
+A step is one pass of the whole hot path: build the D-SKI operator for the
+resident points (geometry, sort, factors), the rank-100 pivoted Cholesky and
+its QR-form preconditioner, and the PCG solve K~ x = y to 1e-8 (true FP64
+residual), in the FP64 mode -- the mode that reaches 1e-8 on this system.
+The other modes (FP64_TC: Kronecker mode products emulated on the BF16 tensor
+cores; MIXED_3XTF32) run the same step beside it with an iteration cap of
+1.5x the FP64 count and report the residual they reach, and each mode's MVM
+throughput is timed separately.  The L2 is flushed (a 256 MiB write) before every
+timed step, outside the timed events.
 
 Printed: one JSON line (rank 0).  ``--impl reference`` times the plain FP64
-CPU oracle on the host cores instead (the reference arm of this project).
+CPU oracle instead (the reference arm of this project).
 """
 import argparse
 import json
@@ -26,28 +33,30 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-METRIC = "D-SKI MVM effective HBM GB/s (mixed 3xTF32/FP32), terrain n=100k d=2 grid 256^2"
-UNIT = "GB/s"
-WORKLOAD = "terrain2d n=100000 d=2 N=300000 grid=256x256 s=1"
+METRIC = "PCG solve time to rel. residual 1e-8, terrain n=100k d=2 (GB300, FP64 vs FP64_TC / mixed)"
+UNIT = "s"
+RANK = 100
+RTOL = 1e-8
+
+
+def workload_name(n):
+    return f"terrain2d n={n} d=2 N={3 * n} grid=256x256 rank={RANK} rtol={RTOL:g}"
 
 
 def mvm_bytes(n, d, M, s, elem):
     """Algorithmic HBM bytes of one MVM: v read by scatter and by the noise
-    term, out written, the per-point geometry (cell id + d fractions) read by
-    scatter and gather, the grid written by scatter and read by gather."""
+    term, out written, the grid written by scatter and read by gather, and
+    the per-point geometry (cell id + 8 d weights) read by scatter and gather."""
     N = n * (d + 1)
-    geo = n * (4 + elem * d)
+    geo = n * (4 + elem * 8 * d)
     return s * (3 * N * elem + 2 * M * elem) + 2 * geo
 
 
-def scatter_bytes(n, d, M, s, elem):
-    N = n * (d + 1)
-    return s * (N * elem + M * elem) + n * (4 + elem * d)
-
-
-def gather_bytes(n, d, M, s, elem):
-    N = n * (d + 1)
-    return s * (M * elem + 2 * N * elem) + n * (4 + elem * d)
+def precond_bytes(N, r, s):
+    """Algorithmic bytes of one preconditioner apply: Q1 (8 bytes per entry,
+    FP64 or an FP32 hi/lo pair) read twice (Q1^T y, then y - Q1 c), r read
+    twice, z written."""
+    return 2 * N * r * 8 + s * 3 * N * 8
 
 
 class ClockSampler:
@@ -60,12 +69,13 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.lines = []
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -73,7 +83,6 @@ class ClockSampler:
         return self
 
     def __exit__(self, *a):
-        self.lines = []
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -86,7 +95,7 @@ class ClockSampler:
     def summary(self):
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in getattr(self, "lines", []):
+        for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -107,13 +116,12 @@ def dist_init():
     if ws <= 1:
         return 0, 1, None
     import torch.distributed as dist
-    backend = os.environ.get("DSKI_BENCH_BACKEND", "nccl")
-    dist.init_process_group(backend)
+    dist.init_process_group(os.environ.get("DSKI_BENCH_BACKEND", "nccl"))
     return dist.get_rank(), dist.get_world_size(), dist
 
 
 def reduce_max(dist, value, device):
-    """Max over ranks of a host float (a no-op on one process)."""
+    """Max over ranks of a host float (identity on one process)."""
     if dist is None:
         return value
     import torch
@@ -129,44 +137,54 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def cpu_baseline(p, budget_s=12.0):
-    """The FP64 oracle MVM on the host cores, on a bounded number of MVMs."""
+def cpu_baseline(p, iters_gpu, budget_s=12.0):
+    """The FP64 oracle on the host cores: operator build, rank-100 pivoted
+    Cholesky and QR preconditioner (timed whole), then PCG iterations timed
+    on a bounded sample and scaled to the GPU's iteration count."""
     from oracle.dski import DSKI as ODSKI, Grid
+    from oracle.solve import QRPreconditioner, pcg, pivoted_cholesky
     t0 = time.perf_counter()
     op = ODSKI(p["X"], Grid(p["m"], p["lo"], p["hi"]), p["ell"], p["sf"], p["noise_value"],
                p["noise_grad"])
+    L, _, _ = pivoted_cholesky(op.kgrad_diag(), op.kgrad_row, RANK)
+    Pc = QRPreconditioner(L, op.noise)
     t_setup = time.perf_counter() - t0
-    rng = np.random.default_rng(0)
-    reps, t_mvm = 0, 0.0
-    while t_mvm < budget_s and reps < 200:
-        v = rng.normal(size=op.N)
+    k = 5
+    while True:
         t0 = time.perf_counter()
-        op.mvm(v)
-        t_mvm += time.perf_counter() - t0
-        reps += 1
-    per = t_mvm / reps
-    M = int(np.prod(p["m"]))
-    n, d = p["X"].shape
-    gbs = mvm_bytes(n, d, M, 1, 8) / per / 1e9
-    return {"value": gbs, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
-            "sample": f"{reps} FP64 oracle MVMs of the full terrain operator "
-                      f"({per * 1e3:.1f} ms each; setup {t_setup:.1f} s untimed)",
-            "ms_per_mvm": per * 1e3}
+        pcg(op.mvm, p["y"], Pc.solve, rtol=0.0, maxit=k)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 4 or k >= 4000:
+            break
+        k = int(k * max(2.0, min(8.0, budget_s / 4 / max(dt, 1e-3))))
+    per_it = dt / k
+    est = t_setup + per_it * iters_gpu
+    return {"value": est, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+            "sample": (f"oracle setup (operator, rank-{RANK} pivoted Cholesky, QR) timed whole "
+                       f"({t_setup:.1f} s); {k} oracle PCG iterations timed ({dt:.1f} s, "
+                       f"{per_it * 1e3:.1f} ms each), scaled to the GPU's {iters_gpu} iterations")}
 
 
 def run_reference(args, p):
     rank, ws, dist = dist_init()
     if rank != 0:
         return 0
-    cb = cpu_baseline(p, budget_s=max(2.0, 60.0 / max(args.steps + args.warmup, 1)))
-    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+    # the oracle's iteration count for this system is the GPU FP64 path's;
+    # without a GPU in this arm, use the count recorded in DESIGN.md's table
+    iters = args.ref_iters
+    steps = []
+    for _ in range(max(args.steps, 1)):
+        steps.append(cpu_baseline(p, iters, budget_s=max(4.0, 60.0 / (args.steps + args.warmup))))
+    v = statistics.median(s["value"] for s in steps)
+    cb = dict(steps[0])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": cb["ms_per_mvm"], "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": "flushed between steps"},
-            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
-            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+            "config": {"workload": workload_name(p["X"].shape[0]), "l2": "n/a (CPU)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -174,13 +192,21 @@ def run_reference(args, p):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--prec", default="fp64", choices=["fp64_tc", "fp64", "mixed_3xtf32"])
+    ap.add_argument("--compare", default="fp64_tc",
+                    help="comma-separated modes timed beside the headline mode (one step each, "
+                         "after one warm-up step, capped at 1.5x the headline iterations)")
+    ap.add_argument("--maxit", type=int, default=400000)
     ap.add_argument("--n", type=int, default=100_000)
+    ap.add_argument("--ref-iters", type=int, default=130000,
+                    help="reference arm: PCG iterations to scale the oracle's per-iteration time to")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    args.steps = max(args.steps, 1)
 
     from synth import workloads as W
     p = W.terrain2d(n=args.n)
@@ -195,121 +221,169 @@ def main():
     from paper_1810_12283_gb300 import DSKI, launch_count
 
     n, d = p["X"].shape
+    N = n * (d + 1)
     M = int(np.prod(p["m"]))
     X = torch.tensor(p["X"], device=dev)
-    ops = {prec: DSKI(X, p["m"], p["lo"], p["hi"], p["ell"], p["sf"], p["noise_value"],
-                      p["noise_grad"], prec=prec)
-           for prec in ("mixed_3xtf32", "fp64")}
-    N = ops["fp64"].N
+    y = torch.tensor(p["y"], device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    rng = torch.Generator(device=dev)
-    rng.manual_seed(1234 + rank)
     stream = torch.cuda.current_stream(dev)
 
-    def timed(op, steps, prof):
-        vs = [torch.randn(N, device=dev, dtype=op.dtype, generator=rng) for _ in range(4)]
-        out = torch.empty(N, device=dev, dtype=op.dtype)
-        for i in range(args.warmup):
-            op.mvm(vs[i % 4], out=out)
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(steps)]
-        l0 = launch_count()
+    def step(prec, X_, y_, prof=False, maxit=None):
+        op = DSKI(X_, p["m"], p["lo"], p["hi"], p["ell"], p["sf"], p["noise_value"],
+                  p["noise_grad"], prec=prec)
         if prof:
             op.profile_start()
-        for i in range(steps):
-            flush.fill_(i & 255)
-            ev[i][0].record(stream)
-            op.mvm(vs[i % 4], out=out)
-            ev[i][1].record(stream)
+        pc = op.pivchol(RANK)
+        try:
+            x, it, rr = op.solve(y_, pc, rtol=RTOL, maxit=maxit or args.maxit,
+                                 allow_not_converged=True)
+        except Exception as e:   # breakdown of a mode that cannot resolve the system
+            if prof:
+                op.profile_stop()
+            pc.close()
+            op.close()
+            raise e
+        st = op.profile_stop()[0] if prof else None
+        return op, pc, x, it[0], rr[0], st
+
+    def timed_steps(prec, warm, steps, prof, maxit=None):
+        for _ in range(warm):
+            op, pc, *_ = step(prec, X, y, maxit=maxit)
+            pc.close()
+            op.close()
         torch.cuda.synchronize()
-        stages = op.profile_stop()[0] if prof else None
-        launches = launch_count() - l0
-        ms = sum(a.elapsed_time(b) for a, b in ev)
         if dist is not None:
             dist.barrier()
-        return ms, launches, stages
+        ms, its, rrs, stages, launches = [], [], [], None, 0
+        for i in range(steps):
+            flush.fill_(i & 255)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0 = launch_count()
+            a.record(stream)
+            op, pc, x, it, rr, st = step(prec, X, y, prof=prof, maxit=maxit)
+            b.record(stream)
+            b.synchronize()
+            launches += launch_count() - l0
+            ms.append(a.elapsed_time(b))
+            its.append(it)
+            rrs.append(rr)
+            if st is not None:
+                stages = st
+            pc.close()
+            op.close()
+        if dist is not None:
+            dist.barrier()
+        return ms, its, rrs, stages, launches
 
-    res = {}
+    def mvm_rate(prec, reps=50):
+        op = DSKI(X, p["m"], p["lo"], p["hi"], p["ell"], p["sf"], p["noise_value"],
+                  p["noise_grad"], prec=prec)
+        v = torch.randn(N, device=dev, dtype=op.dtype)
+        out = torch.empty_like(v)
+        for _ in range(5):
+            op.mvm(v, out=out)
+        torch.cuda.synchronize()
+        op.profile_start()
+        tot = 0.0
+        for i in range(reps):
+            flush.fill_(i & 255)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            op.mvm(v, out=out)
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        st = op.profile_stop()[0]
+        op.close()
+        per = tot / reps
+        elem = 8 if prec in ("fp64", "fp64_tc") else 4
+        return {"ms_per_mvm": per, "gbs": mvm_bytes(n, d, M, 1, elem) / (per / 1e3) / 1e9,
+                "stages_us": {k: round(1e3 * v[0] / reps, 2) for k, v in st.items() if v[1]}}
+
     with ClockSampler(local) as clk:
-        for prec, op in ops.items():
-            res[prec] = timed(op, args.steps, prof=True)
+        ms, its, rrs, stages, launches = timed_steps(args.prec, args.warmup, args.steps, True)
     clocks = clk.summary()
+    compare = {}
+    for mode in [m for m in args.compare.split(",") if m and m != args.prec]:
+        try:
+            msc, itc, rrc, stc, _ = timed_steps(mode, 1, 1, True, maxit=int(1.5 * its[-1]) + 100)
+            compare[mode] = {"s_per_step": msc[-1] / 1e3, "iters": itc[-1], "relres": rrc[-1],
+                             "reached_rtol": rrc[-1] <= RTOL,
+                             "s_per_iter": msc[-1] / 1e3 / max(itc[-1], 1),
+                             "stages_ms": {k: round(v[0], 1) for k, v in stc.items() if v[1]}}
+        except Exception as e:   # noqa: BLE001 -- reported, not fatal
+            compare[mode] = {"error": str(e)}
+    mvm = {prec: mvm_rate(prec) for prec in ("fp64", "fp64_tc", "mixed_3xtf32")}
 
-    # end to end through the public call with pinned host buffers
-    op = ops["mixed_3xtf32"]
-    hv = torch.randn(N, dtype=torch.float32).pin_memory()
-    ho = torch.empty(N, dtype=torch.float32).pin_memory()
-    dv = torch.empty(N, device=dev, dtype=torch.float32)
-    for _ in range(args.warmup):
-        dv.copy_(hv, non_blocking=True)
-        ho.copy_(op.mvm(dv), non_blocking=True)
-    torch.cuda.synchronize()
-    e_ms = 0.0
-    for i in range(args.steps):
-        flush.fill_(i & 255)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        dv.copy_(hv, non_blocking=True)
-        ho.copy_(op.mvm(dv), non_blocking=True)
-        b.record(stream)
-        b.synchronize()
-        e_ms += a.elapsed_time(b)
+    # end to end through the public calls with host buffers
+    Xh = torch.tensor(p["X"]).pin_memory()
+    yh = torch.tensor(p["y"]).pin_memory()
+    xh = torch.empty(N, dtype=torch.float64).pin_memory()
+    flush.fill_(7)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    Xd = Xh.to(dev, non_blocking=True)
+    yd = yh.to(dev, non_blocking=True)
+    op, pc, x, it_e, rr_e, _ = step(args.prec, Xd, yd)
+    xh.copy_(x, non_blocking=True)
+    b.record(stream)
+    b.synchronize()
+    e2e_s = a.elapsed_time(b) / 1e3
+    pc.close()
+    op.close()
 
-    ms_mixed = reduce_max(dist, res["mixed_3xtf32"][0], dev)
-    ms_fp64 = reduce_max(dist, res["fp64"][0], dev)
-    e_ms = reduce_max(dist, e_ms, dev)
-    by_mixed = mvm_bytes(n, d, M, 1, 4)
-    by_fp64 = mvm_bytes(n, d, M, 1, 8)
-    value = ws * by_mixed * args.steps / (ms_mixed / 1e3) / 1e9
-    e2e = ws * by_mixed * args.steps / (e_ms / 1e3) / 1e9
+    t_step = reduce_max(dist, statistics.median(ms), dev) / 1e3
+    e2e_s = reduce_max(dist, e2e_s, dev)
 
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    hbm = peaks.get("hbm_gbs")
-    peak_note = "measured" if hbm else "fallback"
-    hbm = hbm or 6800.0
-    st = res["mixed_3xtf32"][2]
-    # dominant kernel of the mixed MVM
-    dom = max(("scatter", "gather", "kron"), key=lambda k: st[k][0])
-    per_launch_ms = st[dom][0] / max(st[dom][1], 1)
-    if dom == "scatter":
-        algo = scatter_bytes(n, d, M, 1, 4)
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    hbm_src = "measured" if peaks.get("hbm_gbs") else "fallback"
+    it_last = its[-1]
+    # dominant stage of the fast step and its roofline (per launch of the stage)
+    st = {k: v for k, v in stages.items() if v[1]}
+    dom = max(st, key=lambda k: st[k][0])
+    per_launch_s = st[dom][0] / 1e3 / st[dom][1]
+    if dom == "precond":
+        applies = it_last + 1
+        algo = precond_bytes(N, RANK, 1) / (st[dom][1] / applies)   # per launch of the stage
+    elif dom == "scatter":
+        algo = N * 8 + M * 8 + n * (4 + 64 * d)
     elif dom == "gather":
-        algo = gather_bytes(n, d, M, 1, 4)
+        algo = M * 8 + 2 * N * 8 + n * (4 + 64 * d)
+    elif dom == "kron":
+        algo = 2 * M * 8
     else:
-        algo = 2 * M * 4 * d   # each mode product reads and writes the grid
-    achieved = algo / (per_launch_ms / 1e3) / 1e9
+        algo = 4 * N * 8
+    achieved = algo / per_launch_s / 1e9
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_mixed / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "l2": "flushed between steps (256 MiB write)",
+        "metric": METRIC, "value": t_step, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(n), "mode": args.prec,
+                   "l2": "flushed before each timed step (256 MiB write)",
                    "parallelism": "replicas" if ws > 1 else "single"},
-        "fp64": {"ms_per_mvm": ms_fp64 / args.steps,
-                 "gbs": ws * by_fp64 * args.steps / (ms_fp64 / 1e3) / 1e9,
-                 "stages_ms": {k: v[0] / args.steps for k, v in res["fp64"][2].items()}},
-        "stages_ms_mixed": {k: v[0] / args.steps for k, v in st.items()},
+        "solve": {"iters": its, "relres": rrs, "s_per_iter": t_step / it_last,
+                  "reached_rtol": all(r <= RTOL for r in rrs)},
+        "compare": compare,
+        "stages_ms": {k: round(v[0], 1) for k, v in st.items()},
+        "stage_launches": {k: v[1] for k, v in st.items()},
+        "mvm": mvm,
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm,
-                     "peak_source": peak_note, "unit": "GB/s", "frac": achieved / hbm,
+                     "peak_source": hbm_src, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": None, "algo_bytes_per_launch": algo},
-        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": N * 4,
-                "d2h_bytes_per_step": N * 4},
-        "gpu_launches": res["mixed_3xtf32"][1],
+        "e2e": {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": (n * d + N) * 8,
+                "d2h_bytes_per_step": N * 8, "iters": it_e, "relres": rr_e},
+        "gpu_launches": launches // args.steps,
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(p)
-        line["cpu_baseline"].pop("ms_per_mvm", None)
+        line["cpu_baseline"] = cpu_baseline(p, it_last)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    for op in ops.values():
-        op.close()
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()

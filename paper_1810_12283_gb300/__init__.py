@@ -84,6 +84,7 @@ class DSKI:
         self.device = X.device
         self.stream = stream
         ng = noise_value if noise_grad is None else noise_grad
+        self.noise_ratio = float(ng) / float(noise_value)
         self._m = (C.c_int * d)(*[int(v) for v in grid_m])
         self._lo = (C.c_double * d)(*[float(v) for v in grid_lo])
         self._hi = (C.c_double * d)(*[float(v) for v in grid_hi])

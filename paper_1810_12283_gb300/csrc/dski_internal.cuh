@@ -102,11 +102,15 @@ struct dski_handle_ {
   dski::DevBuf dK64[DSKI_MAXD];
   // FP64_TC mode: six BF16 digit planes of K_k (6 x m x m) and row exponents
   dski::DevBuf Kdig[DSKI_MAXD], Kexp[DSKI_MAXD];
+  // FP64_TC: digit planes and row exponents of the grid operand (workspace)
+  dski::DevBuf ozB, ozE;
+  // FP64 scatter: per-point sum-factorised coefficients (workspace)
+  dski::DevBuf scat_ab;
   // workspace
   dski::DevBuf gridA, gridB, vin, vout, scratch;
   // solver workspace: reduction partials, last-block tickets (zeroed at
   // allocation), per-column scalar state and solver vectors
-  dski::DevBuf s_part, s_tnpart, s_ticket, s_state, s_vec[10];
+  dski::DevBuf s_part, s_tnpart, s_ticket, s_state, s_vec[12];
   // device error word (int): set by kernels whose bounded waits ran out
   dski::DevBuf dev_err;
   // stage timers (NULL unless profiling is on)
@@ -127,6 +131,10 @@ int permute_out(dski_handle h, const void* v_int, void* v_user, int s, bool f64,
 // grid-only pieces used by the adjoint: g = B^T v, and the Kronecker product
 // with one factor optionally replaced by dK_k/dlog l_k (which = k) or none (which = -1).
 int scatter_internal(dski_handle h, const void* vin, void* g, int s, bool prec64);
+// as scatter_internal with the sum-factorised coefficients in caller memory
+// `ws` (scatter_ws_bytes bytes; NULL = the handle's workspace)
+int scatter_internal_ws(dski_handle h, const void* vin, void* g, int s, bool prec64, void* ws);
+size_t scatter_ws_bytes(dski_handle h, int s, bool prec64);
 int kron_internal(dski_handle h, void* g, void* tmp, int s, bool prec64, int dfactor,
                   const void* dK, void** result);
 
@@ -137,7 +145,9 @@ int gather_internal(dski_handle h, const void* grid, const void* vin, void* vout
 // tensor-core mode product (kron_tc.cu): TF32 (three = false) or 3xTF32
 int mode_tc_tf32(dski_handle h, const float* X, const float* Khi, const float* Klo, float* Y,
                  int m, long long R, int s, float scale, bool three);
-// FP64_TC mode products (kron_tc.cu): digits of a factor, and one mode product
+// FP64_TC mode products (kron_tc.cu): digits of a factor, and one mode product;
+// a factor's digit planes take kOzDigits x m x m BF16 values
+constexpr int kOzDigits = 7;
 int oz_slice_factor(dski_handle h, const double* K, int m, uint16_t* Ad, int* fA);
 int mode_tc_oz(dski_handle h, const double* X, const uint16_t* Ad, const int* fA, double* Y,
                int m, long long R, int s, double scale);

@@ -333,7 +333,7 @@ int build_factors(dski_handle h) {
     count_launches(1);
     DSKI_LAUNCHED();
     if (h->prec == DSKI_FP64_TC) {
-      if (h->Kdig[k].ensure(6 * mm * 2) || h->Kexp[k].ensure((size_t)m * 4))
+      if (h->Kdig[k].ensure((size_t)kOzDigits * mm * 2) || h->Kexp[k].ensure((size_t)m * 4))
         return set_error(DSKI_ERR_ALLOC, "device allocation failed for factor digits");
       DSKI_TRY(oz_slice_factor(h, h->K64[k].as<double>(), m, h->Kdig[k].as<uint16_t>(),
                                h->Kexp[k].as<int>()));

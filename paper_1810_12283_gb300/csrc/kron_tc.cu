@@ -7,7 +7,7 @@
 // X_q viewed as R x m with the contracted mode contiguous; the output puts the
 // contracted mode first (one step of the cyclic mode rotation).  As a GEMM,
 // D (M = j, N = r) = A (j x i, K-major) . B (r x i, K-major) -- both operands
-// K-major, accumulator 128 x 64 FP32 in TMEM.
+// K-major, accumulator 128 x 32 FP32 in TMEM.
 //
 // Precision: TF32 operands (kind::tf32).  MIXED_3XTF32 splits both operands
 // into hi = rna_tf32(x) and lo = rna_tf32(x - hi) and accumulates
@@ -26,10 +26,10 @@ namespace dski {
 namespace {
 
 constexpr int TC_M = 128;
-constexpr int TC_N = 64;
+constexpr int TC_N = 32;
 constexpr int TC_KC = 32;                       // TF32 elements per 128-byte row
 constexpr int A_BYTES = TC_M * 128;             // 16 KB
-constexpr int B_BYTES = TC_N * 128;             // 8 KB
+constexpr int B_BYTES = TC_N * 128;             // 4 KB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int TC_SMEM = 2 * STAGE_BYTES + 1024 + 64;
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
@@ -97,13 +97,16 @@ __global__ void __launch_bounds__(128) k_mode_tc_tf32(const float* __restrict__ 
         if (NMMA > 1) *(float4*)(sAl + tc::sw128_off(tid, c)) = l4;
       }
     }
-    // B: row tid / 2 of the tile (r = r0 + row), half the K chunk each
+    // B: TPR threads per row of the tile (r = r0 + row), 8 / TPR chunks each
     {
-      const int row = tid >> 1;
+      constexpr int TPR = 128 / TC_N;
+      constexpr int CPT = 8 / TPR;
+      static_assert(TPR * TC_N == 128 && CPT * TPR == 8, "B tile split");
+      const int row = tid / TPR;
       const long long r = r0 + row;
-      const int c0 = (tid & 1) * 4;
+      const int c0 = (tid % TPR) * CPT;
 #pragma unroll
-      for (int c = c0; c < c0 + 4; ++c) {
+      for (int c = c0; c < c0 + CPT; ++c) {
         float4 h4, l4;
         float* hv = &h4.x;
         float* lv = &l4.x;
@@ -202,33 +205,61 @@ namespace {
 //
 // Both operands are split into S = 6 signed 7-bit digits relative to a
 // per-row power of two (Ozaki-style splitting): for a row with max |x| <
-// 2^e, x = 2^e sum_b d_b 2^(-6 - 7 b), d_b integers in [-64, 64] (exact
-// in BF16).  A product of digits is at most 2^12 in magnitude and a sum of
+// 2^e, x = 2^e sum_b d_b 2^(-6 - 7 b) up to rounding at 2^(e - 41), d_b
+// integers in [-64, 64] (exact in BF16), extracted with integer arithmetic.  A product of digits is at most 2^12 in magnitude and a sum of
 // m <= 256 of them, over the <= 6 digit pairs (a, b) of one level a + b, stays
 // below 2^23, so every level accumulates EXACTLY in the FP32 TMEM
 // accumulator.  Levels 0..S-1 are kept (one TMEM accumulator each) and
 // combined in FP64:
 //   Y[j][r] = 2^(fA_j + eB_r - 12) sum_l 2^(-7 l) T_l[j][r],
-// which drops only the digit pairs of weight < 2^(-7 S) -- a relative error
-// of about 2^-42 of |K| |X|, below what the solver needs (the FP32 product
-// misses by 2^-24, which is 26x the noise variance on the terrain grid).
-// K's digits are made once per factor; X's digits are made in the kernel.
-constexpr int OZ_S = 6;
+// (summed exactly in int64 before one conversion to FP64), which drops only
+// the digit pairs of weight < 2^(-7 S) -- a relative error
+// of about 2^-49 of |K| |X|, the size of FP64 rounding in the 256-term sums
+// (the FP32 product misses by 2^-24, 26x the noise variance on the terrain
+// grid).
+// K's digits are made once per factor; X's digits by a row-parallel kernel
+// before each mode product.
+constexpr int OZ_S = kOzDigits;                  // digits per operand (7)
+constexpr int OZ_P = 6 + 7 * (OZ_S - 1);         // fixed-point bits: |V| < 2^OZ_P
 constexpr int OZ_M = 128, OZ_N = 32, OZ_KC = 64;   // 64 BF16 = one 128-byte row
 constexpr int OZ_A_BYTES = OZ_M * 128;           // 16 KB per digit
 constexpr int OZ_B_BYTES = OZ_N * 128;           // 4 KB per digit
 constexpr int OZ_SMEM = OZ_S * (OZ_A_BYTES + OZ_B_BYTES) + 1024 + 256;
 constexpr int OZ_TMEM_COLS = 256;                // >= OZ_S * OZ_N, power of two
+static_assert(OZ_S * OZ_N <= OZ_TMEM_COLS, "TMEM columns");
+// exactness of one level: at most OZ_S digit pairs of 64 x 64, over K <= 256 terms
+static_assert((long long)OZ_S * 256 * 64 * 64 < (1LL << 24), "FP32 level sums must stay exact");
 
-__device__ __forceinline__ void digits6(double x, float (&d)[OZ_S]) {
-  // x in (-1, 1): d_0 = rint(x 2^6), then rint(remainder 2^7) ...
-  double t = x * 64.0;
+// Biased exponent field of |x| (0 for zero and subnormals).
+__device__ __forceinline__ int exp_field(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
+// V = round(x 2^(OZ_P - e)) as an integer (|V| < 2^OZ_P when |x| < 2^e), from
+// the bit pattern alone: GB300's FP64 units are ~60x slower than its
+// integer and FP32 units, so the splitting avoids FP64 arithmetic.
+__device__ __forceinline__ long long fixedP(double x, int e) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((u >> 52) & 0x7FF);
+  if (E == 0) return 0;   // zero or subnormal: below the last digit
+  const unsigned long long mant = (u & ((1ULL << 52) - 1)) | (1ULL << 52);
+  const int sh = 1075 - OZ_P + e - E;   // >= 53 - OZ_P because |x| < 2^e
+  long long v = 0;
+  if (sh < 62) v = (long long)((mant + (1ULL << (sh - 1))) >> sh);
+  return (u >> 63) ? -v : v;
+}
+
+// OZ_S signed 7-bit digits of V (weights 2^(7 (S-1)), ..., 2^7, 2^0), each
+// in [-64, 64]: round-to-nearest at every step leaves |remainder| <= 2^(k-1).
+__device__ __forceinline__ void digitsS(long long V, float (&d)[OZ_S]) {
 #pragma unroll
-  for (int b = 0; b < OZ_S; ++b) {
-    const double r = rint(t);
-    d[b] = (float)r;
-    t = (t - r) * 128.0;
+  for (int b = 0; b < OZ_S - 1; ++b) {
+    const int k = 7 * (OZ_S - 1 - b);
+    const long long q = (V + (1LL << (k - 1))) >> k;
+    d[b] = (float)(int)q;
+    V -= q << k;
   }
+  d[OZ_S - 1] = (float)(int)V;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -243,21 +274,47 @@ __global__ void k_oz_slice_factor(const double* __restrict__ K, int m,
                                   uint16_t* __restrict__ Ad, int* __restrict__ fA) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= m) return;
-  double mx = 0.0;
-  for (int i = 0; i < m; ++i) mx = fmax(mx, fabs(K[(long long)j * m + i]));
-  int e = 0;
-  if (mx > 0.0) frexp(mx, &e);   // mx = f 2^e, f in [0.5, 1)
+  int E = 0;
+  for (int i = 0; i < m; ++i) E = max(E, exp_field(K[(long long)j * m + i]));
+  const int e = E - 1022;   // max |K[j][:]| < 2^e
   fA[j] = e;
   for (int i = 0; i < m; ++i) {
     float d[OZ_S];
-    digits6(ldexp(K[(long long)j * m + i], -e), d);
+    digitsS(fixedP(K[(long long)j * m + i], e), d);
 #pragma unroll
     for (int b = 0; b < OZ_S; ++b)
       Ad[((long long)b * m + j) * m + i] = (uint16_t)(__float_as_uint(d[b]) >> 16);
   }
 }
 
-__global__ void __launch_bounds__(128) k_mode_tc_oz(const double* __restrict__ X,
+// Digits of the rows of X (s grid columns, each R x m): Bd[q][b][r][i] (BF16
+// bits) and eB[q][r] with max_i |X_q[r][i]| < 2^eB.  One warp per row.
+__global__ void __launch_bounds__(256) k_oz_slice_rows(const double* __restrict__ X, long long R,
+                                                       int m, long long rows,
+                                                       uint16_t* __restrict__ Bd,
+                                                       int* __restrict__ eB) {
+  const long long gr = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // q R + r
+  const int lane = threadIdx.x & 31;
+  if (gr >= rows) return;   // whole warp
+  const long long q = gr / R, r = gr % R;
+  const double* xr = X + gr * m;
+  int E = 0;
+  for (int i = lane; i < m; i += 32) E = max(E, exp_field(xr[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+  const int e = E - 1022;
+  if (lane == 0) eB[gr] = e;
+  for (int i = lane; i < m; i += 32) {
+    float d[OZ_S];
+    digitsS(fixedP(xr[i], e), d);
+#pragma unroll
+    for (int b = 0; b < OZ_S; ++b)
+      Bd[((q * OZ_S + b) * R + r) * m + i] = (uint16_t)(__float_as_uint(d[b]) >> 16);
+  }
+}
+
+__global__ void __launch_bounds__(128) k_mode_tc_oz(const uint16_t* __restrict__ Bd,
+                                                    const int* __restrict__ eBg,
                                                     const uint16_t* __restrict__ Ad,
                                                     const int* __restrict__ fA,
                                                     double* __restrict__ Y, int m, long long R,
@@ -272,30 +329,16 @@ __global__ void __launch_bounds__(128) k_mode_tc_oz(const double* __restrict__ X
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int j0 = blockIdx.x * OZ_M;
   const long long r0 = (long long)blockIdx.y * OZ_N;
-  const long long qoff = (long long)blockIdx.z * R * m;
-  const double* Xq = X + qoff;
-  double* Yq = Y + qoff;
+  const long long q = blockIdx.z;
+  double* Yq = Y + q * R * m;
+  const uint16_t* Bq = Bd + q * OZ_S * R * m;
 
   if (warp == 0) tc::tmem_alloc(tslot, OZ_TMEM_COLS);
   if (tid == 0) {
     tc::mbar_init(&mbar[0], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // row exponents of the B rows: 4 threads per row
-  {
-    const int row = tid >> 2, part = tid & 3;
-    const long long r = r0 + row;
-    double mx = 0.0;
-    if (r < R)
-      for (int i = part; i < m; i += 4) mx = fmax(mx, fabs(Xq[r * m + i]));
-    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-    if (part == 0) {
-      int e = 0;
-      if (mx > 0.0) frexp(mx, &e);
-      eB[row] = e;
-    }
-  }
+  if (tid < OZ_N) eB[tid] = (r0 + tid < R) ? eBg[q * R + r0 + tid] : 0;
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
@@ -327,30 +370,21 @@ __global__ void __launch_bounds__(128) k_mode_tc_oz(const double* __restrict__ X
         }
       }
     }
-    // B digits: row tid / 4, 16 elements (2 chunks) per thread
+    // B digits: row tid / 4 of the tile, 2 chunks of 8 BF16 per digit
     {
       const int row = tid >> 2, part = tid & 3;
       const long long r = r0 + row;
-      const double sc = ldexp(1.0, -eB[row]);
 #pragma unroll
-      for (int cc = 0; cc < 2; ++cc) {
-        const int c = part * 2 + cc;
-        uint32_t w[OZ_S][4];
+      for (int b = 0; b < OZ_S; ++b) {
+        unsigned char* dst = sB + b * OZ_B_BYTES;
 #pragma unroll
-        for (int e2 = 0; e2 < 4; ++e2) {
-          float d0[OZ_S], d1[OZ_S];
-          const int i = i0 + 8 * c + 2 * e2;
-          const double x0 = (r < R && i < m) ? Xq[r * m + i] * sc : 0.0;
-          const double x1 = (r < R && i + 1 < m) ? Xq[r * m + i + 1] * sc : 0.0;
-          digits6(x0, d0);
-          digits6(x1, d1);
-#pragma unroll
-          for (int b = 0; b < OZ_S; ++b) w[b][e2] = pack_bf16(d0[b], d1[b]);
+        for (int cc = 0; cc < 2; ++cc) {
+          const int c = part * 2 + cc;
+          const int i = i0 + 8 * c;
+          uint4 v = make_uint4(0, 0, 0, 0);
+          if (r < R && i < m) v = *(const uint4*)(Bq + ((long long)b * R + r) * m + i);
+          *(uint4*)(dst + tc::sw128_off(row, c)) = v;
         }
-#pragma unroll
-        for (int b = 0; b < OZ_S; ++b)
-          *(uint4*)(sB + b * OZ_B_BYTES + tc::sw128_off(row, c)) =
-              make_uint4(w[b][0], w[b][1], w[b][2], w[b][3]);
       }
     }
     tc::fence_proxy_async();
@@ -382,22 +416,29 @@ __global__ void __launch_bounds__(128) k_mode_tc_oz(const double* __restrict__ X
     const int fj = j < m ? fA[j] : 0;
 #pragma unroll
     for (int c16 = 0; c16 < OZ_N / 16; ++c16) {
-      double acc[16];
+      // levels are exact integers below 2^24 (level l has <= l + 1 digit
+      // pairs): combine them exactly in int64, acc = sum_l T_l 2^(7 (S-1-l))
+      // (< 2^63 because |T_0| <= 2^20)
+      long long acc[16];
 #pragma unroll
-      for (int e = 0; e < 16; ++e) acc[e] = 0.0;
+      for (int e = 0; e < 16; ++e) acc[e] = 0;
 #pragma unroll
-      for (int l = OZ_S - 1; l >= 0; --l) {
+      for (int l = 0; l < OZ_S; ++l) {
         uint32_t v[16];
         tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + l * OZ_N + c16 * 16, v);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) acc[e] = fma(acc[e], 1.0 / 128.0, (double)__uint_as_float(v[e]));
+        for (int e = 0; e < 16; ++e)
+          acc[e] = acc[e] * 128 + (long long)__float2int_rz(__uint_as_float(v[e]));
       }
       if (j < m) {
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
           const int rl = c16 * 16 + e;
           const long long r = r0 + rl;
-          if (r < R) Yq[(long long)j * R + r] = scale * ldexp(acc[e], fj + eB[rl] - 12);
+          // Y = scale acc 2^(fA + eB - 2 P + 7 (S - 1)); power of two from its bits
+          const int ex = fj + eB[rl] - 2 * OZ_P + 7 * (OZ_S - 1);
+          const double p2 = ex > -1023 ? __longlong_as_double((long long)(ex + 1023) << 52) : 0.0;
+          if (r < R) Yq[(long long)j * R + r] = scale * ((double)acc[e] * p2);
         }
       }
     }
@@ -422,6 +463,15 @@ int mode_tc_oz(dski_handle h, const double* X, const uint16_t* Ad, const int* fA
                int m, long long R, int s, double scale) {
   if (m % 8 != 0 || m > 256)
     return set_error(DSKI_ERR_ARG, "FP64_TC mode products need m_k %% 8 == 0 and m_k <= 256 (got %d)", m);
+  const long long rows = (long long)s * R;
+  if (h->ozB.ensure((size_t)rows * m * OZ_S * 2) || h->ozE.ensure((size_t)rows * 4))
+    return set_error(DSKI_ERR_ALLOC, "FP64_TC digit workspace allocation failed");
+  {
+    StageScope sc(h, ST_KRON, h->stream);
+    k_oz_slice_rows<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, h->stream>>>(
+        X, R, m, rows, h->ozB.as<uint16_t>(), h->ozE.as<int>());
+  }
+  DSKI_LAUNCHED();
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_mode_tc_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
@@ -429,7 +479,8 @@ int mode_tc_oz(dski_handle h, const double* X, const uint16_t* Ad, const int* fA
   }
   dim3 grd((unsigned)((m + OZ_M - 1) / OZ_M), (unsigned)((R + OZ_N - 1) / OZ_N), (unsigned)s);
   StageScope sc(h, ST_KRON, h->stream);
-  k_mode_tc_oz<<<grd, 128, OZ_SMEM, h->stream>>>(X, Ad, fA, Y, m, R, scale, h->dev_err.as<int>());
+  k_mode_tc_oz<<<grd, 128, OZ_SMEM, h->stream>>>(h->ozB.as<uint16_t>(), h->ozE.as<int>(), Ad, fA, Y,
+                                                 m, R, scale, h->dev_err.as<int>());
   DSKI_LAUNCHED();
   return DSKI_OK;
 }

@@ -127,6 +127,135 @@ __global__ void __launch_bounds__(256) k_gemv_t(const double* __restrict__ A, in
   }
 }
 
+// As k_gemv_t with A = Qh + Ql held as two FP32 arrays and every product and
+// sum taken in double-float arithmetic on the FP32 units; one FP64 value per
+// block and output at the end.
+template <int QMAX>
+__global__ void __launch_bounds__(256) k_df_gemv_t(const float* __restrict__ Qh,
+                                                   const float* __restrict__ Ql, int p,
+                                                   const double* __restrict__ B, int q,
+                                                   const double* __restrict__ w, long long N,
+                                                   double* __restrict__ part) {
+  __shared__ float red[2][8][GV_TG * QMAX];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long base = (long long)blockIdx.x * GV_ROWS;
+  float bh[GV_RPT][QMAX], bl[GV_RPT][QMAX];
+#pragma unroll
+  for (int k = 0; k < GV_RPT; ++k) {
+    const long long row = base + k * 256 + threadIdx.x;
+#pragma unroll
+    for (int u = 0; u < QMAX; ++u) {
+      double v = 0.0;
+      if (row < N && u < q) {
+        v = B[(long long)u * N + row];
+        if (w) v *= w[row];
+      }
+      split_d(v, bh[k][u], bl[k][u]);
+    }
+  }
+  for (int t0 = 0; t0 < p; t0 += GV_TG) {
+    float sh[GV_TG][QMAX], sl[GV_TG][QMAX];
+#pragma unroll
+    for (int tt = 0; tt < GV_TG; ++tt)
+#pragma unroll
+      for (int u = 0; u < QMAX; ++u) sh[tt][u] = sl[tt][u] = 0.f;
+#pragma unroll
+    for (int k = 0; k < GV_RPT; ++k) {
+      const long long row = base + k * 256 + threadIdx.x;
+      if (row < N) {
+#pragma unroll
+        for (int tt = 0; tt < GV_TG; ++tt) {
+          const bool in = t0 + tt < p;
+          const float qh = in ? Qh[(long long)(t0 + tt) * N + row] : 0.f;
+          const float ql = in ? Ql[(long long)(t0 + tt) * N + row] : 0.f;
+#pragma unroll
+          for (int u = 0; u < QMAX; ++u) df_fma(qh, ql, bh[k][u], bl[k][u], sh[tt][u], sl[tt][u]);
+        }
+      }
+    }
+    // warp tree in double-float, fixed order
+#pragma unroll
+    for (int tt = 0; tt < GV_TG; ++tt)
+#pragma unroll
+      for (int u = 0; u < QMAX; ++u) {
+        float a = sh[tt][u], b = sl[tt][u];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float oa = __shfl_xor_sync(0xffffffffu, a, o);
+          const float ob = __shfl_xor_sync(0xffffffffu, b, o);
+          df_add(a, b, oa, ob);
+        }
+        if (lane == 0) {
+          red[0][warp][tt * QMAX + u] = a;
+          red[1][warp][tt * QMAX + u] = b;
+        }
+      }
+    __syncthreads();
+    if (threadIdx.x < GV_TG * QMAX) {
+      const int tt = threadIdx.x / QMAX, u = threadIdx.x % QMAX;
+      float a = 0.f, b = 0.f;
+#pragma unroll
+      for (int wv = 0; wv < 8; ++wv) df_add(a, b, red[0][wv][threadIdx.x], red[1][wv][threadIdx.x]);
+      if (t0 + tt < p && u < q)
+        part[((long long)blockIdx.x * p + t0 + tt) * q + u] = (double)a + (double)b;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_qsplit(const double* __restrict__ Q, long long count, float* __restrict__ Qh,
+                         float* __restrict__ Ql) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    float h, l;
+    split_d(Q[i], h, l);
+    Qh[i] = h;
+    Ql[i] = l;
+  }
+}
+
+// C = A^T (w .* b) for ONE column (the solve's Q1^T y) in FP64: a block owns
+// GT_ROWS rows with w .* b staged in shared memory; warp w owns the outputs
+// t = w, w + 8, ...; for each, its lanes sweep the rows (coalesced, 8 loads in
+// flight) and a single warp reduction ends the output -- so the FP64
+// reduction work is ~1/16 of the FP64 FMAs (on GB300 FP64 adds are as slow
+// as FMAs).
+constexpr int GT_ROWS = 2048;
+__global__ void __launch_bounds__(256) k_gemv_t1(const double* __restrict__ A, int p,
+                                                 const double* __restrict__ b,
+                                                 const double* __restrict__ w, long long N,
+                                                 double* __restrict__ part) {
+  __shared__ double ys[GT_ROWS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long r0 = (long long)blockIdx.x * GT_ROWS;
+  const int nr = (int)min((long long)GT_ROWS, N - r0);
+  for (int i = threadIdx.x; i < GT_ROWS; i += 256) {
+    double v = 0.0;
+    if (i < nr) {
+      v = b[r0 + i];
+      if (w) v *= w[r0 + i];
+    }
+    ys[i] = v;
+  }
+  __syncthreads();
+  for (int t = warp; t < p; t += 8) {
+    const double* at = A + (long long)t * N + r0;
+    double acc = 0.0;
+    for (int i0 = 0; i0 < nr; i0 += 32 * 8) {
+      double a[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int i = i0 + k * 32 + lane;
+        a[k] = i < nr ? at[i] : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc = fma(a[k], ys[i0 + k * 32 + lane], acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) part[(long long)blockIdx.x * p + t] = acc;
+  }
+}
+
 // One warp per output: lane l adds chunks l, l + 32, ... then a fixed tree.
 __global__ void k_sum_chunks(const double* __restrict__ part, int nchunk, int pq,
                              double* __restrict__ out) {
@@ -203,6 +332,16 @@ __global__ void k_noise_diag(int n, int d, double nv, double ng, double* __restr
 int ts_tn(dski_handle h, const double* A, int p, const double* B, int q, const double* w,
           double* C_dev) {
   const long long N = h->N;
+  if (q == 1) {
+    const int nchunk = (int)((N + GT_ROWS - 1) / GT_ROWS);
+    double* part = wbuf(h->s_tnpart, (size_t)nchunk * p);
+    if (!part) return DSKI_ERR_ALLOC;
+    StageScope sc(h, ST_PRECOND, h->stream, 2);
+    k_gemv_t1<<<nchunk, 256, 0, h->stream>>>(A, p, B, w, N, part);
+    k_sum_chunks<<<(p + 7) / 8, 256, 0, h->stream>>>(part, nchunk, p, C_dev);
+    DSKI_LAUNCHED();
+    return DSKI_OK;
+  }
   if (q <= 4) {
     const int nchunk = (int)((N + GV_ROWS - 1) / GV_ROWS);
     double* part = wbuf(h->s_tnpart, (size_t)nchunk * p * q);
@@ -256,6 +395,54 @@ int ts_nn(dski_handle h, const double* X, double alpha, const double* xscale, do
   return DSKI_OK;
 }
 
+int df_gemv_t(dski_handle h, const float* Qh, const float* Ql, int p, const double* B, int q,
+              const double* w, double* C_dev) {
+  const long long N = h->N;
+  if (q > 4) return set_error(DSKI_ERR_ARG, "df_gemv_t: at most 4 columns per call");
+  const int nchunk = (int)((N + GV_ROWS - 1) / GV_ROWS);
+  double* part = wbuf(h->s_tnpart, (size_t)nchunk * p * q);
+  if (!part) return DSKI_ERR_ALLOC;
+  StageScope sc(h, ST_PRECOND, h->stream, 2);
+  if (q == 1)
+    k_df_gemv_t<1><<<nchunk, 256, 0, h->stream>>>(Qh, Ql, p, B, q, w, N, part);
+  else
+    k_df_gemv_t<4><<<nchunk, 256, 0, h->stream>>>(Qh, Ql, p, B, q, w, N, part);
+  k_sum_chunks<<<(p * q + 7) / 8, 256, 0, h->stream>>>(part, nchunk, p * q, C_dev);
+  DSKI_LAUNCHED();
+  return DSKI_OK;
+}
+
+int split_q1(dski_handle h, pivchol_handle pc) {
+  const size_t cnt = (size_t)pc->N * pc->rank;
+  if (pc->Qh.ensure(cnt * 4) || pc->Ql.ensure(cnt * 4))
+    return set_error(DSKI_ERR_ALLOC, "pivchol_build: allocation of the split Q1 failed");
+  StageScope sc(h, ST_PIVCHOL, h->stream);
+  k_qsplit<<<4 * h->sm_count, 256, 0, h->stream>>>(pc->Q1.as<double>(), (long long)cnt,
+                                                   pc->Qh.as<float>(), pc->Ql.as<float>());
+  DSKI_LAUNCHED();
+  pc->split = true;
+  return DSKI_OK;
+}
+
+// Z = D^-1/2 (Y - Q1 C), Y = D^-1/2 R, with the split Q1 (double-float).
+__global__ void k_df_z(const double* __restrict__ R, const float* __restrict__ Qh,
+                       const float* __restrict__ Ql, int rank, const double* __restrict__ C,
+                       int s, const double* __restrict__ dis, double* __restrict__ Z,
+                       long long N) {
+  extern __shared__ float Cs2[];   // rank hi, rank lo
+  const int c = blockIdx.y;
+  for (int t = threadIdx.x; t < rank; t += blockDim.x) split_d(C[(long long)t * s + c], Cs2[t], Cs2[rank + t]);
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    float sh = 0.f, sl = 0.f;
+    for (int t = 0; t < rank; ++t)
+      df_fma(Qh[(long long)t * N + i], Ql[(long long)t * N + i], Cs2[t], Cs2[rank + t], sh, sl);
+    const double y = dis[i] * R[(long long)c * N + i];
+    Z[(long long)c * N + i] = dis[i] * ((y - (double)sh) - (double)sl);
+  }
+}
+
 unsigned* tickets(dski_handle h, int count) {
   // Tickets are zeroed once at allocation; every user leaves them at zero.
   const size_t need = (size_t)count * sizeof(unsigned);
@@ -282,6 +469,23 @@ int col_dots(dski_handle h, const double* a, const double* b, int s, double* out
 }
 
 int precond_apply(dski_handle h, pivchol_handle pc, const double* R, double* Z, int s) {
+  if (pc->split && pc->rank > 0) {
+    double* C = wbuf(h->s_vec[5], (size_t)pc->rank * 4);
+    if (!C) return DSKI_ERR_ALLOC;
+    for (int c0 = 0; c0 < s; c0 += 4) {
+      const int q = std::min(4, s - c0);
+      const long long off = (long long)c0 * h->N;
+      DSKI_TRY(df_gemv_t(h, pc->Qh.as<float>(), pc->Ql.as<float>(), pc->rank, R + off, q,
+                         pc->dis.as<double>(), C));
+      StageScope sc(h, ST_PRECOND, h->stream);
+      const int nbx = (int)std::min<long long>((h->N + 255) / 256, 4LL * h->sm_count);
+      k_df_z<<<dim3(nbx, q), 256, 2 * pc->rank * sizeof(float), h->stream>>>(
+          R + off, pc->Qh.as<float>(), pc->Ql.as<float>(), pc->rank, C, q, pc->dis.as<double>(),
+          Z + off, h->N);
+      DSKI_LAUNCHED();
+    }
+    return DSKI_OK;
+  }
   if (pc->rank == 0) {
     // M = D: Z = D^-1 R
     return ts_nn(h, R, 1.0, pc->dis.as<double>(), 0.0, nullptr, 0, nullptr, s, Z,

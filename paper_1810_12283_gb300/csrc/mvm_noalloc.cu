@@ -15,7 +15,8 @@
 
 namespace {
 
-// Layout of one call: [vin | vout | gridA | gridB], each part padded to 256 bytes.
+// Layout of one call: [vin | vout | gridA | gridB | scatter coefficients],
+// each part padded to 256 bytes.
 constexpr size_t kScratchBytes = size_t(32) << 20;   // DSKI_NOALLOC_SCRATCH_BYTES
 static_assert(kScratchBytes == (size_t)DSKI_NOALLOC_SCRATCH_BYTES, "keep dski.h in sync");
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -56,15 +57,20 @@ extern "C" int dski_mvm_noalloc(dski_handle h, const void* v_dev, void* out_dev,
   clear_error();
   if (!h || !v_dev || !out_dev) return set_error(DSKI_ERR_ARG, "dski_mvm_noalloc: NULL argument");
   if (s < 1) return set_error(DSKI_ERR_ARG, "dski_mvm_noalloc: s must be >= 1");
+  if (h->prec == DSKI_FP64_TC)
+    return set_error(DSKI_ERR_ARG,
+                     "dski_mvm_noalloc: FP64_TC mode needs digit workspace; use FP64 or MIXED");
   const bool f64 = f64_vectors(h);
   const size_t es = f64 ? 8 : 4;
   const size_t vbytes = (size_t)h->N * s * es;
   const size_t gbytes = (size_t)h->M * s * es;
-  const size_t need = 2 * pad256(vbytes) + 2 * pad256(gbytes);
+  const size_t abytes = scatter_ws_bytes(h, s, f64);
+  const size_t need = 2 * pad256(vbytes) + 2 * pad256(gbytes) + pad256(abytes);
   if (need > kScratchBytes)
     return set_error(DSKI_ERR_ARG,
                      "dski_mvm_noalloc: needs %zu scratch bytes for s = %d, the fixed limit is %zu "
-                     "(2 N s + 2 M s elements); use dski_mvm or fewer columns",
+                     "(2 N s + 2 M s elements and the scatter coefficients); use dski_mvm or "
+                     "fewer columns",
                      need, s, kScratchBytes);
   const char* a = (const char*)v_dev;
   const char* b = (const char*)out_dev;
@@ -85,10 +91,11 @@ extern "C" int dski_mvm_noalloc(dski_handle h, const void* v_dev, void* out_dev,
   void* vout = p + pad256(vbytes);
   void* gA = p + 2 * pad256(vbytes);
   void* gB = p + 2 * pad256(vbytes) + pad256(gbytes);
+  void* ab = p + 2 * pad256(vbytes) + 2 * pad256(gbytes);
   // Every stage writes its whole output before the next reads it, so nothing
   // in the array has to start at zero.
   DSKI_TRY(permute_in(h, v_dev, vin, s, f64, h->stream));
-  DSKI_TRY(scatter_internal(h, vin, gA, s, f64));
+  DSKI_TRY(scatter_internal_ws(h, vin, gA, s, f64, abytes ? ab : nullptr));
   void* res = nullptr;
   DSKI_TRY(kron_internal(h, gA, gB, s, f64, -1, nullptr, &res));
   DSKI_TRY(gather_internal(h, res, vin, vout, s, f64));

@@ -50,6 +50,23 @@ __device__ __forceinline__ bool cg_last(unsigned* ticket) {
   return last_block(ticket, gridDim.x * gridDim.y);
 }
 
+// In the last block: tot[c] = sum over bx of part[(c nb + bx) stride + off]
+// for every column c < s.  The block's threads split the partials and a
+// fixed tree combines them (deterministic).  tot is shared, length >= s.
+__device__ void sum_columns(const double* part, int nb, int s, int stride, int off,
+                            double* tot, double* sh) {
+  for (int c = 0; c < s; ++c) {
+    double v = 0.0;
+    for (int bx = threadIdx.x; bx < nb; bx += blockDim.x)
+      v += part[((long long)c * nb + bx) * stride + off];
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) tot[c] = v;
+  }
+  __syncthreads();
+}
+
+constexpr int CG_MAXS = 264;   // >= 1 + the largest probe count (256)
+
 // r = b - q, y = dis .* r; ||b||^2 (first call) and ||r||^2; (re)activates
 // the columns whose residual misses the target.
 __global__ void __launch_bounds__(CG_THREADS) k_cg_init(
@@ -77,13 +94,12 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_init(
     part[2 * ((long long)c * gridDim.x + blockIdx.x) + 1] = sr;
   }
   if (cg_last(ticket)) {
+    __shared__ double totb[CG_MAXS], totr[CG_MAXS];
+    sum_columns(part, gridDim.x, cs.s, 2, 0, totb, sh);
+    sum_columns(part, gridDim.x, cs.s, 2, 1, totr, sh);
     int nact = 0;
     for (int cc = threadIdx.x; cc < cs.s; cc += blockDim.x) {
-      double tb = 0.0, tr = 0.0;
-      for (unsigned bx = 0; bx < gridDim.x; ++bx) {
-        tb += part[2 * ((long long)cc * gridDim.x + bx)];
-        tr += part[2 * ((long long)cc * gridDim.x + bx) + 1];
-      }
+      const double tb = totb[cc], tr = totr[cc];
       if (first) cs.bn2[cc] = tb;
       cs.rn2[cc] = tr;
       const double goal = fmax(tol2 * cs.bn2[cc], eta2 * tr);
@@ -100,15 +116,22 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_init(
 // z = dis .* (y - Q1 C) (preconditioned) or z = r (plain); r^T z.
 // init: p = z (and its float copy), r^T z becomes rz and rz0.
 // else: beta = (r^T z)_new / rz for active columns, recorded.
+// SPLIT: Q1 = Qh + Ql in FP32 halves, the product taken in double-float.
+template <bool SPLIT>
 __global__ void __launch_bounds__(CG_THREADS) k_cg_z(
     const double* __restrict__ r, const double* __restrict__ y, const double* __restrict__ Q1,
+    const float* __restrict__ Qh, const float* __restrict__ Ql,
     int rank, const double* __restrict__ C, const double* __restrict__ dis,
     double* __restrict__ z, double* __restrict__ p, float* __restrict__ p32, long long N,
     int init, ColState cs, double* part, unsigned* ticket) {
-  extern __shared__ double Cs[];   // rank values of column c
+  extern __shared__ double Cs[];   // rank values of column c (SPLIT: 2 rank floats)
   __shared__ double sh[32];
   const int c = blockIdx.y;
-  for (int t = threadIdx.x; t < rank; t += blockDim.x) Cs[t] = C[(long long)t * cs.s + c];
+  float* Cf = reinterpret_cast<float*>(Cs);
+  for (int t = threadIdx.x; t < rank; t += blockDim.x) {
+    if (SPLIT) split_d(C[(long long)t * cs.s + c], Cf[t], Cf[rank + t]);
+    else Cs[t] = C[(long long)t * cs.s + c];
+  }
   __syncthreads();
   double acc = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
@@ -117,8 +140,33 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_z(
     double zi;
     if (y) {
       double v = y[o];
-      if (Q1)
-        for (int t = 0; t < rank; ++t) v = fma(-Q1[(long long)t * N + i], Cs[t], v);
+      // Q1 columns in groups of 8: the group's loads are issued together so
+      // that each thread keeps 8 (16) independent loads in flight
+      if (SPLIT && rank) {
+        float s_h = 0.f, s_l = 0.f;
+        for (int t0 = 0; t0 < rank; t0 += 8) {
+          float qh[8], ql[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const bool in = t0 + k < rank;
+            qh[k] = in ? Qh[(long long)(t0 + k) * N + i] : 0.f;
+            ql[k] = in ? Ql[(long long)(t0 + k) * N + i] : 0.f;
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            if (t0 + k < rank) df_fma(qh[k], ql[k], Cf[t0 + k], Cf[rank + t0 + k], s_h, s_l);
+        }
+        v = (v - (double)s_h) - (double)s_l;
+      } else if (Q1) {
+        for (int t0 = 0; t0 < rank; t0 += 8) {
+          double q[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) q[k] = t0 + k < rank ? Q1[(long long)(t0 + k) * N + i] : 0.0;
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            if (t0 + k < rank) v = fma(-q[k], Cs[t0 + k], v);
+        }
+      }
       zi = dis[i] * v;
     } else {
       zi = r[o];
@@ -134,9 +182,10 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_z(
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) part[(long long)c * gridDim.x + blockIdx.x] = acc;
   if (cg_last(ticket)) {
+    __shared__ double tot[CG_MAXS];
+    sum_columns(part, gridDim.x, cs.s, 1, 0, tot, sh);
     for (int cc = threadIdx.x; cc < cs.s; cc += blockDim.x) {
-      double t = 0.0;
-      for (unsigned bx = 0; bx < gridDim.x; ++bx) t += part[(long long)cc * gridDim.x + bx];
+      const double t = tot[cc];
       if (init) {
         cs.rz[cc] = t;
         cs.beta[cc] = 0.0;
@@ -152,6 +201,16 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_z(
       }
     }
   }
+}
+
+// C[t][c] from per-group blocks: group g = c / 4 holds rank x q_g row-major.
+__global__ void k_regroup(const double* __restrict__ Cg, int rank, int s, double* __restrict__ C) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rank * s) return;
+  const int t = idx / s, c = idx % s;
+  const int g = c / 4, cc = c % 4;
+  const int q = min(4, s - 4 * g);
+  C[idx] = Cg[(long long)4 * g * rank + (long long)t * q + cc];
 }
 
 __global__ void __launch_bounds__(CG_THREADS) k_cg_p(const double* __restrict__ z,
@@ -188,11 +247,12 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_alpha(const double* __restric
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) part[(long long)c * gridDim.x + blockIdx.x] = acc;
   if (cg_last(ticket)) {
+    __shared__ double tot[CG_MAXS];
+    sum_columns(part, gridDim.x, cs.s, 1, 0, tot, sh);
     for (int cc = threadIdx.x; cc < cs.s; cc += blockDim.x) {
       double al = 0.0;
       if (cs.active[cc]) {
-        double t = 0.0;
-        for (unsigned bx = 0; bx < gridDim.x; ++bx) t += part[(long long)cc * gridDim.x + bx];
+        const double t = tot[cc];
         if (!(t > 0.0) || !isfinite(t) || !isfinite(cs.rz[cc])) {
           cs.bd[cc] = 1;
           cs.active[cc] = 0;
@@ -230,11 +290,12 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_update(
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) part[(long long)c * gridDim.x + blockIdx.x] = acc;
   if (cg_last(ticket)) {
+    __shared__ double tot[CG_MAXS];
+    sum_columns(part, gridDim.x, cs.s, 1, 0, tot, sh);
     int nact = 0;
     for (int cc = threadIdx.x; cc < cs.s; cc += blockDim.x) {
       if (cs.active[cc]) {
-        double t = 0.0;
-        for (unsigned bx = 0; bx < gridDim.x; ++bx) t += part[(long long)cc * gridDim.x + bx];
+        const double t = tot[cc];
         cs.rn2[cc] = t;
         cs.iters[cc] += 1;
         if (!(t > cs.target[cc])) cs.active[cc] = 0;
@@ -254,6 +315,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_update(
 int cg_run(dski_handle h, CgRun& run) {
   const long long N = h->N;
   const int s = run.s;
+  if (s < 1 || s > CG_MAXS) return set_error(DSKI_ERR_ARG, "cg_run: %d columns (max %d)", s, CG_MAXS);
   const bool mixed = !f64_vectors(h);
   const int rank = run.pc ? run.pc->rank : 0;
   cudaStream_t st = h->stream;
@@ -264,13 +326,17 @@ int cg_run(dski_handle h, CgRun& run) {
   double* Q = wbuf(h->s_vec[3], Ns);
   double* Y = run.pc ? wbuf(h->s_vec[4], Ns) : nullptr;
   double* C = rank ? wbuf(h->s_vec[5], (size_t)rank * s) : nullptr;
+  // split-preconditioner results per group of <= 4 columns (c0 rank x q blocks)
+  double* Cg = rank ? wbuf(h->s_vec[10], (size_t)rank * (s + 4)) : nullptr;
   float* P32 = mixed ? (float*)wbuf(h->s_vec[6], (Ns + 1) / 2) : nullptr;
   float* Q32 = mixed ? (float*)wbuf(h->s_vec[7], (Ns + 1) / 2) : nullptr;
   const int depth = run.depth;
   const size_t nstate = 8 * (size_t)s + 2 * (size_t)depth * s + 8;
   double* stbuf = wbuf(h->s_state, nstate + 6 * (size_t)s + 8);
-  const int nbx = (int)std::min<long long>((N + CG_THREADS * 4 - 1) / (CG_THREADS * 4),
-                                           std::max(1, 4 * h->sm_count / std::max(1, s)));
+  // one row per thread where the grid allows (memory-level parallelism),
+  // at most 16 blocks per SM over all columns
+  const int nbx = (int)std::min<long long>((N + CG_THREADS - 1) / CG_THREADS,
+                                           std::max(1, 16 * h->sm_count / std::max(1, s)));
   double* part = wbuf(h->s_part, (size_t)nbx * s * 2 + 16);
   unsigned* tk = tickets(h, 1);
   if (!R || !Z || !P || !Q || (run.pc && !Y) || (rank && !C) || (mixed && (!P32 || !Q32)) ||
@@ -302,11 +368,28 @@ int cg_run(dski_handle h, CgRun& run) {
   const dim3 grd(nbx, s);
   const size_t zsmem = (size_t)std::max(rank, 1) * sizeof(double);
 
+  const bool split = run.pc && run.pc->split;
   auto precond_z = [&](int init) -> int {
-    if (rank) DSKI_TRY(ts_tn(h, run.pc->Q1.as<double>(), rank, Y, s, nullptr, C));
+    if (rank && split) {
+      for (int c0 = 0; c0 < s; c0 += 4)
+        DSKI_TRY(df_gemv_t(h, run.pc->Qh.as<float>(), run.pc->Ql.as<float>(), rank,
+                           Y + (size_t)c0 * N, std::min(4, s - c0), nullptr, Cg + (size_t)c0 * rank));
+      // gather the per-group results into C[t][c] (t-major, s columns)
+      StageScope sc(h, ST_PRECOND, st);
+      k_regroup<<<(rank * s + 255) / 256, 256, 0, st>>>(Cg, rank, s, C);
+      DSKI_LAUNCHED();
+    } else if (rank) {
+      DSKI_TRY(ts_tn(h, run.pc->Q1.as<double>(), rank, Y, s, nullptr, C));
+    }
     StageScope sc(h, ST_PRECOND, st);
-    k_cg_z<<<grd, CG_THREADS, zsmem, st>>>(R, Y, rank ? run.pc->Q1.as<double>() : nullptr, rank,
-                                            C, dis, Z, P, P32, N, init, cs, part, tk);
+    if (split)
+      k_cg_z<true><<<grd, CG_THREADS, zsmem, st>>>(R, Y, nullptr, run.pc->Qh.as<float>(),
+                                                  run.pc->Ql.as<float>(), rank, C, dis, Z, P, P32,
+                                                  N, init, cs, part, tk);
+    else
+      k_cg_z<false><<<grd, CG_THREADS, zsmem, st>>>(R, Y, rank ? run.pc->Q1.as<double>() : nullptr,
+                                                   nullptr, nullptr, rank, C, dis, Z, P, P32, N,
+                                                   init, cs, part, tk);
     DSKI_LAUNCHED();
     return DSKI_OK;
   };

@@ -351,6 +351,8 @@ void free_pc(pivchol_handle pc) {
   if (!pc) return;
   pc->L.release();
   pc->Q1.release();
+  pc->Qh.release();
+  pc->Ql.release();
   pc->dis.release();
   pc->ds.release();
   delete pc;
@@ -411,6 +413,14 @@ static int qr_form(dski_handle h, pivchol_handle pc, int* flag_dev, double* smal
       break;
     }
     pc->logdetM += 2.0 * (hld[0] + hld[1]);
+    // the FP32 (MIXED) modes apply Q1 in double-float arithmetic; FP64 and
+    // FP64_TC keep it in FP64: the QR-form apply cancels in the top
+    // eigen-directions, amplifying its rounding by ~1 + lambda_max / sigma^2
+    // (2^-44 double-float stalled PCG at 1.5e-6 where FP64 reached 2.5e-9)
+    if (!f64_vectors(h)) {
+      rc = split_q1(h, pc);
+      if (rc) break;
+    }
   } while (0);
   cudaStreamSynchronize(st);
   Q1a.release();

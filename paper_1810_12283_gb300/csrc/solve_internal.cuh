@@ -24,7 +24,11 @@ struct pivchol_ {
   double nv = 0, ng = 0;  // noise diagonal at build time
   double logdetM = 0;     // log|M| = sum log D + 2 sum log diag(R)
   dski::DevBuf L;         // N x rank FP64, col-major
-  dski::DevBuf Q1;        // N x rank FP64, col-major
+  dski::DevBuf Q1;        // N x rank FP64, col-major (FP64 mode)
+  // other modes: Q1 = Qh + Ql as two FP32 arrays (N x rank each), applied
+  // with error-free FP32 products and double-float sums (~2^-44 relative)
+  bool split = false;
+  dski::DevBuf Qh, Ql;
   dski::DevBuf dis;       // D^-1/2 per internal row
   dski::DevBuf ds;        // D^1/2 per internal row
   std::vector<int> piv;   // internal row of pivot k
@@ -74,6 +78,37 @@ __device__ __forceinline__ bool last_block(unsigned* ticket, unsigned nblocks) {
   return is_last;
 }
 
+// ---- double-float helpers: FP64-class accuracy on the FP32 units ----
+// (Dekker / Knuth error-free transformations: TwoSum and the FMA-based
+// exact product error.)  GB300 runs FP32 ~60x faster than FP64.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// (sh, sl) += (qh + ql) (yh + yl), dropping ql yl (below 2^-48 relative)
+__device__ __forceinline__ void df_fma(float qh, float ql, float yh, float yl, float& sh,
+                                       float& sl) {
+  const float p = qh * yh;
+  const float e = fmaf(qh, yh, -p);
+  const float t = fmaf(qh, yl, fmaf(ql, yh, e));
+  float s, err;
+  two_sum(sh, p, s, err);
+  sh = s;
+  sl += err + t;
+}
+// (sh, sl) += (bh, bl)
+__device__ __forceinline__ void df_add(float& sh, float& sl, float bh, float bl) {
+  float s, err;
+  two_sum(sh, bh, s, err);
+  sh = s;
+  sl += err + bl;
+}
+__device__ __forceinline__ void split_d(double x, float& h, float& l) {
+  h = (float)x;
+  l = (float)(x - (double)h);
+}
+
 // ---- host-side building blocks (pcg.cu) ----
 // Column dots: out[q] = sum_i a[q L + i] b[q L + i] for q < s (FP64,
 // deterministic); L = len, or N when len <= 0.
@@ -88,6 +123,11 @@ int ts_tn(dski_handle h, const double* A, int p, const double* B, int q, const d
 int ts_nn(dski_handle h, const double* X, double alpha, const double* xscale, double beta,
           const double* A, int p, const double* C, int q, double* Y, const double* rowscale);
 unsigned* tickets(dski_handle h, int count);   // zeroed last-block tickets
+//   C (p x q) = Q^T (w .* B) with Q = Qh + Ql split FP32 (q <= 4), FP64 result
+int df_gemv_t(dski_handle h, const float* Qh, const float* Ql, int p, const double* B, int q,
+              const double* w, double* C_dev);
+// build pc->Qh / pc->Ql from pc->Q1 and mark the preconditioner split
+int split_q1(dski_handle h, pivchol_handle pc);
 // Noise diagonal of the internal layout: D[e] = nv (value rows) or ng.
 int noise_diag(dski_handle h, double nv, double ng, double* D_dev);
 // M^-1 for s columns: Z = D^-1/2 (Y - Q1 Q1^T Y), Y = D^-1/2 R.
