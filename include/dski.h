@@ -202,14 +202,16 @@ int dski_mll_grad(dski_handle h, pivchol_handle pc, const double* y_dev, int pro
  *   mode 1: reset and start recording.  Every stage launch issued on the
  *           handle's stream is bracketed by a pair of CUDA events.
  *   mode 0: stop; synchronise the stream; write, per stage, the summed
- *           device milliseconds to ms_host[DSKI_NSTAGES] and the number of
- *           kernels launched to launches_host[DSKI_NSTAGES] (either may be
- *           NULL).  At most 2^18 event pairs are kept; launches beyond that
- *           are counted but not timed (*truncated_host, may be NULL, = 1).
+ *           device milliseconds to ms_host[DSKI_NSTAGES], the number of
+ *           kernels launched to launches_host[DSKI_NSTAGES] and the number of
+ *           those inside a timed event pair to timed_host[DSKI_NSTAGES] (any
+ *           may be NULL).  At most 2^18 event pairs are kept; launches beyond
+ *           that are counted but not timed (*truncated_host, may be NULL, = 1),
+ *           so ms / timed is the mean time per launch.
  * Errors: ARG, CUDA. */
 #define DSKI_NSTAGES 8
 int dski_profile(dski_handle h, int mode, double* ms_host, long long* launches_host,
-                 int* truncated_host);
+                 long long* timed_host, int* truncated_host);
 
 /* Number of CUDA kernels this library has launched in this process (all
  * handles).  A host-side counter, incremented at every launch site. */

@@ -161,15 +161,18 @@ class DSKI:
 
     def profile_start(self):
         """Start the per-stage device timers (dski_profile mode 1)."""
-        _lib.check(_lib.load().dski_profile(self.h, 1, None, None, None))
+        _lib.check(_lib.load().dski_profile(self.h, 1, None, None, None, None))
 
     def profile_stop(self):
-        """Stop the timers; returns {stage: (ms, launches)} and a truncated flag."""
+        """Stop the timers; returns {stage: (ms, launches, timed launches)}
+        and a truncated flag (ms covers the timed launches only)."""
         ms = (C.c_double * _lib.NSTAGES)()
         la = (C.c_longlong * _lib.NSTAGES)()
+        tl = (C.c_longlong * _lib.NSTAGES)()
         tr = C.c_int()
-        _lib.check(_lib.load().dski_profile(self.h, 0, ms, la, C.byref(tr)))
-        return {name: (ms[k], la[k]) for k, name in enumerate(_lib.STAGES)}, bool(tr.value)
+        _lib.check(_lib.load().dski_profile(self.h, 0, ms, la, tl, C.byref(tr)))
+        return ({name: (ms[k], la[k], tl[k]) for k, name in enumerate(_lib.STAGES)},
+                bool(tr.value))
 
     def logdet(self, pc, probes=16, depth=30, seed=777):
         ld = C.c_double()

@@ -67,7 +67,8 @@ def load(path=LIB_PATH):
     lib.pivchol_destroy.argtypes = [vp]
     lib.pivchol_destroy.restype = None
     lib.dski_last_error.restype = C.c_char_p
-    lib.dski_profile.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_longlong), ip]
+    lib.dski_profile.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_longlong),
+                                 C.POINTER(C.c_longlong), ip]
     lib.dski_launch_count.argtypes = []
     lib.dski_launch_count.restype = C.c_longlong
     lib.pivchol_export.argtypes = [vp, vp, ip]

@@ -39,6 +39,7 @@ struct Profiler {
   size_t next = 0;
   std::vector<Rec> recs;
   long long launches[ST_COUNT] = {};
+  long long timed[ST_COUNT] = {};   // launches inside a recorded event pair
   cudaEvent_t open_ev[ST_COUNT] = {};
   bool active = false;
   bool truncated = false;
@@ -49,6 +50,7 @@ struct Profiler {
     recs.clear();
     for (int k = 0; k < ST_COUNT; ++k) {
       launches[k] = 0;
+      timed[k] = 0;
       open_ev[k] = nullptr;
     }
     truncated = failed = false;
@@ -104,6 +106,7 @@ void stage_end(dski_handle h, int stage, cudaStream_t st, int launches) {
     return;
   }
   p->recs.push_back({a, b, stage});
+  p->timed[stage] += launches;
 }
 
 int DevBuf::ensure(size_t need) {
@@ -283,7 +286,7 @@ extern "C" int dski_mvm(dski_handle h, const void* v_dev, void* out_dev, int s) 
 }
 
 extern "C" int dski_profile(dski_handle h, int mode, double* ms_host, long long* launches_host,
-                            int* truncated_host) {
+                            long long* timed_host, int* truncated_host) {
   clear_error();
   if (!h) return set_error(DSKI_ERR_ARG, "dski_profile: NULL handle");
   if (mode == 1) {
@@ -318,6 +321,7 @@ extern "C" int dski_profile(dski_handle h, int mode, double* ms_host, long long*
     for (int k = 0; k < ST_COUNT; ++k) {
       if (ms_host) ms_host[k] = ms[k];
       if (launches_host) launches_host[k] = p->launches[k];
+      if (timed_host) timed_host[k] = p->timed[k];
     }
     if (truncated_host) *truncated_host = p->truncated ? 1 : 0;
   }

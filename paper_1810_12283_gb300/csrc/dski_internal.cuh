@@ -135,8 +135,25 @@ int scatter_internal(dski_handle h, const void* vin, void* g, int s, bool prec64
 // `ws` (scatter_ws_bytes bytes; NULL = the handle's workspace)
 int scatter_internal_ws(dski_handle h, const void* vin, void* g, int s, bool prec64, void* ws);
 size_t scatter_ws_bytes(dski_handle h, int s, bool prec64);
+// FP64 scatter of (sv v^0, sg v^1..d) (FP64, d >= 2, s <= 4 when scaled)
+int scatter_scaled(dski_handle h, const void* vin, void* g, int s, bool prec64, void* ws,
+                   double sv, double sg);
+// as scatter_scaled; with z != NULL first v <- z + beta_q v (written back)
+int scatter_fused(dski_handle h, const void* vin, void* g, int s, bool prec64, void* ws,
+                  double sv, double sg, const double* z, const double* beta);
+// PCG: P <- Z + beta P fused into the FP64 MVM Q = K~ P (when pcg_fusable)
+bool pcg_fusable(dski_handle h, int s);
+int mvm_pcg_fused(dski_handle h, double* P, const double* Z, const double* beta, double* Q,
+                  int s);
+// FP64 gather: vout^0 = av (B grid)^0 + nv vin^0, vout^p = ag (B grid)^p + ng vin^p
+int gather_scaled(dski_handle h, const double* grid, const double* vin, double* vout, int s,
+                  double av, double ag, double nv, double ng, int stage);
 int kron_internal(dski_handle h, void* g, void* tmp, int s, bool prec64, int dfactor,
                   const void* dK, void** result);
+
+// while on, the mode-product tile autotuner uses its heuristic (no timing, no
+// events) on this thread -- for callers that must not create resources
+void set_no_tune(bool on);
 
 // gather stage alone: vout = B grid + noise .* vin (internal layout)
 int gather_internal(dski_handle h, const void* grid, const void* vin, void* vout, int s,
@@ -147,7 +164,7 @@ int mode_tc_tf32(dski_handle h, const float* X, const float* Khi, const float* K
                  int m, long long R, int s, float scale, bool three);
 // FP64_TC mode products (kron_tc.cu): digits of a factor, and one mode product;
 // a factor's digit planes take kOzDigits x m x m BF16 values
-constexpr int kOzDigits = 7;
+constexpr int kOzDigits = 8;
 int oz_slice_factor(dski_handle h, const double* K, int m, uint16_t* Ad, int* fA);
 int mode_tc_oz(dski_handle h, const double* X, const uint16_t* Ad, const int* fA, double* Y,
                int m, long long R, int s, double scale);

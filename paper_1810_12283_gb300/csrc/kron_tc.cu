@@ -212,15 +212,16 @@ namespace {
 // accumulator.  Levels 0..S-1 are kept (one TMEM accumulator each) and
 // combined in FP64:
 //   Y[j][r] = 2^(fA_j + eB_r - 12) sum_l 2^(-7 l) T_l[j][r],
-// (summed exactly in int64 before one conversion to FP64), which drops only
-// the digit pairs of weight < 2^(-7 S) -- a relative error
-// of about 2^-49 of |K| |X|, the size of FP64 rounding in the 256-term sums
+// (summed exactly in two int64 halves), which drops only the digit pairs of
+// weight < 2^(-7 S) -- a relative error of about 2^-56 of |K| |X|, below FP64
+// rounding in the 256-term sums
 // (the FP32 product misses by 2^-24, 26x the noise variance on the terrain
 // grid).
 // K's digits are made once per factor; X's digits by a row-parallel kernel
 // before each mode product.
-constexpr int OZ_S = kOzDigits;                  // digits per operand (7)
+constexpr int OZ_S = kOzDigits;                  // digits per operand (8)
 constexpr int OZ_P = 6 + 7 * (OZ_S - 1);         // fixed-point bits: |V| < 2^OZ_P
+static_assert(OZ_P <= 62 && OZ_P - 53 <= 8, "fixed-point range");
 constexpr int OZ_M = 128, OZ_N = 32, OZ_KC = 64;   // 64 BF16 = one 128-byte row
 constexpr int OZ_A_BYTES = OZ_M * 128;           // 16 KB per digit
 constexpr int OZ_B_BYTES = OZ_N * 128;           // 4 KB per digit
@@ -228,7 +229,7 @@ constexpr int OZ_SMEM = OZ_S * (OZ_A_BYTES + OZ_B_BYTES) + 1024 + 256;
 constexpr int OZ_TMEM_COLS = 256;                // >= OZ_S * OZ_N, power of two
 static_assert(OZ_S * OZ_N <= OZ_TMEM_COLS, "TMEM columns");
 // exactness of one level: at most OZ_S digit pairs of 64 x 64, over K <= 256 terms
-static_assert((long long)OZ_S * 256 * 64 * 64 < (1LL << 24), "FP32 level sums must stay exact");
+static_assert((long long)OZ_S * 256 * 64 * 64 <= (1LL << 24), "FP32 level sums must stay exact");
 
 // Biased exponent field of |x| (0 for zero and subnormals).
 __device__ __forceinline__ int exp_field(double x) {
@@ -243,9 +244,12 @@ __device__ __forceinline__ long long fixedP(double x, int e) {
   const int E = (int)((u >> 52) & 0x7FF);
   if (E == 0) return 0;   // zero or subnormal: below the last digit
   const unsigned long long mant = (u & ((1ULL << 52) - 1)) | (1ULL << 52);
+  // |V| = mant 2^(E - 1075 + OZ_P - e); the shift can be left (by at most
+  // OZ_P - 53 when |x| is the row maximum) or right (with rounding)
   const int sh = 1075 - OZ_P + e - E;   // >= 53 - OZ_P because |x| < 2^e
   long long v = 0;
-  if (sh < 62) v = (long long)((mant + (1ULL << (sh - 1))) >> sh);
+  if (sh <= 0) v = (long long)(mant << (-sh));
+  else if (sh < 62) v = (long long)((mant + (1ULL << (sh - 1))) >> sh);
   return (u >> 63) ? -v : v;
 }
 
@@ -417,19 +421,28 @@ __global__ void __launch_bounds__(128) k_mode_tc_oz(const uint16_t* __restrict__
 #pragma unroll
     for (int c16 = 0; c16 < OZ_N / 16; ++c16) {
       // levels are exact integers below 2^24 (level l has <= l + 1 digit
-      // pairs): combine them exactly in int64, acc = sum_l T_l 2^(7 (S-1-l))
-      // (< 2^63 because |T_0| <= 2^20)
-      long long acc[16];
+      // pairs): combine them exactly in two int64 halves,
+      //   hi = sum_{l < H} T_l 2^(7 (H-1-l)),  lo = sum_{l >= H} T_l 2^(7 (S-1-l)),
+      // sum_l T_l 2^(-7 l) = 2^(-7 (S-1)) (hi 2^(7 (S-H)) + lo)
+      constexpr int H = OZ_S / 2;
+      long long hi[16], lo[16];
 #pragma unroll
-      for (int e = 0; e < 16; ++e) acc[e] = 0;
+      for (int e = 0; e < 16; ++e) hi[e] = lo[e] = 0;
 #pragma unroll
       for (int l = 0; l < OZ_S; ++l) {
         uint32_t v[16];
         tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + l * OZ_N + c16 * 16, v);
 #pragma unroll
-        for (int e = 0; e < 16; ++e)
-          acc[e] = acc[e] * 128 + (long long)__float2int_rz(__uint_as_float(v[e]));
+        for (int e = 0; e < 16; ++e) {
+          const long long t = (long long)__float2int_rz(__uint_as_float(v[e]));
+          if (l < H) hi[e] = hi[e] * 128 + t;
+          else lo[e] = lo[e] * 128 + t;
+        }
       }
+      double acc[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e)
+        acc[e] = fma((double)hi[e], (double)(1LL << (7 * (OZ_S - H))), (double)lo[e]);
       if (j < m) {
 #pragma unroll
         for (int e = 0; e < 16; ++e) {

@@ -469,6 +469,7 @@ int col_dots(dski_handle h, const double* a, const double* b, int s, double* out
 }
 
 int precond_apply(dski_handle h, pivchol_handle pc, const double* R, double* Z, int s) {
+  if (pc->grid_form) return grid_precond_apply(h, pc, R, Z, s);
   if (pc->split && pc->rank > 0) {
     double* C = wbuf(h->s_vec[5], (size_t)pc->rank * 4);
     if (!C) return DSKI_ERR_ALLOC;

@@ -8,6 +8,8 @@
 // The mode products here are the SIMT path (FP64 DFMA, or FP32 FFMA);
 // the tensor-core (3x)TF32 path lives in kron_tc.cu.
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "dski_internal.cuh"
 #include "keys.cuh"
@@ -149,17 +151,31 @@ __global__ void __launch_bounds__(256) k_scatter(MvmGeo g, const int* __restrict
 // A point-parallel pass forms A, B (P, Q) once per point; the node pass then
 // costs two FMAs per (node, point) instead of six (eight), which matters on
 // GB300 where FP64 arithmetic bounds the scatter.
+// PCG fusion: with z != NULL the pass first replaces v by z + beta_q v (the
+// CG search-direction update) and writes it back, then forms the products.
 template <int D>
 __global__ void __launch_bounds__(256) k_scatter_prep(const double* __restrict__ wt,
-                                                      const double* __restrict__ v, int s,
-                                                      int n, long long N,
+                                                      double* __restrict__ v, int s,
+                                                      int n, long long N, double sv, double sg,
+                                                      const double* __restrict__ z,
+                                                      const double* __restrict__ beta,
                                                       double* __restrict__ ab) {
   constexpr int NC = D == 2 ? 8 : 32;   // coefficients per point and column
   const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const double* wj = wt + j * (8 * D);
   for (int q = 0; q < s; ++q) {
-    const double* vq = v + (long long)q * N + j * (D + 1);
+    double* vq0 = v + (long long)q * N + j * (D + 1);
+    if (z) {
+      const double* zq = z + (long long)q * N + j * (D + 1);
+      const double be = beta[q];
+#pragma unroll
+      for (int c = 0; c <= D; ++c) vq0[c] = fma(be, vq0[c], zq[c]);
+    }
+    double vq[D + 1];
+    vq[0] = sv * vq0[0];
+#pragma unroll
+    for (int c = 1; c <= D; ++c) vq[c] = sg * vq0[c];
     double* o = ab + ((long long)q * n + j) * NC;
     if (D == 2) {
 #pragma unroll
@@ -251,15 +267,17 @@ __global__ void __launch_bounds__(256) k_scatter_ab(MvmGeo g, const int* __restr
 }
 
 // -------------------------------------------------------------- gather ----
-// out_j^0 = sum_u w_j(u) h(u) + nv v_j^0,  out_j^p = sum_u dw_{j,p}(u) h(u) + ng v_j^p,
-// evaluated dimension by dimension over the 4^d stencil.
+// out_j^0 = av sum_u w_j(u) h(u) + nv v_j^0,
+// out_j^p = ag sum_u dw_{j,p}(u) h(u) + ng v_j^p,
+// evaluated dimension by dimension over the 4^d stencil (av = ag = 1 and
+// nv, ng the noise for the MVM; other values for the preconditioner).
 template <class T, int D, int CB>
 __global__ void __launch_bounds__(256) k_gather(MvmGeo g, const int* __restrict__ cell,
                                                 const T* __restrict__ wt,
                                                 const T* __restrict__ grid,
                                                 const T* __restrict__ v, T* __restrict__ out,
                                                 int s, int n, long long N, long long M, T nv,
-                                                T ng) {
+                                                T ng, T av, T ag) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const int q0 = blockIdx.y * CB;
@@ -342,9 +360,9 @@ __global__ void __launch_bounds__(256) k_gather(MvmGeo g, const int* __restrict_
     }
     const T* vq = v + (long long)(q0 + q) * N + e;
     T* oq = out + (long long)(q0 + q) * N + e;
-    oq[0] = r[0] + nv * vq[0];
+    oq[0] = av * r[0] + nv * vq[0];
 #pragma unroll
-    for (int cc = 1; cc <= D; ++cc) oq[cc] = r[cc] + ng * vq[cc];
+    for (int cc = 1; cc <= D; ++cc) oq[cc] = ag * r[cc] + ng * vq[cc];
   }
 }
 
@@ -441,13 +459,20 @@ void launch_scatter(dski_handle h, const MvmGeo& g, const T* wt, const T* v, T* 
                                            v, grid, s, (long long)h->N, (long long)h->M);
 }
 
+struct GatherScale {
+  double av = 1.0, ag = 1.0;   // multiply B h on value / gradient rows
+  double nv = 0.0, ng = 0.0;   // multiply v on value / gradient rows
+  int stage = ST_GATHER;
+};
+
 template <class T, int D, int CB>
 void launch_gather(dski_handle h, const MvmGeo& g, const T* wt, const T* grid, const T* v,
-                   T* out, int s, cudaStream_t st) {
+                   T* out, int s, cudaStream_t st, const GatherScale& gs) {
   dim3 grd((unsigned)((h->n + 255) / 256), (unsigned)((s + CB - 1) / CB));
-  StageScope sc(h, ST_GATHER, st);
+  StageScope sc(h, gs.stage, st);
   k_gather<T, D, CB><<<grd, 256, 0, st>>>(g, h->cell.as<int>(), wt, grid, v, out, s, h->n,
-                                          (long long)h->N, (long long)h->M, (T)h->nv, (T)h->ng);
+                                          (long long)h->N, (long long)h->M, (T)gs.nv, (T)gs.ng,
+                                          (T)gs.av, (T)gs.ag);
 }
 
 template <class T, int D>
@@ -460,30 +485,108 @@ void scatter_dispatch(dski_handle h, const MvmGeo& g, const T* wt, const T* v, T
 
 template <class T, int D>
 void gather_dispatch(dski_handle h, const MvmGeo& g, const T* wt, const T* grid, const T* v,
-                     T* out, int s, cudaStream_t st) {
-  if (s == 1) launch_gather<T, D, 1>(h, g, wt, grid, v, out, s, st);
-  else if (s <= 4) launch_gather<T, D, 4>(h, g, wt, grid, v, out, s, st);
-  else launch_gather<T, D, 8>(h, g, wt, grid, v, out, s, st);
+                     T* out, int s, cudaStream_t st, const GatherScale* gsp = nullptr) {
+  GatherScale gs;
+  if (gsp) {
+    gs = *gsp;
+  } else {
+    gs.nv = h->nv;
+    gs.ng = h->ng;
+  }
+  if (s == 1) launch_gather<T, D, 1>(h, g, wt, grid, v, out, s, st, gs);
+  else if (s <= 4) launch_gather<T, D, 4>(h, g, wt, grid, v, out, s, st, gs);
+  else launch_gather<T, D, 8>(h, g, wt, grid, v, out, s, st, gs);
+}
+
+template <class T>
+void mode_simt_variant(int v, const T* X, const T* K, T* Y, int m, long long R, int s, T scale,
+                       cudaStream_t st) {
+  const int b = v == 0 ? 64 : (v == 1 ? 32 : 16);
+  dim3 grd((unsigned)((R + b - 1) / b), (unsigned)((m + b - 1) / b), (unsigned)s);
+  if (v == 0) k_mode_simt<T, 4, 4><<<grd, 256, 0, st>>>(X, K, Y, m, R, scale);
+  else if (v == 1) k_mode_simt<T, 2, 2><<<grd, 256, 0, st>>>(X, K, Y, m, R, scale);
+  else k_mode_simt<T, 1, 1><<<grd, 256, 0, st>>>(X, K, Y, m, R, scale);
+}
+
+// Tile autotuner of the SIMT mode product: the first product of a given
+// (element size, m, R, s) on a device times the three tile shapes (64, 32,
+// 16 square; one warm-up and three timed launches each, CUDA events on the
+// caller's stream) and remembers the fastest.  While the stream is being
+// captured into a graph no timing is possible and a CTA-count heuristic picks.
+struct TuneKey {
+  int dev, es, m, s;
+  long long R;
+  bool operator<(const TuneKey& o) const {
+    if (dev != o.dev) return dev < o.dev;
+    if (es != o.es) return es < o.es;
+    if (m != o.m) return m < o.m;
+    if (s != o.s) return s < o.s;
+    return R < o.R;
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+thread_local bool g_no_tune = false;   // set by callers that must not create events
+
+template <class T>
+int pick_variant(const T* X, const T* K, T* Y, int m, long long R, int s, T scale, int sms,
+                 cudaStream_t st) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const TuneKey key{dev, (int)sizeof(T), m, s, R};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+  }
+  auto ctas = [&](int b) { return ((R + b - 1) / b) * (long long)((m + b - 1) / b) * s; };
+  const int heur = ctas(64) >= 2LL * sms ? 0 : (ctas(32) >= 2LL * sms ? 1 : 2);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (g_no_tune || cudaStreamIsCapturing(st, &cap) != cudaSuccess ||
+      cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return heur;
+  }
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    cudaGetLastError();
+    if (a) cudaEventDestroy(a);
+    return heur;
+  }
+  int best = heur;
+  float best_ms = 1e30f;
+  for (int v = 0; v < 3; ++v) {
+    mode_simt_variant<T>(v, X, K, Y, m, R, s, scale, st);
+    cudaEventRecord(a, st);
+    for (int rep = 0; rep < 3; ++rep) mode_simt_variant<T>(v, X, K, Y, m, R, s, scale, st);
+    cudaEventRecord(b, st);
+    float ms = 0.f;
+    if (cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess &&
+        ms < best_ms) {
+      best_ms = ms;
+      best = v;
+    }
+  }
+  cudaGetLastError();
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  count_launches(12);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = best;
+  return best;
 }
 
 template <class T>
 void mode_simt(dski_handle h, const T* X, const T* K, T* Y, int m, long long R, int s, T scale,
                int sms, cudaStream_t st) {
+  const int v = pick_variant<T>(X, K, Y, m, R, s, scale, sms, st);
   StageScope sc(h, ST_KRON, st);
-  auto ctas = [&](int b) { return ((R + b - 1) / b) * (long long)((m + b - 1) / b) * s; };
-  if (ctas(64) >= 2LL * sms) {
-    dim3 grd((unsigned)((R + 63) / 64), (unsigned)((m + 63) / 64), (unsigned)s);
-    k_mode_simt<T, 4, 4><<<grd, 256, 0, st>>>(X, K, Y, m, R, scale);
-  } else if (ctas(32) >= 2LL * sms) {
-    dim3 grd((unsigned)((R + 31) / 32), (unsigned)((m + 31) / 32), (unsigned)s);
-    k_mode_simt<T, 2, 2><<<grd, 256, 0, st>>>(X, K, Y, m, R, scale);
-  } else {
-    dim3 grd((unsigned)((R + 15) / 16), (unsigned)((m + 15) / 16), (unsigned)s);
-    k_mode_simt<T, 1, 1><<<grd, 256, 0, st>>>(X, K, Y, m, R, scale);
-  }
+  mode_simt_variant<T>(v, X, K, Y, m, R, s, scale, st);
 }
 
 }  // namespace
+
+void set_no_tune(bool on) { g_no_tune = on; }
 
 size_t scatter_ws_bytes(dski_handle h, int s, bool prec64) {
   if (!(prec64 && h->d >= 2 && s <= 4)) return 0;
@@ -495,6 +598,16 @@ int scatter_internal(dski_handle h, const void* vin, void* g, int s, bool prec64
 }
 
 int scatter_internal_ws(dski_handle h, const void* vin, void* g, int s, bool prec64, void* ws) {
+  return scatter_scaled(h, vin, g, s, prec64, ws, 1.0, 1.0);
+}
+
+int scatter_scaled(dski_handle h, const void* vin, void* g, int s, bool prec64, void* ws,
+                   double sv, double sg) {
+  return scatter_fused(h, vin, g, s, prec64, ws, sv, sg, nullptr, nullptr);
+}
+
+int scatter_fused(dski_handle h, const void* vin, void* g, int s, bool prec64, void* ws,
+                  double sv, double sg, const double* z, const double* beta) {
   const MvmGeo geo = make_geo(h);
   cudaStream_t st = h->stream;
   if (prec64 && h->d >= 2 && s <= 4) {
@@ -509,13 +622,13 @@ int scatter_internal_ws(dski_handle h, const void* vin, void* g, int s, bool pre
     const dim3 gs((unsigned)((h->M * 4 + 255) / 256), 1);
     StageScope sc(h, ST_SCATTER, st, 2);
     if (h->d == 2) {
-      k_scatter_prep<2><<<gp, 256, 0, st>>>(wt, (const double*)vin, s, h->n, h->N, ab);
+      k_scatter_prep<2><<<gp, 256, 0, st>>>(wt, (double*)vin, s, h->n, h->N, sv, sg, z, beta, ab);
       if (s == 1)
         k_scatter_ab<2, 1><<<gs, 256, 0, st>>>(geo, h->cell_start.as<int>(), h->cell.as<int>(), wt, ab, (double*)g, s, h->n, h->M);
       else
         k_scatter_ab<2, 4><<<gs, 256, 0, st>>>(geo, h->cell_start.as<int>(), h->cell.as<int>(), wt, ab, (double*)g, s, h->n, h->M);
     } else {
-      k_scatter_prep<3><<<gp, 256, 0, st>>>(wt, (const double*)vin, s, h->n, h->N, ab);
+      k_scatter_prep<3><<<gp, 256, 0, st>>>(wt, (double*)vin, s, h->n, h->N, sv, sg, z, beta, ab);
       if (s == 1)
         k_scatter_ab<3, 1><<<gs, 256, 0, st>>>(geo, h->cell_start.as<int>(), h->cell.as<int>(), wt, ab, (double*)g, s, h->n, h->M);
       else
@@ -524,6 +637,8 @@ int scatter_internal_ws(dski_handle h, const void* vin, void* g, int s, bool pre
     DSKI_LAUNCHED();
     return DSKI_OK;
   }
+  if (sv != 1.0 || sg != 1.0 || z)
+    return set_error(DSKI_ERR_ARG, "scaled / fused scatter needs FP64, d >= 2 and s <= 4");
   if (prec64) {
     const double* fr = h->W64.as<double>();
     switch (h->d) {
@@ -608,6 +723,25 @@ int mvm_internal(dski_handle h, const void* vin, void* vout, int s, bool prec64)
   return DSKI_OK;
 }
 
+int gather_scaled(dski_handle h, const double* grid, const double* vin, double* vout, int s,
+                  double av, double ag, double nv, double ng, int stage) {
+  const MvmGeo geo = make_geo(h);
+  GatherScale gs;
+  gs.av = av;
+  gs.ag = ag;
+  gs.nv = nv;
+  gs.ng = ng;
+  gs.stage = stage;
+  const double* fr = h->W64.as<double>();
+  switch (h->d) {
+    case 1: gather_dispatch<double, 1>(h, geo, fr, grid, vin, vout, s, h->stream, &gs); break;
+    case 2: gather_dispatch<double, 2>(h, geo, fr, grid, vin, vout, s, h->stream, &gs); break;
+    default: gather_dispatch<double, 3>(h, geo, fr, grid, vin, vout, s, h->stream, &gs); break;
+  }
+  DSKI_LAUNCHED();
+  return DSKI_OK;
+}
+
 int gather_internal(dski_handle h, const void* grid, const void* vin, void* vout, int s,
                     bool prec64) {
   const MvmGeo geo = make_geo(h);
@@ -629,6 +763,19 @@ int gather_internal(dski_handle h, const void* grid, const void* vin, void* vout
   }
   DSKI_LAUNCHED();
   return DSKI_OK;
+}
+
+bool pcg_fusable(dski_handle h, int s) { return f64_vectors(h) && h->d >= 2 && s <= 4; }
+
+int mvm_pcg_fused(dski_handle h, double* P, const double* Z, const double* beta, double* Q,
+                  int s) {
+  const size_t gbytes = (size_t)h->M * s * 8;
+  if (h->gridA.ensure(gbytes) || h->gridB.ensure(gbytes))
+    return set_error(DSKI_ERR_ALLOC, "grid workspace allocation failed (%zu bytes)", gbytes);
+  DSKI_TRY(scatter_fused(h, P, h->gridA.ptr, s, true, nullptr, 1.0, 1.0, Z, beta));
+  void* res = nullptr;
+  DSKI_TRY(kron_internal(h, h->gridA.ptr, h->gridB.ptr, s, true, -1, nullptr, &res));
+  return gather_internal(h, res, P, Q, s, true);
 }
 
 int permute_in(dski_handle h, const void* v_user, void* v_int, int s, bool f64, cudaStream_t st) {

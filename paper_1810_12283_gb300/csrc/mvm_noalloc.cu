@@ -93,7 +93,11 @@ extern "C" int dski_mvm_noalloc(dski_handle h, const void* v_dev, void* out_dev,
   void* gB = p + 2 * pad256(vbytes) + pad256(gbytes);
   void* ab = p + 2 * pad256(vbytes) + 2 * pad256(gbytes);
   // Every stage writes its whole output before the next reads it, so nothing
-  // in the array has to start at zero.
+  // in the array has to start at zero.  The tile autotuner stays off here.
+  struct NoTune {
+    NoTune() { set_no_tune(true); }
+    ~NoTune() { set_no_tune(false); }
+  } no_tune;
   DSKI_TRY(permute_in(h, v_dev, vin, s, f64, h->stream));
   DSKI_TRY(scatter_internal_ws(h, vin, gA, s, f64, abytes ? ab : nullptr));
   void* res = nullptr;

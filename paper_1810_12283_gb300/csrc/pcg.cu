@@ -117,10 +117,11 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_init(
 // init: p = z (and its float copy), r^T z becomes rz and rz0.
 // else: beta = (r^T z)_new / rz for active columns, recorded.
 // SPLIT: Q1 = Qh + Ql in FP32 halves, the product taken in double-float.
+// ZIN: z given (computed by the grid-form apply); only the dots/updates run.
 template <bool SPLIT>
 __global__ void __launch_bounds__(CG_THREADS) k_cg_z(
     const double* __restrict__ r, const double* __restrict__ y, const double* __restrict__ Q1,
-    const float* __restrict__ Qh, const float* __restrict__ Ql,
+    const float* __restrict__ Qh, const float* __restrict__ Ql, const double* __restrict__ zin,
     int rank, const double* __restrict__ C, const double* __restrict__ dis,
     double* __restrict__ z, double* __restrict__ p, float* __restrict__ p32, long long N,
     int init, ColState cs, double* part, unsigned* ticket) {
@@ -138,7 +139,9 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_z(
        i += (long long)gridDim.x * blockDim.x) {
     const long long o = (long long)c * N + i;
     double zi;
-    if (y) {
+    if (zin) {
+      zi = zin[o];
+    } else if (y) {
       double v = y[o];
       // Q1 columns in groups of 8: the group's loads are issued together so
       // that each thread keeps 8 (16) independent loads in flight
@@ -172,11 +175,11 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_z(
       zi = r[o];
     }
     acc = fma(r[o], zi, acc);
+    // z is kept also at a (re)start: the fused MVM forms p = z + beta p from it
+    if (!zin) z[o] = zi;
     if (init) {
       p[o] = zi;
       if (p32) p32[o] = (float)zi;
-    } else {
-      z[o] = zi;
     }
   }
   acc = block_sum(acc, sh);
@@ -369,7 +372,18 @@ int cg_run(dski_handle h, CgRun& run) {
   const size_t zsmem = (size_t)std::max(rank, 1) * sizeof(double);
 
   const bool split = run.pc && run.pc->split;
+  const bool gridf = run.pc && run.pc->grid_form;
+  const bool fused = !mixed && pcg_fusable(h, s);
   auto precond_z = [&](int init) -> int {
+    if (gridf) {
+      DSKI_TRY(grid_precond_apply(h, run.pc, R, Z, s));
+      StageScope sc(h, ST_PCGVEC, st);
+      k_cg_z<false><<<grd, CG_THREADS, zsmem, st>>>(R, nullptr, nullptr, nullptr, nullptr, Z, 0,
+                                                   nullptr, nullptr, Z, P, P32, N, init, cs, part,
+                                                   tk);
+      DSKI_LAUNCHED();
+      return DSKI_OK;
+    }
     if (rank && split) {
       for (int c0 = 0; c0 < s; c0 += 4)
         DSKI_TRY(df_gemv_t(h, run.pc->Qh.as<float>(), run.pc->Ql.as<float>(), rank,
@@ -384,12 +398,12 @@ int cg_run(dski_handle h, CgRun& run) {
     StageScope sc(h, ST_PRECOND, st);
     if (split)
       k_cg_z<true><<<grd, CG_THREADS, zsmem, st>>>(R, Y, nullptr, run.pc->Qh.as<float>(),
-                                                  run.pc->Ql.as<float>(), rank, C, dis, Z, P, P32,
-                                                  N, init, cs, part, tk);
+                                                  run.pc->Ql.as<float>(), nullptr, rank, C, dis, Z,
+                                                  P, P32, N, init, cs, part, tk);
     else
       k_cg_z<false><<<grd, CG_THREADS, zsmem, st>>>(R, Y, rank ? run.pc->Q1.as<double>() : nullptr,
-                                                   nullptr, nullptr, rank, C, dis, Z, P, P32, N,
-                                                   init, cs, part, tk);
+                                                   nullptr, nullptr, nullptr, rank, C, dis, Z, P,
+                                                   P32, N, init, cs, part, tk);
     DSKI_LAUNCHED();
     return DSKI_OK;
   };
@@ -413,18 +427,21 @@ int cg_run(dski_handle h, CgRun& run) {
       k_cg_alpha<float><<<grd, CG_THREADS, 0, st>>>(P, Q32, N, cs, part, tk);
       k_cg_update<float><<<grd, CG_THREADS, 0, st>>>(run.X, R, Y, P, Q32, dis, N, cs, part, tk);
     } else {
-      DSKI_TRY(mvm_internal(h, P, Q, s, true));
+      // fused: the previous iteration's p = z + beta p happens in the MVM's
+      // first pass (after an (re)start beta = 0 and p = z already)
+      if (fused) DSKI_TRY(mvm_pcg_fused(h, P, Z, cs.beta, Q, s));
+      else DSKI_TRY(mvm_internal(h, P, Q, s, true));
       StageScope sc(h, ST_PCGVEC, st, 2);
       k_cg_alpha<double><<<grd, CG_THREADS, 0, st>>>(P, Q, N, cs, part, tk);
       k_cg_update<double><<<grd, CG_THREADS, 0, st>>>(run.X, R, Y, P, Q, dis, N, cs, part, tk);
     }
     DSKI_LAUNCHED();
     DSKI_TRY(precond_z(0));
-    {
+    if (!fused) {
       StageScope sc(h, ST_PCGVEC, st);
       k_cg_p<<<grd, CG_THREADS, 0, st>>>(Z, P, P32, N, cs);
+      DSKI_LAUNCHED();
     }
-    DSKI_LAUNCHED();
     return DSKI_OK;
   };
 

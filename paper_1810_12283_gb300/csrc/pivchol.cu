@@ -353,6 +353,10 @@ void free_pc(pivchol_handle pc) {
   pc->Q1.release();
   pc->Qh.release();
   pc->Ql.release();
+  pc->Hf.release();
+  pc->H1T.release();
+  pc->Sg.release();
+  pc->gwork.release();
   pc->dis.release();
   pc->ds.release();
   delete pc;
@@ -361,7 +365,8 @@ void free_pc(pivchol_handle pc) {
 }  // namespace
 
 // CholeskyQR2 of [D^-1/2 L; I]: Q1 = D^-1/2 L R1^-1 R2^-1, log|M|.
-static int qr_form(dski_handle h, pivchol_handle pc, int* flag_dev, double* small) {
+static int qr_form(dski_handle h, pivchol_handle pc, int* flag_dev, double* small,
+                   const int* piv_dev) {
   const int r = pc->rank;
   const long long N = h->N;
   cudaStream_t st = h->stream;
@@ -413,6 +418,8 @@ static int qr_form(dski_handle h, pivchol_handle pc, int* flag_dev, double* smal
       break;
     }
     pc->logdetM += 2.0 * (hld[0] + hld[1]);
+    rc = grid_precond_build(h, pc, piv_dev, R1i, R2i);
+    if (rc) break;
     // the FP32 (MIXED) modes apply Q1 in double-float arithmetic; FP64 and
     // FP64_TC keep it in FP64: the QR-form apply cancels in the top
     // eigen-directions, amplifying its rounding by ~1 + lambda_max / sigma^2
@@ -526,7 +533,7 @@ extern "C" int pivchol_build(dski_handle h, int rank, pivchol_handle* out, int* 
     pc->logdetM = (double)h->n * std::log(h->nv) + (double)h->n * h->d * std::log(h->ng);
     if (pc->rank > 0) {
       if (cudaMemsetAsync(flag, 0, sizeof(int), st) != cudaSuccess) { rc = DSKI_ERR_CUDA; break; }
-      rc = qr_form(h, pc, flag, small);
+      rc = qr_form(h, pc, flag, small, piv_list);
       if (rc) break;
       int hflag = 0;
       if (cudaMemcpy(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {

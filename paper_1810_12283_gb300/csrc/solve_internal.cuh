@@ -29,6 +29,11 @@ struct pivchol_ {
   // with error-free FP32 products and double-float sums (~2^-44 relative)
   bool split = false;
   dski::DevBuf Qh, Ql;
+  // grid form (d = 2, M < N, FP64 vectors): M^-1 r = D^-1 (r - B H S H^T B^T D^-1 r)
+  // with H's columns rank-1 Kronecker products (factors Hf: r x m0 then r x m1,
+  // H1T = the second block transposed) and S = T T^T (r x r)
+  bool grid_form = false;
+  dski::DevBuf Hf, H1T, Sg, gwork;
   dski::DevBuf dis;       // D^-1/2 per internal row
   dski::DevBuf ds;        // D^1/2 per internal row
   std::vector<int> piv;   // internal row of pivot k
@@ -128,6 +133,11 @@ int df_gemv_t(dski_handle h, const float* Qh, const float* Ql, int p, const doub
               const double* w, double* C_dev);
 // build pc->Qh / pc->Ql from pc->Q1 and mark the preconditioner split
 int split_q1(dski_handle h, pivchol_handle pc);
+// grid form of the preconditioner (precond_grid.cu): build after CholeskyQR2
+// (no-op where it does not apply), and apply to s internal-layout columns
+int grid_precond_build(dski_handle h, pivchol_handle pc, const int* piv_dev, const double* R1i,
+                       const double* R2i);
+int grid_precond_apply(dski_handle h, pivchol_handle pc, const double* R, double* Z, int s);
 // Noise diagonal of the internal layout: D[e] = nv (value rows) or ng.
 int noise_diag(dski_handle h, double nv, double ng, double* D_dev);
 // M^-1 for s columns: Z = D^-1/2 (Y - Q1 Q1^T Y), Y = D^-1/2 R.

@@ -1,0 +1,60 @@
+"""Host-side logic of bench.py (no GPU): the max-over-ranks reduction of the
+N > 1 path on two gloo ranks, and the algorithmic byte counts the roofline
+fields are computed from."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), DSKI_BENCH_BACKEND="gloo")
+    import bench
+    r, ws, d = bench.dist_init()
+    assert (r, ws) == (rank, world)
+    got = bench.reduce_max(d, 1.5 + 2.0 * rank, torch.device("cpu"))
+    out.put((rank, got))
+    d.barrier()
+    d.destroy_process_group()
+
+
+def test_reduce_max_over_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    res = dict(q.get(timeout=10) for _ in range(2))
+    assert res == {0: 3.5, 1: 3.5}
+
+
+def test_single_process_reduce_is_identity():
+    import bench
+    assert bench.reduce_max(None, 2.25, torch.device("cpu")) == 2.25
+
+
+def test_algorithmic_byte_counts():
+    import bench
+    # terrain MVM in FP64: v read twice and out written (3 N), grid written and
+    # read (2 M), geometry (cell id + 8 d weights) read twice
+    n, d, M = 100_000, 2, 65_536
+    N = n * (d + 1)
+    assert bench.mvm_bytes(n, d, M, 1, 8) == 3 * N * 8 + 2 * M * 8 + 2 * n * (4 + 8 * 8 * d)
+    assert bench.precond_bytes(N, 100, 1) == 2 * N * 100 * 8 + 3 * N * 8
