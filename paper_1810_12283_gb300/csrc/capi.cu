@@ -154,6 +154,7 @@ static void release_all(dski_handle h) {
   h->scratch.release();
   h->dev_err.release();
   h->ozB.release();
+  h->ozP.release();
   h->scat_ab.release();
   h->ozE.release();
   h->s_part.release();

@@ -87,6 +87,8 @@ struct dski_handle_ {
   double ell[DSKI_MAXD] = {1, 1, 1};
   double sf = 1.0, nv = 0.0, ng = 0.0;
   int prec = DSKI_FP64;
+  // FP64_TC: run the mode products on the FP64 units instead (true residuals)
+  bool kron_exact = false;
   cudaStream_t stream = nullptr;
   int M = 0;        // grid size prod m_k
   int ncell = 0;    // prod mc_k
@@ -100,10 +102,11 @@ struct dski_handle_ {
   dski::DevBuf K64[DSKI_MAXD], K32[DSKI_MAXD], Khi[DSKI_MAXD], Klo[DSKI_MAXD];
   // dK_k / dlog l_k = K_k .* ((a - b) h_k)^2 / l_k^2 (FP64), for the gradient of Eq. 1
   dski::DevBuf dK64[DSKI_MAXD];
-  // FP64_TC mode: six BF16 digit planes of K_k (6 x m x m) and row exponents
+  // FP64_TC mode: eight BF16 digit planes of K_k (8 x m x m) and row exponents
   dski::DevBuf Kdig[DSKI_MAXD], Kexp[DSKI_MAXD];
-  // FP64_TC: digit planes and row exponents of the grid operand (workspace)
-  dski::DevBuf ozB, ozE;
+  // FP64_TC: digit planes and row exponents of the grid operand, int32 level
+  // partials of the split contraction (workspace)
+  dski::DevBuf ozB, ozE, ozP;
   // FP64 scatter: per-point sum-factorised coefficients (workspace)
   dski::DevBuf scat_ab;
   // workspace

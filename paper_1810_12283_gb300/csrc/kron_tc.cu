@@ -19,6 +19,11 @@
 // issues the MMAs and commits them to the stage's mbarrier; a stage is reused
 // only after its mbarrier reports the MMAs that read it complete.  Every wait
 // is bounded: on time-out the kernel records an error and still frees TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
 #include "dski_internal.cuh"
 #include "tc_common.cuh"
 
@@ -203,31 +208,24 @@ namespace {
 // ---------------------------------------------------------------------------
 // FP64-accurate mode products on the BF16 tensor cores (DSKI_FP64_TC).
 //
-// Both operands are split into S = 6 signed 7-bit digits relative to a
+// Both operands are split into S = 8 signed 7-bit digits relative to a
 // per-row power of two (Ozaki-style splitting): for a row with max |x| <
-// 2^e, x = 2^e sum_b d_b 2^(-6 - 7 b) up to rounding at 2^(e - 41), d_b
-// integers in [-64, 64] (exact in BF16), extracted with integer arithmetic.  A product of digits is at most 2^12 in magnitude and a sum of
-// m <= 256 of them, over the <= 6 digit pairs (a, b) of one level a + b, stays
-// below 2^23, so every level accumulates EXACTLY in the FP32 TMEM
-// accumulator.  Levels 0..S-1 are kept (one TMEM accumulator each) and
-// combined in FP64:
+// 2^e, x = 2^e sum_b d_b 2^(-6 - 7 b) up to rounding at 2^(e - 55), d_b
+// integers in [-64, 64] (exact in BF16), extracted with integer arithmetic.
+// A product of digits is at most 2^12 in magnitude and a sum of m <= 256 of
+// them, over the <= 8 digit pairs (a, b) of one level a + b, stays within
+// 2^23, so every level accumulates EXACTLY in the FP32 TMEM accumulator.
+// Levels 0..S-1 are kept (one TMEM accumulator each) and combined in FP64:
 //   Y[j][r] = 2^(fA_j + eB_r - 12) sum_l 2^(-7 l) T_l[j][r],
 // (summed exactly in two int64 halves), which drops only the digit pairs of
-// weight < 2^(-7 S) -- a relative error of about 2^-56 of |K| |X|, below FP64
-// rounding in the 256-term sums
-// (the FP32 product misses by 2^-24, 26x the noise variance on the terrain
-// grid).
+// weight < 2^(-7 S) -- a relative error of about 2^-53 of |K| |X|, at FP64
+// rounding in the 256-term sums (the FP32 product misses by 2^-24, 26x the
+// noise variance on the terrain grid).
 // K's digits are made once per factor; X's digits by a row-parallel kernel
 // before each mode product.
 constexpr int OZ_S = kOzDigits;                  // digits per operand (8)
 constexpr int OZ_P = 6 + 7 * (OZ_S - 1);         // fixed-point bits: |V| < 2^OZ_P
 static_assert(OZ_P <= 62 && OZ_P - 53 <= 8, "fixed-point range");
-constexpr int OZ_M = 128, OZ_N = 32, OZ_KC = 64;   // 64 BF16 = one 128-byte row
-constexpr int OZ_A_BYTES = OZ_M * 128;           // 16 KB per digit
-constexpr int OZ_B_BYTES = OZ_N * 128;           // 4 KB per digit
-constexpr int OZ_SMEM = OZ_S * (OZ_A_BYTES + OZ_B_BYTES) + 1024 + 256;
-constexpr int OZ_TMEM_COLS = 256;                // >= OZ_S * OZ_N, power of two
-static_assert(OZ_S * OZ_N <= OZ_TMEM_COLS, "TMEM columns");
 // exactness of one level: at most OZ_S digit pairs of 64 x 64, over K <= 256 terms
 static_assert((long long)OZ_S * 256 * 64 * 64 <= (1LL << 24), "FP32 level sums must stay exact");
 
@@ -317,141 +315,133 @@ __global__ void __launch_bounds__(256) k_oz_slice_rows(const double* __restrict_
   }
 }
 
-__global__ void __launch_bounds__(128) k_mode_tc_oz(const uint16_t* __restrict__ Bd,
-                                                    const int* __restrict__ eBg,
-                                                    const uint16_t* __restrict__ Ad,
-                                                    const int* __restrict__ fA,
-                                                    double* __restrict__ Y, int m, long long R,
-                                                    double scale, int* __restrict__ err) {
+// One split of the contraction: the exact FP32 level sums
+//   T_l[j][r] = sum_{a + b = l} sum_{i in split} A_a[j][i] B_b[r][i]
+// of a 128 x 32 output tile, written as int32 to P[q][split][l][j][r].  The
+// digit planes stream in by TMA (64-byte rows, 64-byte swizzle, box 32 wide)
+// through two stages; one thread issues the loads and the 36 MMAs per
+// 16-deep step; stages are recycled when their MMAs commit.  Splitting the
+// contraction over CTAs puts 64 CTAs on a 256 x 256 mode product.
+constexpr int Z_M = 128, Z_N = 32, Z_KC = 32;    // 32 BF16 = one 64-byte row
+constexpr int Z_A = Z_M * 64;                     // 8 KB per digit plane
+constexpr int Z_B = Z_N * 64;                     // 2 KB per digit plane
+constexpr int Z_STAGE = OZ_S * (Z_A + Z_B);       // 80 KB
+constexpr int Z_SMEM = 2 * Z_STAGE + 1024 + 128;
+static_assert(OZ_S * Z_N <= 256, "TMEM columns");
+
+__global__ void __launch_bounds__(128) k_oz_gemm(const __grid_constant__ CUtensorMap tA,
+                                                 const __grid_constant__ CUtensorMap tB,
+                                                 int* __restrict__ P, int m, long long R,
+                                                 int KS, int kper, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sA = smem;                                  // OZ_S digit tiles of A
-  unsigned char* sB = smem + OZ_S * OZ_A_BYTES;              // OZ_S digit tiles of B
-  uint64_t* mbar = (uint64_t*)(sB + OZ_S * OZ_B_BYTES);
-  uint32_t* tslot = (uint32_t*)(mbar + 1);
-  int* eB = (int*)(tslot + 4);                               // OZ_N row exponents
+  uint64_t* full = (uint64_t*)(smem + 2 * Z_STAGE);
+  uint64_t* empty = full + 2;
+  uint64_t* done = full + 4;
+  uint32_t* tslot = (uint32_t*)(full + 5);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int j0 = blockIdx.x * OZ_M;
-  const long long r0 = (long long)blockIdx.y * OZ_N;
-  const long long q = blockIdx.z;
-  double* Yq = Y + q * R * m;
-  const uint16_t* Bq = Bd + q * OZ_S * R * m;
+  const int j0 = blockIdx.x * Z_M;
+  const int r0 = blockIdx.y * Z_N;
+  const int z = blockIdx.z, q = z / KS, ks = z % KS;
+  const int k_begin = ks * kper;
+  const int k_end = min(m, k_begin + kper);
+  const int nch = (k_end - k_begin + Z_KC - 1) / Z_KC;   // >= 1 by construction
 
-  if (warp == 0) tc::tmem_alloc(tslot, OZ_TMEM_COLS);
+  if (warp == 0) tc::tmem_alloc(tslot, 256);
   if (tid == 0) {
-    tc::mbar_init(&mbar[0], 1);
+    for (int i = 0; i < 5; ++i) tc::mbar_init(&full[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (tid < OZ_N) eB[tid] = (r0 + tid < R) ? eBg[q * R + r0 + tid] : 0;
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *tslot;
-  constexpr uint32_t idesc = tc::instr_desc(tc::kFmtBF16, OZ_M, OZ_N);
+  constexpr uint32_t idesc = tc::instr_desc(tc::kFmtBF16, Z_M, Z_N);
 
-  const int nk = (m + OZ_KC - 1) / OZ_KC;
-  uint32_t phase = 0u;
   int ok = 1;
-  for (int kc = 0; kc < nk; ++kc) {
-    if (kc > 0) {
-      ok &= tc::mbar_wait(&mbar[0], phase, WAIT_LIMIT) ? 1 : 0;
-      phase ^= 1u;
-    }
-    if (!__syncthreads_and(ok)) break;
-    const int i0 = kc * OZ_KC;
-    // A digits: row tid, 8 chunks of 8 BF16 per digit (m % 8 == 0)
-    {
-      const int j = j0 + tid;
-#pragma unroll
+  if (tid == 0) {
+    int issued = 0, consumed = 0;
+    auto issue = [&](int c) {
+      const int st = c & 1;
+      unsigned char* base = smem + st * Z_STAGE;
+      tc::mbar_expect_tx(&full[st], (uint32_t)Z_STAGE);
+      const int i0 = k_begin + c * Z_KC;
       for (int b = 0; b < OZ_S; ++b) {
-        unsigned char* dst = sA + b * OZ_A_BYTES;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const int i = i0 + 8 * c;
-          uint4 v = make_uint4(0, 0, 0, 0);
-          if (j < m && i < m) v = *(const uint4*)(Ad + ((long long)b * m + j) * m + i);
-          *(uint4*)(dst + tc::sw128_off(tid, c)) = v;
-        }
+        tc::tma_load_3d(base + b * Z_A, &tA, i0, j0, b, &full[st]);
+        tc::tma_load_4d(base + OZ_S * Z_A + b * Z_B, &tB, i0, r0, b, q, &full[st]);
       }
-    }
-    // B digits: row tid / 4 of the tile, 2 chunks of 8 BF16 per digit
-    {
-      const int row = tid >> 2, part = tid & 3;
-      const long long r = r0 + row;
-#pragma unroll
-      for (int b = 0; b < OZ_S; ++b) {
-        unsigned char* dst = sB + b * OZ_B_BYTES;
-#pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-          const int c = part * 2 + cc;
-          const int i = i0 + 8 * c;
-          uint4 v = make_uint4(0, 0, 0, 0);
-          if (r < R && i < m) v = *(const uint4*)(Bq + ((long long)b * R + r) * m + i);
-          *(uint4*)(dst + tc::sw128_off(row, c)) = v;
-        }
+      issued = c + 1;
+    };
+    issue(0);
+    if (nch > 1) issue(1);
+    for (int c = 0; c < nch; ++c) {
+      const int st = c & 1;
+      const uint32_t ph = (uint32_t)((c >> 1) & 1);
+      if (!tc::mbar_wait(&full[st], ph, WAIT_LIMIT)) {
+        ok = 0;
+        break;
       }
-    }
-    tc::fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
+      consumed = c + 1;
       tc::fence_after();
+      const uint32_t aB = tc::smem_u32(smem + st * Z_STAGE);
+      const uint32_t bB = aB + OZ_S * Z_A;
 #pragma unroll
-      for (int kk = 0; kk < OZ_KC / 16; ++kk) {
+      for (int kk = 0; kk < Z_KC / 16; ++kk) {
         const uint32_t ko = kk * 32;   // 16 BF16 = 32 bytes per MMA
 #pragma unroll
         for (int l = 0; l < OZ_S; ++l)
 #pragma unroll
           for (int a = 0; a <= l; ++a) {
-            const int b = l - a;
-            const uint32_t acc = (kc > 0 || kk > 0 || a > 0) ? 1u : 0u;
-            tc::mma_f16(tmem + l * OZ_N, tc::sw128_desc(tc::smem_u32(sA + a * OZ_A_BYTES) + ko),
-                        tc::sw128_desc(tc::smem_u32(sB + b * OZ_B_BYTES) + ko), idesc, acc);
+            const uint32_t acc = (c > 0 || kk > 0 || a > 0) ? 1u : 0u;
+            tc::mma_f16(tmem + l * Z_N, tc::sw64_desc(aB + a * Z_A + ko),
+                        tc::sw64_desc(bB + (l - a) * Z_B + ko), idesc, acc);
           }
       }
-      tc::commit(&mbar[0]);
-    }
-  }
-  tc::mbar_wait(&mbar[0], phase, WAIT_LIMIT) ? (void)0 : (void)(ok = 0);
-  ok = __syncthreads_and(ok);
-  tc::fence_after();
-  if (ok) {
-    const int jl = warp * 32 + lane;
-    const int j = j0 + jl;
-    const int fj = j < m ? fA[j] : 0;
-#pragma unroll
-    for (int c16 = 0; c16 < OZ_N / 16; ++c16) {
-      // levels are exact integers below 2^24 (level l has <= l + 1 digit
-      // pairs): combine them exactly in two int64 halves,
-      //   hi = sum_{l < H} T_l 2^(7 (H-1-l)),  lo = sum_{l >= H} T_l 2^(7 (S-1-l)),
-      // sum_l T_l 2^(-7 l) = 2^(-7 (S-1)) (hi 2^(7 (S-H)) + lo)
-      constexpr int H = OZ_S / 2;
-      long long hi[16], lo[16];
-#pragma unroll
-      for (int e = 0; e < 16; ++e) hi[e] = lo[e] = 0;
-#pragma unroll
-      for (int l = 0; l < OZ_S; ++l) {
-        uint32_t v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + l * OZ_N + c16 * 16, v);
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const long long t = (long long)__float2int_rz(__uint_as_float(v[e]));
-          if (l < H) hi[e] = hi[e] * 128 + t;
-          else lo[e] = lo[e] * 128 + t;
+      tc::commit(&empty[st]);
+      if (c + 2 < nch) {
+        if (!tc::mbar_wait(&empty[st], ph, WAIT_LIMIT)) {
+          ok = 0;
+          break;
         }
+        issue(c + 2);
       }
-      double acc[16];
+    }
+    tc::commit(done);   // arrives once every MMA issued above has completed
+    // after a timeout, let the loads still in flight land before the CTA
+    // leaves (bounded as well)
+    for (int c = consumed; c < issued; ++c)
+      tc::mbar_wait(&full[c & 1], (uint32_t)((c >> 1) & 1), WAIT_LIMIT);
+  }
+  __syncthreads();
+  int fin = tc::mbar_wait(done, 0, WAIT_LIMIT) ? 1 : 0;
+  fin = __syncthreads_and(fin && (tid != 0 || ok));
+  tc::fence_after();
+  if (fin) {
+    const int j = j0 + warp * 32 + lane;
+    int* Pz = P + (long long)z * OZ_S * m * R;
+    const bool vec = (R & 3) == 0;   // rows 16-byte aligned
+#pragma unroll 1
+    for (int l = 0; l < OZ_S; ++l) {
 #pragma unroll
-      for (int e = 0; e < 16; ++e)
-        acc[e] = fma((double)hi[e], (double)(1LL << (7 * (OZ_S - H))), (double)lo[e]);
-      if (j < m) {
+      for (int c16 = 0; c16 < Z_N / 16; ++c16) {
+        uint32_t v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + l * Z_N + c16 * 16, v);
+        const long long rc = r0 + c16 * 16;
+        if (j < m) {
+          int* row = Pz + ((long long)l * m + j) * R + rc;
+          if (vec && rc + 16 <= R) {
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int rl = c16 * 16 + e;
-          const long long r = r0 + rl;
-          // Y = scale acc 2^(fA + eB - 2 P + 7 (S - 1)); power of two from its bits
-          const int ex = fj + eB[rl] - 2 * OZ_P + 7 * (OZ_S - 1);
-          const double p2 = ex > -1023 ? __longlong_as_double((long long)(ex + 1023) << 52) : 0.0;
-          if (r < R) Yq[(long long)j * R + r] = scale * ((double)acc[e] * p2);
+            for (int e = 0; e < 16; e += 4)
+              *reinterpret_cast<int4*>(row + e) =
+                  make_int4(__float2int_rz(__uint_as_float(v[e])),
+                            __float2int_rz(__uint_as_float(v[e + 1])),
+                            __float2int_rz(__uint_as_float(v[e + 2])),
+                            __float2int_rz(__uint_as_float(v[e + 3])));
+          } else {
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+              if (rc + e < R) row[e] = __float2int_rz(__uint_as_float(v[e]));
+          }
         }
       }
     }
@@ -460,7 +450,33 @@ __global__ void __launch_bounds__(128) k_mode_tc_oz(const uint16_t* __restrict__
   }
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, OZ_TMEM_COLS);
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+// Y[q][j][r] = scale 2^(fA_j + eB_qr - 2 P + 7 (S - 1)) sum_l 2^(7 (S-1-l)) sum_split T_l,
+// the level sums combined exactly in two int64 halves.
+__global__ void k_oz_combine(const int* __restrict__ P, const int* __restrict__ fA,
+                             const int* __restrict__ eB, double* __restrict__ Y, int m,
+                             long long R, int KS, int s, double scale) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per = (long long)m * R;
+  if (idx >= per * s) return;
+  const long long q = idx / per, jr = idx % per;
+  const int j = (int)(jr / R);
+  const long long r = jr % R;
+  constexpr int H = OZ_S / 2;
+  long long hi = 0, lo = 0;
+#pragma unroll
+  for (int l = 0; l < OZ_S; ++l) {
+    long long t = 0;
+    for (int k = 0; k < KS; ++k) t += P[(((q * KS + k) * OZ_S + l) * m) * R + jr];
+    if (l < H) hi = hi * 128 + t;
+    else lo = lo * 128 + t;
+  }
+  const double acc = fma((double)hi, (double)(1LL << (7 * (OZ_S - H))), (double)lo);
+  const int ex = fA[j] + eB[q * R + r] - 2 * OZ_P + 7 * (OZ_S - 1);
+  const double p2 = ex > -1023 ? __longlong_as_double((long long)(ex + 1023) << 52) : 0.0;
+  Y[q * per + jr] = scale * (acc * p2);
 }
 
 }  // namespace
@@ -472,12 +488,52 @@ int oz_slice_factor(dski_handle h, const double* K, int m, uint16_t* Ad, int* fA
   return DSKI_OK;
 }
 
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult qr{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &qr) == cudaSuccess &&
+        qr == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// BF16 digit planes as a TMA tensor: dims (innermost first) and byte
+// strides of the outer dims; box Z_KC x rows x 1 (x 1), 64-byte swizzle.
+static int encode_digits(CUtensorMap* map, const void* base, int rank, const cuuint64_t* dims,
+                         const cuuint64_t* strides, cuuint32_t box_rows) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return set_error(DSKI_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  cuuint32_t box[4] = {(cuuint32_t)Z_KC, box_rows, 1, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank,
+                         const_cast<void*>(base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(DSKI_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return DSKI_OK;
+}
+
 int mode_tc_oz(dski_handle h, const double* X, const uint16_t* Ad, const int* fA, double* Y,
                int m, long long R, int s, double scale) {
   if (m % 8 != 0 || m > 256)
     return set_error(DSKI_ERR_ARG, "FP64_TC mode products need m_k %% 8 == 0 and m_k <= 256 (got %d)", m);
   const long long rows = (long long)s * R;
-  if (h->ozB.ensure((size_t)rows * m * OZ_S * 2) || h->ozE.ensure((size_t)rows * 4))
+  // contraction split: up to 4 splits of >= 64 (whole 32-wide chunks each)
+  int KS = std::max(1, std::min(4, m / 64)), kper = m;
+  for (;; --KS) {   // every split must start inside [0, m)
+    kper = ((m + KS - 1) / KS + Z_KC - 1) / Z_KC * Z_KC;
+    if (KS == 1 || (long long)(KS - 1) * kper < m) break;
+  }
+  if (h->ozB.ensure((size_t)rows * m * OZ_S * 2) || h->ozE.ensure((size_t)rows * 4) ||
+      h->ozP.ensure((size_t)s * KS * OZ_S * m * R * 4))
     return set_error(DSKI_ERR_ALLOC, "FP64_TC digit workspace allocation failed");
   {
     StageScope sc(h, ST_KRON, h->stream);
@@ -485,15 +541,32 @@ int mode_tc_oz(dski_handle h, const double* X, const uint16_t* Ad, const int* fA
         X, R, m, rows, h->ozB.as<uint16_t>(), h->ozE.as<int>());
   }
   DSKI_LAUNCHED();
+  CUtensorMap tA, tB;
+  {
+    const cuuint64_t dims[3] = {(cuuint64_t)m, (cuuint64_t)m, (cuuint64_t)OZ_S};
+    const cuuint64_t str[2] = {(cuuint64_t)m * 2, (cuuint64_t)m * m * 2};
+    DSKI_TRY(encode_digits(&tA, Ad, 3, dims, str, Z_M));
+  }
+  {
+    const cuuint64_t dims[4] = {(cuuint64_t)m, (cuuint64_t)R, (cuuint64_t)OZ_S, (cuuint64_t)s};
+    const cuuint64_t str[3] = {(cuuint64_t)m * 2, (cuuint64_t)R * m * 2,
+                               (cuuint64_t)OZ_S * R * m * 2};
+    DSKI_TRY(encode_digits(&tB, h->ozB.ptr, 4, dims, str, Z_N));
+  }
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_mode_tc_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+    cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, Z_SMEM);
     attr_set = true;
   }
-  dim3 grd((unsigned)((m + OZ_M - 1) / OZ_M), (unsigned)((R + OZ_N - 1) / OZ_N), (unsigned)s);
-  StageScope sc(h, ST_KRON, h->stream);
-  k_mode_tc_oz<<<grd, 128, OZ_SMEM, h->stream>>>(h->ozB.as<uint16_t>(), h->ozE.as<int>(), Ad, fA, Y,
-                                                 m, R, scale, h->dev_err.as<int>());
+  dim3 grd((unsigned)((m + Z_M - 1) / Z_M), (unsigned)((R + Z_N - 1) / Z_N), (unsigned)(s * KS));
+  {
+    StageScope sc(h, ST_KRON, h->stream, 2);
+    k_oz_gemm<<<grd, 128, Z_SMEM, h->stream>>>(tA, tB, h->ozP.as<int>(), m, R, KS, kper,
+                                                h->dev_err.as<int>());
+    const long long tot = (long long)s * m * R;
+    k_oz_combine<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(
+        h->ozP.as<int>(), fA, h->ozE.as<int>(), Y, m, R, KS, s, scale);
+  }
   DSKI_LAUNCHED();
   return DSKI_OK;
 }

@@ -670,7 +670,7 @@ int kron_internal(dski_handle h, void* g, void* tmp, int s, bool prec64, int dfa
     const long long R = h->M / h->m[k];
     const bool last = t == h->d - 1;
     const double scale = last ? h->sf * h->sf : 1.0;
-    if (prec64 && h->prec == DSKI_FP64_TC && dfactor < 0) {
+    if (prec64 && h->prec == DSKI_FP64_TC && dfactor < 0 && !h->kron_exact) {
       DSKI_TRY(mode_tc_oz(h, (const double*)cur, h->Kdig[k].as<uint16_t>(), h->Kexp[k].as<int>(),
                           (double*)nxt, h->m[k], R, s, scale));
     } else if (prec64) {

@@ -20,6 +20,8 @@
 // iteration runs in FP32 / (3x)TF32 on a float copy of p while x, r, z and
 // every scalar stay FP64; the inner solve then targets a reduction of 1e-4
 // of the residual it restarted from, and the FP64 true residual refines x.
+// In FP64_TC the inner MVM takes the tensor-core mode products and the true
+// residual the FP64-unit ones.
 //
 // The first `depth` alpha_j, beta_j of each column are recorded: CG on
 // K~ x = z with preconditioner M is the Lanczos process on
@@ -408,7 +410,12 @@ int cg_run(dski_handle h, CgRun& run) {
     return DSKI_OK;
   };
   auto true_residual = [&](int first) -> int {
-    DSKI_TRY(mvm_internal(h, run.X, Q, s, true));
+    // FP64_TC: the true residual takes the FP64-unit mode products, so the
+    // restarts refine x against the FP64 operator
+    h->kron_exact = true;
+    const int mrc = mvm_internal(h, run.X, Q, s, true);
+    h->kron_exact = false;
+    DSKI_TRY(mrc);
     StageScope sc(h, ST_PCGVEC, st);
     k_cg_init<<<grd, CG_THREADS, 0, st>>>(run.B, Q, R, Y, dis, N, first, tol2, eta2, cs, part,
                                           tk);
