@@ -153,10 +153,7 @@ static void release_all(dski_handle h) {
   h->vout.release();
   h->scratch.release();
   h->dev_err.release();
-  h->ozB.release();
-  h->ozP.release();
   h->scat_ab.release();
-  h->ozE.release();
   h->s_part.release();
   h->s_tnpart.release();
   h->s_ticket.release();

@@ -104,9 +104,6 @@ struct dski_handle_ {
   dski::DevBuf dK64[DSKI_MAXD];
   // FP64_TC mode: eight BF16 digit planes of K_k (8 x m x m) and row exponents
   dski::DevBuf Kdig[DSKI_MAXD], Kexp[DSKI_MAXD];
-  // FP64_TC: digit planes and row exponents of the grid operand, int32 level
-  // partials of the split contraction (workspace)
-  dski::DevBuf ozB, ozE, ozP;
   // FP64 scatter: per-point sum-factorised coefficients (workspace)
   dski::DevBuf scat_ab;
   // workspace
@@ -165,7 +162,8 @@ int gather_internal(dski_handle h, const void* grid, const void* vin, void* vout
 // tensor-core mode product (kron_tc.cu): TF32 (three = false) or 3xTF32
 int mode_tc_tf32(dski_handle h, const float* X, const float* Khi, const float* Klo, float* Y,
                  int m, long long R, int s, float scale, bool three);
-// FP64_TC mode products (kron_tc.cu): digits of a factor, and one mode product;
+// FP64_TC mode products (kron_tc.cu): digits and row exponents of a factor,
+// and one mode product;
 // a factor's digit planes take kOzDigits x m x m BF16 values
 constexpr int kOzDigits = 8;
 int oz_slice_factor(dski_handle h, const double* K, int m, uint16_t* Ad, int* fA);

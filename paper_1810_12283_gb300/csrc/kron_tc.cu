@@ -208,26 +208,53 @@ namespace {
 // ---------------------------------------------------------------------------
 // FP64-accurate mode products on the BF16 tensor cores (DSKI_FP64_TC).
 //
-// Both operands are split into S = 8 signed 7-bit digits relative to a
-// per-row power of two (Ozaki-style splitting): for a row with max |x| <
-// 2^e, x = 2^e sum_b d_b 2^(-6 - 7 b) up to rounding at 2^(e - 55), d_b
-// integers in [-64, 64] (exact in BF16), extracted with integer arithmetic.
-// A product of digits is at most 2^12 in magnitude and a sum of m <= 256 of
-// them, over the <= 8 digit pairs (a, b) of one level a + b, stays within
-// 2^23, so every level accumulates EXACTLY in the FP32 TMEM accumulator.
-// Levels 0..S-1 are kept (one TMEM accumulator each) and combined in FP64:
-//   Y[j][r] = 2^(fA_j + eB_r - 12) sum_l 2^(-7 l) T_l[j][r],
-// (summed exactly in two int64 halves), which drops only the digit pairs of
-// weight < 2^(-7 S) -- a relative error of about 2^-53 of |K| |X|, at FP64
-// rounding in the 256-term sums (the FP32 product misses by 2^-24, 26x the
-// noise variance on the terrain grid).
-// K's digits are made once per factor; X's digits by a row-parallel kernel
-// before each mode product.
+// Operands are split into S = 8 signed digits relative to a per-row power
+// of two (Ozaki-style splitting): for a row with max |x| < 2^e,
+// x = 2^(e - P) V with the integer V = round(x 2^(P - e)), |V| < 2^P, P = 62,
+// and V = sum_b d_b 2^(8 (S - 1 - b)), |d_0| <= 64, |d_b| <= 128: integers
+// exact in BF16, extracted with integer arithmetic on the FP64 bit pattern
+// (GB300's FP64 units are ~60x slower than its integer and FP32 units).  A
+// digit product is at most 2^14; one CTA contracts 32 terms, so a level sum
+//   T_l = sum_{a + b = l} sum_i A_a[j][i] B_b[r][i]   (at most 8 digit pairs)
+// stays below 2^22 and accumulates EXACTLY in its FP32 TMEM accumulator.
+// Levels 0..S-1 are kept:
+//   Y[j][r] = 2^(fA_j + eB_r - 2 P + 8 (S - 1)) sum_l 2^(8 (S - 1 - l)) T_l,
+// exact up to the dropped pairs (weight < 2^(-8 S) of the leading term) and
+// the operands' rounding to 62 bits of their row maxima: FP64-class accuracy
+// (the FP32 product misses by 2^-24, 26x the noise variance on the terrain
+// grid).  K's digits are made once per factor.
+//
+// One kernel per mode product.  CTA (j tile of 128, r tile of 32, column q,
+// contraction split ks of 32); the KS splits of one output tile form a
+// thread-block cluster.
+//   1. TMA brings K's 8 digit planes of the split (64-byte swizzled rows);
+//      meanwhile the threads load the split's 32 x 32 slice of X (FP64) and
+//      its per-row maximum exponent.
+//   2. Cluster barrier; every CTA takes the row maxima over the whole
+//      contraction from the cluster's shared memories (distributed shared
+//      memory) and writes its slice's digits, 64-byte swizzled, as the B
+//      operand.
+//   3. One thread issues the 36 digit-pair MMAs per 16-deep step into 8 TMEM
+//      level accumulators.
+//   4. Each thread folds its row's levels into an exact int64 pair (hi, lo)
+//      and stages it; after a cluster barrier every CTA sums a 1/KS share of
+//      the tile over the cluster (fixed order: deterministic) and writes FP64.
 constexpr int OZ_S = kOzDigits;                  // digits per operand (8)
-constexpr int OZ_P = 6 + 7 * (OZ_S - 1);         // fixed-point bits: |V| < 2^OZ_P
-static_assert(OZ_P <= 62 && OZ_P - 53 <= 8, "fixed-point range");
-// exactness of one level: at most OZ_S digit pairs of 64 x 64, over K <= 256 terms
-static_assert((long long)OZ_S * 256 * 64 * 64 <= (1LL << 24), "FP32 level sums must stay exact");
+constexpr int OZ_P = 6 + 8 * (OZ_S - 1);         // fixed-point bits: |V| < 2^OZ_P
+static_assert(OZ_P <= 62, "fixed-point range");
+constexpr int Z_M = 128, Z_N = 32, Z_KC = 32;    // tile rows, tile columns, split depth
+constexpr int Z_A = Z_M * 64;                     // one A digit plane: 128 rows x 64 B
+constexpr int Z_B = Z_N * 64;                     // one B digit plane: 32 rows x 64 B
+constexpr int Z_STAGE = OZ_S * (Z_A + Z_B);       // 80 KB of operands
+constexpr int Z_ROW = Z_N * 16 + 16;              // staged (hi, lo) row, padded
+static_assert(Z_M * Z_ROW <= Z_STAGE, "staging reuses the operand buffers");
+constexpr int Z_EXP = Z_STAGE;                    // 2 x 32 ints: row maxima (partial, full)
+constexpr int Z_BAR = Z_STAGE + 256;
+constexpr int Z_SMEM = Z_STAGE + 256 + 64 + 1024;
+constexpr int Z_MAXKS = 8;                        // portable cluster size
+static_assert(OZ_S * Z_N <= 256, "TMEM columns");
+// exactness of one level: at most OZ_S digit pairs of 2^14 over Z_KC terms
+static_assert((long long)OZ_S * Z_KC * 128 * 128 < (1LL << 24), "FP32 level sums must stay exact");
 
 // Biased exponent field of |x| (0 for zero and subnormals).
 __device__ __forceinline__ int exp_field(double x) {
@@ -235,8 +262,7 @@ __device__ __forceinline__ int exp_field(double x) {
 }
 
 // V = round(x 2^(OZ_P - e)) as an integer (|V| < 2^OZ_P when |x| < 2^e), from
-// the bit pattern alone: GB300's FP64 units are ~60x slower than its
-// integer and FP32 units, so the splitting avoids FP64 arithmetic.
+// the bit pattern alone.
 __device__ __forceinline__ long long fixedP(double x, int e) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const int E = (int)((u >> 52) & 0x7FF);
@@ -251,29 +277,24 @@ __device__ __forceinline__ long long fixedP(double x, int e) {
   return (u >> 63) ? -v : v;
 }
 
-// OZ_S signed 7-bit digits of V (weights 2^(7 (S-1)), ..., 2^7, 2^0), each
-// in [-64, 64]: round-to-nearest at every step leaves |remainder| <= 2^(k-1).
-__device__ __forceinline__ void digitsS(long long V, float (&d)[OZ_S]) {
+// The OZ_S digits of V as BF16 bit patterns: round-to-nearest at every step
+// leaves |remainder| <= 2^(k-1), so every digit after the first is in
+// [-128, 128] (the first in [-64, 64]); all are integers exact in BF16.
+__device__ __forceinline__ void digits_bf16(long long V, uint16_t (&d)[OZ_S]) {
 #pragma unroll
   for (int b = 0; b < OZ_S - 1; ++b) {
-    const int k = 7 * (OZ_S - 1 - b);
+    const int k = 8 * (OZ_S - 1 - b);
     const long long q = (V + (1LL << (k - 1))) >> k;
-    d[b] = (float)(int)q;
+    d[b] = (uint16_t)(__float_as_uint((float)(int)q) >> 16);
     V -= q << k;
   }
-  d[OZ_S - 1] = (float)(int)V;
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-  // exact: a, b are integers in [-64, 64]
-  const uint32_t ua = __float_as_uint(a) >> 16, ub = __float_as_uint(b) >> 16;
-  return ua | (ub << 16);
+  d[OZ_S - 1] = (uint16_t)(__float_as_uint((float)(int)V) >> 16);
 }
 
 // Digits of K (m x m, row-major): Ad[b][j][i] (BF16 bits) and fA[j] with
 // max_i |K[j][i]| < 2^fA[j].  One thread per row.
-__global__ void k_oz_slice_factor(const double* __restrict__ K, int m,
-                                  uint16_t* __restrict__ Ad, int* __restrict__ fA) {
+__global__ void k_oz_slice_factor(const double* __restrict__ K, int m, uint16_t* __restrict__ Ad,
+                                  int* __restrict__ fA) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= m) return;
   int E = 0;
@@ -281,109 +302,134 @@ __global__ void k_oz_slice_factor(const double* __restrict__ K, int m,
   const int e = E - 1022;   // max |K[j][:]| < 2^e
   fA[j] = e;
   for (int i = 0; i < m; ++i) {
-    float d[OZ_S];
-    digitsS(fixedP(K[(long long)j * m + i], e), d);
+    uint16_t d[OZ_S];
+    digits_bf16(fixedP(K[(long long)j * m + i], e), d);
 #pragma unroll
-    for (int b = 0; b < OZ_S; ++b)
-      Ad[((long long)b * m + j) * m + i] = (uint16_t)(__float_as_uint(d[b]) >> 16);
+    for (int b = 0; b < OZ_S; ++b) Ad[((long long)b * m + j) * m + i] = d[b];
   }
 }
 
-// Digits of the rows of X (s grid columns, each R x m): Bd[q][b][r][i] (BF16
-// bits) and eB[q][r] with max_i |X_q[r][i]| < 2^eB.  One warp per row.
-__global__ void __launch_bounds__(256) k_oz_slice_rows(const double* __restrict__ X, long long R,
-                                                       int m, long long rows,
-                                                       uint16_t* __restrict__ Bd,
-                                                       int* __restrict__ eB) {
-  const long long gr = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // q R + r
-  const int lane = threadIdx.x & 31;
-  if (gr >= rows) return;   // whole warp
-  const long long q = gr / R, r = gr % R;
-  const double* xr = X + gr * m;
-  int E = 0;
-  for (int i = lane; i < m; i += 32) E = max(E, exp_field(xr[i]));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
-  const int e = E - 1022;
-  if (lane == 0) eB[gr] = e;
-  for (int i = lane; i < m; i += 32) {
-    float d[OZ_S];
-    digitsS(fixedP(xr[i], e), d);
-#pragma unroll
-    for (int b = 0; b < OZ_S; ++b)
-      Bd[((q * OZ_S + b) * R + r) * m + i] = (uint16_t)(__float_as_uint(d[b]) >> 16);
-  }
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+// address of the same shared-memory location in cluster CTA `rank`
+__device__ __forceinline__ uint32_t map_cluster(uint32_t saddr, uint32_t rank) {
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(saddr), "r"(rank));
+  return ra;
+}
+__device__ __forceinline__ int ld_cluster_s32(uint32_t a) {
+  int v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ longlong2 ld_cluster_pair(uint32_t a) {
+  longlong2 v;
+  asm volatile("ld.shared::cluster.v2.s64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "r"(a) : "memory");
+  return v;
 }
 
-// One split of the contraction: the exact FP32 level sums
-//   T_l[j][r] = sum_{a + b = l} sum_{i in split} A_a[j][i] B_b[r][i]
-// of a 128 x 32 output tile, written as int32 to P[q][split][l][j][r].  The
-// digit planes stream in by TMA (64-byte rows, 64-byte swizzle, box 32 wide)
-// through two stages; one thread issues the loads and the 36 MMAs per
-// 16-deep step; stages are recycled when their MMAs commit.  Splitting the
-// contraction over CTAs puts 64 CTAs on a 256 x 256 mode product.
-constexpr int Z_M = 128, Z_N = 32, Z_KC = 32;    // 32 BF16 = one 64-byte row
-constexpr int Z_A = Z_M * 64;                     // 8 KB per digit plane
-constexpr int Z_B = Z_N * 64;                     // 2 KB per digit plane
-constexpr int Z_STAGE = OZ_S * (Z_A + Z_B);       // 80 KB
-constexpr int Z_SMEM = 2 * Z_STAGE + 1024 + 128;
-static_assert(OZ_S * Z_N <= 256, "TMEM columns");
-
-__global__ void __launch_bounds__(128) k_oz_gemm(const __grid_constant__ CUtensorMap tA,
-                                                 const __grid_constant__ CUtensorMap tB,
-                                                 int* __restrict__ P, int m, long long R,
-                                                 int KS, int kper, int* __restrict__ err) {
+// Y_q[j][r] = scale sum_i K[j][i] X_q[r][i]; X: s columns of R x m (FP64,
+// row-major), Y: s columns of m x R.  Grid (m/128, R/32, s KS), cluster
+// (1, 1, KS), KS = ceil(m / 32) <= 8, 128 threads.
+__global__ void __launch_bounds__(128) k_oz_mode(const __grid_constant__ CUtensorMap tA,
+                                                 const double* __restrict__ X,
+                                                 const int* __restrict__ fA, double* __restrict__ Y,
+                                                 int m, long long R, int KS, double scale,
+                                                 int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(smem + 2 * Z_STAGE);
-  uint64_t* empty = full + 2;
-  uint64_t* done = full + 4;
-  uint32_t* tslot = (uint32_t*)(full + 5);
+  int* pmax = (int*)(smem + Z_EXP);        // this split's row maxima (exponent fields)
+  int* emax = pmax + Z_N;                  // over the whole contraction: e per row
+  uint64_t* full = (uint64_t*)(smem + Z_BAR);
+  uint64_t* done = full + 1;
+  uint32_t* tslot = (uint32_t*)(full + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int j0 = blockIdx.x * Z_M;
-  const int r0 = blockIdx.y * Z_N;
-  const int z = blockIdx.z, q = z / KS, ks = z % KS;
-  const int k_begin = ks * kper;
-  const int k_end = min(m, k_begin + kper);
-  const int nch = (k_end - k_begin + Z_KC - 1) / Z_KC;   // >= 1 by construction
+  const long long r0 = (long long)blockIdx.y * Z_N;
+  const int q = blockIdx.z / KS;
+  const uint32_t crank = cluster_rank();   // == blockIdx.z % KS: the contraction split
+  const int i0 = (int)crank * Z_KC;
 
   if (warp == 0) tc::tmem_alloc(tslot, 256);
   if (tid == 0) {
-    for (int i = 0; i < 5; ++i) tc::mbar_init(&full[i], 1);
+    tc::mbar_init(full, 1);
+    tc::mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *tslot;
-  constexpr uint32_t idesc = tc::instr_desc(tc::kFmtBF16, Z_M, Z_N);
+  if (tid == 0) {
+    tc::mbar_expect_tx(full, (uint32_t)(OZ_S * Z_A));
+    for (int b = 0; b < OZ_S; ++b) tc::tma_load_3d(smem + b * Z_A, &tA, i0, j0, b, full);
+  }
 
+  // 1. this thread's 8 operand values: row rr, columns i0 + 8 c .. + 7
+  const int rr = tid >> 2, c = tid & 3;
+  double xv[8];
+  {
+    const long long r = r0 + rr;
+    const int ib = i0 + 8 * c;
+    const bool in = r < R && ib < m;   // m % 8 == 0: a chunk is all in or all out
+    const double2* src = reinterpret_cast<const double2*>(X + ((long long)q * R + r) * m + ib);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const double2 t = in ? src[u] : make_double2(0.0, 0.0);
+      xv[2 * u] = t.x;
+      xv[2 * u + 1] = t.y;
+    }
+  }
+  int E = 0;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) E = max(E, exp_field(xv[u]));
+  E = max(E, __shfl_xor_sync(0xffffffffu, E, 1));
+  E = max(E, __shfl_xor_sync(0xffffffffu, E, 2));
+  if (c == 0) pmax[rr] = E;
+  cluster_sync();   // every split's row maxima are visible
+
+  // 2. row maxima over the contraction; the slice's digits as the B operand
+  const uint32_t sbase = tc::smem_u32(smem);
+  if (tid < Z_N) {
+    const uint32_t a = tc::smem_u32(pmax + tid);
+    int Em = 0;
+    for (int src = 0; src < KS; ++src) Em = max(Em, ld_cluster_s32(map_cluster(a, (uint32_t)src)));
+    emax[tid] = Em - 1022;   // max |X[r][:]| < 2^e
+  }
+  __syncthreads();
+  {
+    const int e = emax[rr];
+    uint16_t dg[8][OZ_S];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) digits_bf16(fixedP(xv[u], e), dg[u]);
+    unsigned char* bB = smem + OZ_S * Z_A;
+#pragma unroll
+    for (int b = 0; b < OZ_S; ++b) {
+      uint4 w;
+      w.x = (uint32_t)dg[0][b] | ((uint32_t)dg[1][b] << 16);
+      w.y = (uint32_t)dg[2][b] | ((uint32_t)dg[3][b] << 16);
+      w.z = (uint32_t)dg[4][b] | ((uint32_t)dg[5][b] << 16);
+      w.w = (uint32_t)dg[6][b] | ((uint32_t)dg[7][b] << 16);
+      *reinterpret_cast<uint4*>(bB + b * Z_B + tc::sw64_off(rr, c)) = w;
+    }
+  }
+  tc::fence_proxy_async();   // the digits are read by the tensor cores
+  __syncthreads();
+
+  // 3. the digit-pair MMAs
+  constexpr uint32_t idesc = tc::instr_desc(tc::kFmtBF16, Z_M, Z_N);
   int ok = 1;
   if (tid == 0) {
-    int issued = 0, consumed = 0;
-    auto issue = [&](int c) {
-      const int st = c & 1;
-      unsigned char* base = smem + st * Z_STAGE;
-      tc::mbar_expect_tx(&full[st], (uint32_t)Z_STAGE);
-      const int i0 = k_begin + c * Z_KC;
-      for (int b = 0; b < OZ_S; ++b) {
-        tc::tma_load_3d(base + b * Z_A, &tA, i0, j0, b, &full[st]);
-        tc::tma_load_4d(base + OZ_S * Z_A + b * Z_B, &tB, i0, r0, b, q, &full[st]);
-      }
-      issued = c + 1;
-    };
-    issue(0);
-    if (nch > 1) issue(1);
-    for (int c = 0; c < nch; ++c) {
-      const int st = c & 1;
-      const uint32_t ph = (uint32_t)((c >> 1) & 1);
-      if (!tc::mbar_wait(&full[st], ph, WAIT_LIMIT)) {
-        ok = 0;
-        break;
-      }
-      consumed = c + 1;
+    if (tc::mbar_wait(full, 0, WAIT_LIMIT)) {
       tc::fence_after();
-      const uint32_t aB = tc::smem_u32(smem + st * Z_STAGE);
+      const uint32_t aB = sbase;
       const uint32_t bB = aB + OZ_S * Z_A;
 #pragma unroll
       for (int kk = 0; kk < Z_KC / 16; ++kk) {
@@ -391,92 +437,100 @@ __global__ void __launch_bounds__(128) k_oz_gemm(const __grid_constant__ CUtenso
 #pragma unroll
         for (int l = 0; l < OZ_S; ++l)
 #pragma unroll
-          for (int a = 0; a <= l; ++a) {
-            const uint32_t acc = (c > 0 || kk > 0 || a > 0) ? 1u : 0u;
-            tc::mma_f16(tmem + l * Z_N, tc::sw64_desc(aB + a * Z_A + ko),
-                        tc::sw64_desc(bB + (l - a) * Z_B + ko), idesc, acc);
-          }
+          for (int p = 0; p <= l; ++p)
+            tc::mma_f16(tmem + l * Z_N, tc::sw64_desc(aB + p * Z_A + ko),
+                        tc::sw64_desc(bB + (l - p) * Z_B + ko), idesc, (kk > 0 || p > 0) ? 1u : 0u);
       }
-      tc::commit(&empty[st]);
-      if (c + 2 < nch) {
-        if (!tc::mbar_wait(&empty[st], ph, WAIT_LIMIT)) {
-          ok = 0;
-          break;
-        }
-        issue(c + 2);
-      }
+    } else {
+      ok = 0;
+      tc::mbar_wait(full, 0, WAIT_LIMIT);   // let the loads land (bounded) before reuse
     }
     tc::commit(done);   // arrives once every MMA issued above has completed
-    // after a timeout, let the loads still in flight land before the CTA
-    // leaves (bounded as well)
-    for (int c = consumed; c < issued; ++c)
-      tc::mbar_wait(&full[c & 1], (uint32_t)((c >> 1) & 1), WAIT_LIMIT);
   }
   __syncthreads();
   int fin = tc::mbar_wait(done, 0, WAIT_LIMIT) ? 1 : 0;
   fin = __syncthreads_and(fin && (tid != 0 || ok));
   tc::fence_after();
-  if (fin) {
-    const int j = j0 + warp * 32 + lane;
-    int* Pz = P + (long long)z * OZ_S * m * R;
-    const bool vec = (R & 3) == 0;   // rows 16-byte aligned
+
+  // 4. fold this thread's row into the exact pair
+  //   hi = sum_{l < S/2} T_l 2^(8 (S/2 - 1 - l)),  lo = sum_{l >= S/2} T_l 2^(8 (S - 1 - l))
+  // and stage it (row warp 32 + lane, 16 bytes per column)
+  {
+    constexpr int H = OZ_S / 2;
+    unsigned char* srow = smem + (warp * 32 + lane) * Z_ROW;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
-    for (int l = 0; l < OZ_S; ++l) {
+    for (int c16 = 0; c16 < Z_N / 16; ++c16) {
+      long long hi[16], lo[16];
+      uint32_t v[2][16];
+      tc::tmem_ld16_async(trow + c16 * 16, v[0]);
+      tc::tmem_wait_ld(v[0]);
 #pragma unroll
-      for (int c16 = 0; c16 < Z_N / 16; ++c16) {
-        uint32_t v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + l * Z_N + c16 * 16, v);
-        const long long rc = r0 + c16 * 16;
-        if (j < m) {
-          int* row = Pz + ((long long)l * m + j) * R + rc;
-          if (vec && rc + 16 <= R) {
+      for (int l = 0; l < OZ_S; ++l) {
+        // level l + 1 streams in while level l is folded
+        if (l + 1 < OZ_S) tc::tmem_ld16_async(trow + (l + 1) * Z_N + c16 * 16, v[(l + 1) & 1]);
 #pragma unroll
-            for (int e = 0; e < 16; e += 4)
-              *reinterpret_cast<int4*>(row + e) =
-                  make_int4(__float2int_rz(__uint_as_float(v[e])),
-                            __float2int_rz(__uint_as_float(v[e + 1])),
-                            __float2int_rz(__uint_as_float(v[e + 2])),
-                            __float2int_rz(__uint_as_float(v[e + 3])));
-          } else {
-#pragma unroll
-            for (int e = 0; e < 16; ++e)
-              if (rc + e < R) row[e] = __float2int_rz(__uint_as_float(v[e]));
-          }
+        for (int e = 0; e < 16; ++e) {
+          const long long t = fin ? (long long)__float2int_rz(__uint_as_float(v[l & 1][e])) : 0;
+          if (l == 0) hi[e] = t;
+          else if (l < H) hi[e] = hi[e] * 256 + t;
+          else if (l == H) lo[e] = t;
+          else lo[e] = lo[e] * 256 + t;
         }
+        if (l + 1 < OZ_S) tc::tmem_wait_ld(v[(l + 1) & 1]);
+      }
+#pragma unroll
+      for (int e = 0; e < 16; ++e)
+        *reinterpret_cast<longlong2*>(srow + (c16 * 16 + e) * 16) = make_longlong2(hi[e], lo[e]);
+    }
+  }
+  if (!fin && tid == 0) atomicExch(err, 1);
+  cluster_sync();   // every split's pairs are staged
+
+  // 5. this CTA's share of the tile (rows [rb, re), all columns), summed over
+  // the cluster in rank order
+  {
+    const int rb = (int)((crank * Z_M) / KS), re = (int)(((crank + 1) * Z_M) / KS);
+    uint32_t rbase[Z_MAXKS];
+#pragma unroll
+    for (int src = 0; src < Z_MAXKS; ++src) rbase[src] = src < KS ? map_cluster(sbase, src) : 0u;
+    const long long MR = (long long)m * R;
+    const int nit = (re - rb) * Z_N;
+    for (int it0 = 0; it0 < nit; it0 += 4 * 128) {
+      longlong2 pr[4][Z_MAXKS];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int it = it0 + k * 128 + tid;
+        const uint32_t off = it < nit ? (uint32_t)((rb + it / Z_N) * Z_ROW + (it % Z_N) * 16) : 0u;
+#pragma unroll
+        for (int src = 0; src < Z_MAXKS; ++src)
+          pr[k][src] = (src < KS && it < nit) ? ld_cluster_pair(rbase[src] + off) : make_longlong2(0, 0);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int it = it0 + k * 128 + tid;
+        if (it >= nit) continue;
+        long long hi = 0, lo = 0;
+#pragma unroll
+        for (int src = 0; src < Z_MAXKS; ++src) {
+          hi += pr[k][src].x;
+          lo += pr[k][src].y;
+        }
+        const int row = rb + it / Z_N, col = it % Z_N;
+        const int j = j0 + row;
+        const long long r = r0 + col;
+        if (j >= m || r >= R) continue;
+        const int ex = fA[j] + emax[col] - 2 * OZ_P + 8 * (OZ_S - 1);   // Y = (hi 2^32 + lo) 2^ex
+        const double v = fma((double)hi, 4294967296.0, (double)lo);
+        const double p2 = ex > -1023 ? __longlong_as_double((long long)(ex + 1023) << 52) : 0.0;
+        Y[(long long)q * MR + (long long)j * R + r] = scale * (v * p2);
       }
     }
-  } else if (tid == 0) {
-    atomicExch(err, 1);
   }
+  cluster_sync();   // the other CTAs have read this CTA's pairs
   tc::fence_before();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, 256);
-}
-
-// Y[q][j][r] = scale 2^(fA_j + eB_qr - 2 P + 7 (S - 1)) sum_l 2^(7 (S-1-l)) sum_split T_l,
-// the level sums combined exactly in two int64 halves.
-__global__ void k_oz_combine(const int* __restrict__ P, const int* __restrict__ fA,
-                             const int* __restrict__ eB, double* __restrict__ Y, int m,
-                             long long R, int KS, int s, double scale) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long per = (long long)m * R;
-  if (idx >= per * s) return;
-  const long long q = idx / per, jr = idx % per;
-  const int j = (int)(jr / R);
-  const long long r = jr % R;
-  constexpr int H = OZ_S / 2;
-  long long hi = 0, lo = 0;
-#pragma unroll
-  for (int l = 0; l < OZ_S; ++l) {
-    long long t = 0;
-    for (int k = 0; k < KS; ++k) t += P[(((q * KS + k) * OZ_S + l) * m) * R + jr];
-    if (l < H) hi = hi * 128 + t;
-    else lo = lo * 128 + t;
-  }
-  const double acc = fma((double)hi, (double)(1LL << (7 * (OZ_S - H))), (double)lo);
-  const int ex = fA[j] + eB[q * R + r] - 2 * OZ_P + 7 * (OZ_S - 1);
-  const double p2 = ex > -1023 ? __longlong_as_double((long long)(ex + 1023) << 52) : 0.0;
-  Y[q * per + jr] = scale * (acc * p2);
 }
 
 }  // namespace
@@ -505,69 +559,56 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// BF16 digit planes as a TMA tensor: dims (innermost first) and byte
-// strides of the outer dims; box Z_KC x rows x 1 (x 1), 64-byte swizzle.
-static int encode_digits(CUtensorMap* map, const void* base, int rank, const cuuint64_t* dims,
-                         const cuuint64_t* strides, cuuint32_t box_rows) {
-  auto enc = tensor_map_encoder();
-  if (!enc) return set_error(DSKI_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-  cuuint32_t box[4] = {(cuuint32_t)Z_KC, box_rows, 1, 1};
-  cuuint32_t estr[4] = {1, 1, 1, 1};
-  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank,
-                         const_cast<void*>(base), dims, strides, box, estr,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return set_error(DSKI_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-  return DSKI_OK;
-}
-
+// One mode product on the tensor cores (FP64_TC).  K's digit planes are a
+// 3-D TMA tensor (m x m x 8, innermost first), box 32 x 128 x 1 with 64-byte
+// swizzling.
 int mode_tc_oz(dski_handle h, const double* X, const uint16_t* Ad, const int* fA, double* Y,
                int m, long long R, int s, double scale) {
   if (m % 8 != 0 || m > 256)
     return set_error(DSKI_ERR_ARG, "FP64_TC mode products need m_k %% 8 == 0 and m_k <= 256 (got %d)", m);
-  const long long rows = (long long)s * R;
-  // contraction split: up to 4 splits of >= 64 (whole 32-wide chunks each)
-  int KS = std::max(1, std::min(4, m / 64)), kper = m;
-  for (;; --KS) {   // every split must start inside [0, m)
-    kper = ((m + KS - 1) / KS + Z_KC - 1) / Z_KC * Z_KC;
-    if (KS == 1 || (long long)(KS - 1) * kper < m) break;
-  }
-  if (h->ozB.ensure((size_t)rows * m * OZ_S * 2) || h->ozE.ensure((size_t)rows * 4) ||
-      h->ozP.ensure((size_t)s * KS * OZ_S * m * R * 4))
-    return set_error(DSKI_ERR_ALLOC, "FP64_TC digit workspace allocation failed");
-  {
-    StageScope sc(h, ST_KRON, h->stream);
-    k_oz_slice_rows<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, h->stream>>>(
-        X, R, m, rows, h->ozB.as<uint16_t>(), h->ozE.as<int>());
-  }
-  DSKI_LAUNCHED();
-  CUtensorMap tA, tB;
+  auto enc = tensor_map_encoder();
+  if (!enc) return set_error(DSKI_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  CUtensorMap tA;
   {
     const cuuint64_t dims[3] = {(cuuint64_t)m, (cuuint64_t)m, (cuuint64_t)OZ_S};
     const cuuint64_t str[2] = {(cuuint64_t)m * 2, (cuuint64_t)m * m * 2};
-    DSKI_TRY(encode_digits(&tA, Ad, 3, dims, str, Z_M));
-  }
-  {
-    const cuuint64_t dims[4] = {(cuuint64_t)m, (cuuint64_t)R, (cuuint64_t)OZ_S, (cuuint64_t)s};
-    const cuuint64_t str[3] = {(cuuint64_t)m * 2, (cuuint64_t)R * m * 2,
-                               (cuuint64_t)OZ_S * R * m * 2};
-    DSKI_TRY(encode_digits(&tB, h->ozB.ptr, 4, dims, str, Z_N));
+    const cuuint32_t box[3] = {(cuuint32_t)Z_KC, (cuuint32_t)Z_M, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = enc(&tA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(Ad),
+                           dims, str, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+      return set_error(DSKI_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   }
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, Z_SMEM);
+    cudaFuncSetAttribute(k_oz_mode, cudaFuncAttributeMaxDynamicSharedMemorySize, Z_SMEM);
     attr_set = true;
   }
-  dim3 grd((unsigned)((m + Z_M - 1) / Z_M), (unsigned)((R + Z_N - 1) / Z_N), (unsigned)(s * KS));
-  {
-    StageScope sc(h, ST_KRON, h->stream, 2);
-    k_oz_gemm<<<grd, 128, Z_SMEM, h->stream>>>(tA, tB, h->ozP.as<int>(), m, R, KS, kper,
-                                                h->dev_err.as<int>());
-    const long long tot = (long long)s * m * R;
-    k_oz_combine<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(
-        h->ozP.as<int>(), fA, h->ozE.as<int>(), Y, m, R, KS, s, scale);
-  }
-  DSKI_LAUNCHED();
+  const int KS = (m + Z_KC - 1) / Z_KC;   // <= 8 for m <= 256
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)((m + Z_M - 1) / Z_M), (unsigned)((R + Z_N - 1) / Z_N),
+                     (unsigned)(s * KS));
+  cfg.blockDim = dim3(128);
+  cfg.dynamicSmemBytes = Z_SMEM;
+  cfg.stream = h->stream;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = (unsigned)KS;
+  // let a cluster's CTAs share SMs, so that every cluster of a mode product
+  // can be resident at once
+  attr[1].id = cudaLaunchAttributeClusterSchedulingPolicyPreference;
+  attr[1].val.clusterSchedulingPolicyPreference = cudaClusterSchedulingPolicyLoadBalancing;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  StageScope sc(h, ST_KRON, h->stream);
+  if (cudaLaunchKernelEx(&cfg, k_oz_mode, tA, X, fA, Y, m, R, KS, scale, h->dev_err.as<int>()) !=
+      cudaSuccess)
+    return set_error(DSKI_ERR_CUDA, "FP64_TC mode product launch: %s",
+                     cudaGetErrorString(cudaGetLastError()));
   return DSKI_OK;
 }
 

@@ -160,6 +160,35 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// As tmem_ld16 without the wait: the registers are valid after tmem_wait_ld(v).
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+// Wait for the outstanding tcgen05.ld; v (the registers they write) is tied
+// to the wait so that no use of it is scheduled before.
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
+                 "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]),
+                 "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15])
+               :
+               : "memory");
+}
+
+// Byte offset of 16-byte chunk c (0..3) of row r in a 64B-swizzled K-major
+// tile (64-byte rows, 8-row atoms of 512 bytes): the chunk index is XORed
+// with bits 7-8 of the row's byte offset, i.e. (r / 2) mod 4 -- the layout
+// TMA writes with 64-byte swizzling and the tensor cores read.
+__device__ __forceinline__ uint32_t sw64_off(int r, int c) {
+  return (uint32_t)(r * 64 + ((c ^ ((r >> 1) & 3)) << 4));
+}
+
 // Byte offset of 16-byte chunk c (0..7) of row r in a 128B-swizzled K-major
 // tile: 8-row atoms of 1024 bytes, chunk index XOR (row mod 8).
 __device__ __forceinline__ uint32_t sw128_off(int r, int c) {
