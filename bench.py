@@ -54,6 +54,14 @@ def mvm_bytes(n, d, M, s, elem):
     return s * (3 * N * elem + 2 * M * elem) + 2 * geo
 
 
+def scatter_bytes(n, d, M, s, elem):
+    """HBM model of one scatter: v (N s elements) read, the per-point weight
+    table (8 d elements) and cell id (4 B) read, the grid (M s elements)
+    written."""
+    N = n * (d + 1)
+    return N * s * elem + n * (4 + 8 * d * elem) + M * s * elem
+
+
 def precond_bytes(N, r, s):
     """Algorithmic bytes of one preconditioner apply: Q1 (8 bytes per entry,
     FP64 or an FP32 hi/lo pair) read twice (Q1^T y, then y - Q1 c), r read
@@ -355,19 +363,26 @@ def main():
     st = {k: v for k, v in stages.items() if v[1]}
     per_launch_ms = {k: v[0] / max(v[2], 1) for k, v in st.items()}
     stage_total_ms = {k: per_launch_ms[k] * v[1] for k, v in st.items()}
-    # roofline of the dominant single kernel: the Kronecker mode product
-    # (k_mode_simt in FP64 mode, one launch per mode product; the ncu launch
-    # list ranks it first): 2 M m_k FP64 flops per launch on the FP64 units
-    per_launch_s = per_launch_ms["kron"] / 1e3
+    # roofline of the dominant kernel (the ncu launch list of this command
+    # ranks it first).  FP64: the Kronecker mode product k_mode_simt, one
+    # launch per mode product, 2 M m_k FP64 flops on the FP64 units.  FP64_TC
+    # and the mixed modes: the scatter's node pass k_scatter_ab, timed as one
+    # scatter (k_scatter_prep + k_scatter_ab, one stage scope of 2 launches)
+    # against the HBM model of one scatter (v read, per-point weights and
+    # cell ids read, grid written).
     if args.prec == "fp64":
+        per_s = per_launch_ms["kron"] / 1e3
         algo = 2 * M * p["m"][0]
-        achieved = algo / per_launch_s / 1e12
-        bound, unit, peak = "alu", "TFLOP/s", 1.25
+        achieved = algo / per_s / 1e12
+        kern, bound, unit, peak = "k_mode_simt (kron)", "alu", "TFLOP/s", 1.25
         peak_src = "nominal GB300 FP64 1.25 TFLOP/s (measured DGEMM 1.05)"
     else:
-        algo = 2 * M * 8
-        achieved = algo / per_launch_s / 1e9
-        bound, unit, peak, peak_src = "hbm", "GB/s", hbm, hbm_src
+        per_s = 2 * per_launch_ms["scatter"] / 1e3
+        elem = 8 if args.prec == "fp64_tc" else 4
+        algo = scatter_bytes(n, d, M, 1, elem)
+        achieved = algo / per_s / 1e9
+        kern, bound, unit, peak, peak_src = ("k_scatter_prep + k_scatter_ab (scatter)", "hbm",
+                                             "GB/s", hbm, hbm_src + " HBM copy bandwidth")
     line = {
         "metric": METRIC, "value": t_step, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
@@ -382,7 +397,7 @@ def main():
         "stage_us_per_launch": {k: round(1e3 * v, 2) for k, v in per_launch_ms.items()},
         "stage_launches": {k: v[1] for k, v in st.items()},
         "mvm": mvm,
-        "roofline": {"kernel": "k_mode_simt (kron)", "bound": bound, "achieved": achieved,
+        "roofline": {"kernel": kern, "bound": bound, "achieved": achieved,
                      "peak": peak, "peak_source": peak_src, "unit": unit,
                      "frac": achieved / peak, "traffic": None, "algo_per_launch": algo},
         "e2e": {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": (n * d + N) * 8,

@@ -154,6 +154,7 @@ static void release_all(dski_handle h) {
   h->scratch.release();
   h->dev_err.release();
   h->scat_ab.release();
+  h->ozP.release();
   h->s_part.release();
   h->s_tnpart.release();
   h->s_ticket.release();

@@ -104,6 +104,8 @@ struct dski_handle_ {
   dski::DevBuf dK64[DSKI_MAXD];
   // FP64_TC mode: eight BF16 digit planes of K_k (8 x m x m) and row exponents
   dski::DevBuf Kdig[DSKI_MAXD], Kexp[DSKI_MAXD];
+  // FP64_TC: split-K partial sums of the mode products (workspace)
+  dski::DevBuf ozP;
   // FP64 scatter: per-point sum-factorised coefficients (workspace)
   dski::DevBuf scat_ab;
   // workspace
@@ -169,6 +171,30 @@ constexpr int kOzDigits = 8;
 int oz_slice_factor(dski_handle h, const double* K, int m, uint16_t* Ad, int* fA);
 int mode_tc_oz(dski_handle h, const double* X, const uint16_t* Ad, const int* fA, double* Y,
                int m, long long R, int s, double scale);
+// General FP64-accurate product on the tensor cores:
+//   Y_q[j][r] = scale sum_i A[j][i] xs_q[i] X_q[r][i]   (ytrans: Y_q[r][j])
+// A: Mrows x mp as digit planes Ad (oz_slice) with row exponents fA; X_q:
+// R rows of stride ldx (FP64, zero beyond the contraction), X_q = X + q xq;
+// xs optional (xs_q = xs + q xsq, zero at i >= xsn); mp % 8 == 0, mp <= 256.
+struct OzGemm {
+  const uint16_t* Ad = nullptr;
+  const int* fA = nullptr;
+  int Mrows = 0, mp = 0;
+  const double* X = nullptr;
+  long long ldx = 0, xq = 0, R = 0;
+  const double* xs = nullptr;
+  long long xsq = 0;
+  int xsn = 0;
+  double* Y = nullptr;
+  bool ytrans = false;
+  double scale = 1.0;
+  int s = 1;
+  dski::DevBuf* workspace = nullptr;   // default: the handle's
+};
+int oz_gemm(dski_handle h, const OzGemm& g, int stage);
+// digits of A (rows x cols, row stride lda) into Ad (row stride mp, zero padded)
+int oz_slice(dski_handle h, const double* A, int rows, int cols, int lda, int mp, uint16_t* Ad,
+             int* fA, int stage);
 // vectors of this handle are double (FP64, FP64_TC) or float (MIXED modes)
 inline bool f64_vectors(dski_handle h) { return h->prec == DSKI_FP64 || h->prec == DSKI_FP64_TC; }
 // read and clear the device error word: DSKI_OK, or DSKI_ERR_TIMEOUT if a

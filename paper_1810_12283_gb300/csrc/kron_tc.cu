@@ -237,8 +237,10 @@ namespace {
 //   3. One thread issues the 36 digit-pair MMAs per 16-deep step into 8 TMEM
 //      level accumulators.
 //   4. Each thread folds its row's levels into an exact int64 pair (hi, lo)
-//      and stages it; after a cluster barrier every CTA sums a 1/KS share of
-//      the tile over the cluster (fixed order: deterministic) and writes FP64.
+//      and writes it to an L2-resident workspace; after a cluster barrier
+//      every CTA sums a 1/KS share of the tile over the splits (fixed order:
+//      deterministic) and writes FP64.  (Reading the pairs from the other
+//      CTAs' shared memory instead ran at ~10 B/clock per SM.)
 constexpr int OZ_S = kOzDigits;                  // digits per operand (8)
 constexpr int OZ_P = 6 + 8 * (OZ_S - 1);         // fixed-point bits: |V| < 2^OZ_P
 static_assert(OZ_P <= 62, "fixed-point range");
@@ -246,12 +248,12 @@ constexpr int Z_M = 128, Z_N = 32, Z_KC = 32;    // tile rows, tile columns, spl
 constexpr int Z_A = Z_M * 64;                     // one A digit plane: 128 rows x 64 B
 constexpr int Z_B = Z_N * 64;                     // one B digit plane: 32 rows x 64 B
 constexpr int Z_STAGE = OZ_S * (Z_A + Z_B);       // 80 KB of operands
-constexpr int Z_ROW = Z_N * 16 + 16;              // staged (hi, lo) row, padded
-static_assert(Z_M * Z_ROW <= Z_STAGE, "staging reuses the operand buffers");
+constexpr int Z_TILE = Z_M * Z_N;                 // (hi, lo) pairs per split of a tile
 constexpr int Z_EXP = Z_STAGE;                    // 2 x 32 ints: row maxima (partial, full)
 constexpr int Z_BAR = Z_STAGE + 256;
 constexpr int Z_SMEM = Z_STAGE + 256 + 64 + 1024;
 constexpr int Z_MAXKS = 8;                        // portable cluster size
+constexpr float Z_MAGIC = 12582912.0f;            // 1.5 2^23: t + Z_MAGIC has bits 0x4B400000 + t
 static_assert(OZ_S * Z_N <= 256, "TMEM columns");
 // exactness of one level: at most OZ_S digit pairs of 2^14 over Z_KC terms
 static_assert((long long)OZ_S * Z_KC * 128 * 128 < (1LL << 24), "FP32 level sums must stay exact");
@@ -277,35 +279,71 @@ __device__ __forceinline__ long long fixedP(double x, int e) {
   return (u >> 63) ? -v : v;
 }
 
-// The OZ_S digits of V as BF16 bit patterns: round-to-nearest at every step
-// leaves |remainder| <= 2^(k-1), so every digit after the first is in
-// [-128, 128] (the first in [-64, 64]); all are integers exact in BF16.
+// The OZ_S balanced base-256 digits of V (|V| < 2^62) as BF16 bit patterns:
+// the bytes of V + 0x8080...80, each minus 128, so d_b in [-128, 127] (the
+// first in [-64, 63]) and V = sum_b d_b 2^(8 (S - 1 - b)) exactly.  Every
+// digit is independent of the others (no carry chain), and its BF16 value
+// comes from one exact FP32 add: 0x4B400000 + d is the bit pattern of
+// 1.5 2^23 + d.
 __device__ __forceinline__ void digits_bf16(long long V, uint16_t (&d)[OZ_S]) {
+  static_assert(OZ_S == 8, "one byte per digit of a 64-bit word");
+  const unsigned long long u = (unsigned long long)V + 0x8080808080808080ULL;
+  const uint32_t w[2] = {(uint32_t)(u >> 32), (uint32_t)u};
 #pragma unroll
-  for (int b = 0; b < OZ_S - 1; ++b) {
-    const int k = 8 * (OZ_S - 1 - b);
-    const long long q = (V + (1LL << (k - 1))) >> k;
-    d[b] = (uint16_t)(__float_as_uint((float)(int)q) >> 16);
-    V -= q << k;
+  for (int b = 0; b < OZ_S; ++b) {
+    const uint32_t byte = (w[b >> 2] >> (8 * (3 - (b & 3)))) & 255u;
+    const float f = __uint_as_float(0x4B400000u - 128u + byte) - Z_MAGIC;   // = byte - 128
+    d[b] = (uint16_t)(__float_as_uint(f) >> 16);
   }
-  d[OZ_S - 1] = (uint16_t)(__float_as_uint((float)(int)V) >> 16);
 }
 
-// Digits of K (m x m, row-major): Ad[b][j][i] (BF16 bits) and fA[j] with
-// max_i |K[j][i]| < 2^fA[j].  One thread per row.
-__global__ void k_oz_slice_factor(const double* __restrict__ K, int m, uint16_t* __restrict__ Ad,
-                                  int* __restrict__ fA) {
+// The double nearest (ties away from zero) to (hi 2^32 + lo) 2^ex, by integer
+// operations only (GB300's FP64 units are the scarce resource here).
+__device__ __forceinline__ double exact_to_double(long long hi, long long lo, int ex) {
+  const __int128 W = ((__int128)hi << 32) + (__int128)lo;
+  if (W == 0) return 0.0;
+  const unsigned long long sgn = W < 0 ? (1ULL << 63) : 0ULL;
+  unsigned __int128 A = W < 0 ? (unsigned __int128)(-W) : (unsigned __int128)W;
+  const unsigned long long a1 = (unsigned long long)(A >> 64), a0 = (unsigned long long)A;
+  const int nb = a1 ? 128 - __clzll((long long)a1) : 64 - __clzll((long long)a0);
+  unsigned long long mant;
+  int e2;
+  if (nb > 53) {
+    const int sh = nb - 53;
+    A = (A + ((unsigned __int128)1 << (sh - 1))) >> sh;
+    mant = (unsigned long long)A;
+    e2 = ex + sh;
+    if (mant >> 53) {   // rounding carried into a new bit
+      mant >>= 1;
+      ++e2;
+    }
+  } else {
+    mant = (unsigned long long)A << (53 - nb);
+    e2 = ex - (53 - nb);
+  }
+  const long long be = (long long)e2 + 52 + 1023;   // value = mant 2^e2, mant in [2^52, 2^53)
+  if (be <= 0) return 0.0;                          // below the normal range
+  if (be >= 2047) return __longlong_as_double((long long)(sgn | (0x7FFULL << 52)));
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) |
+                                          (mant & ((1ULL << 52) - 1))));
+}
+
+// Digits of A (rows x cols, row stride lda): Ad[b][j][i] (BF16 bits, row
+// stride mp >= cols, zero beyond cols) and fA[j] with max_i |A[j][i]| <
+// 2^fA[j].  One thread per row.
+__global__ void k_oz_slice_factor(const double* __restrict__ A, int rows, int cols, int lda, int mp,
+                                  uint16_t* __restrict__ Ad, int* __restrict__ fA) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= m) return;
+  if (j >= rows) return;
   int E = 0;
-  for (int i = 0; i < m; ++i) E = max(E, exp_field(K[(long long)j * m + i]));
-  const int e = E - 1022;   // max |K[j][:]| < 2^e
+  for (int i = 0; i < cols; ++i) E = max(E, exp_field(A[(long long)j * lda + i]));
+  const int e = E - 1022;   // max |A[j][:]| < 2^e
   fA[j] = e;
-  for (int i = 0; i < m; ++i) {
+  for (int i = 0; i < mp; ++i) {
     uint16_t d[OZ_S];
-    digits_bf16(fixedP(K[(long long)j * m + i], e), d);
+    digits_bf16(i < cols ? fixedP(A[(long long)j * lda + i], e) : 0LL, d);
 #pragma unroll
-    for (int b = 0; b < OZ_S; ++b) Ad[((long long)b * m + j) * m + i] = d[b];
+    for (int b = 0; b < OZ_S; ++b) Ad[((long long)b * rows + j) * mp + i] = d[b];
   }
 }
 
@@ -329,20 +367,38 @@ __device__ __forceinline__ int ld_cluster_s32(uint32_t a) {
   asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
   return v;
 }
-__device__ __forceinline__ longlong2 ld_cluster_pair(uint32_t a) {
-  longlong2 v;
-  asm volatile("ld.shared::cluster.v2.s64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "r"(a) : "memory");
-  return v;
-}
 
-// Y_q[j][r] = scale sum_i K[j][i] X_q[r][i]; X: s columns of R x m (FP64,
-// row-major), Y: s columns of m x R.  Grid (m/128, R/32, s KS), cluster
-// (1, 1, KS), KS = ceil(m / 32) <= 8, 128 threads.
+// Arguments of one product Y_q = scale A X_q^T (see OzGemm).
+struct OzKArgs {
+  const double* X;
+  long long ldx, xq, R;
+  const double* xs;
+  long long xsq;
+  int xsn;
+  const int* fA;
+  double* Y;
+  int ytrans;
+  longlong2* P;
+  int Mrows, mp, KS;
+  double scale;
+  int* err;
+};
+
+// Y_q[j][r] = scale sum_i A[j][i] xs_q[i] X_q[r][i] (or its transpose): A's
+// digit planes by TMA (Mrows x mp), X FP64 rows of stride ldx.  Grid
+// (Mrows/128, R/32, s KS), cluster (1, 1, KS), KS = ceil(mp / 32) <= 8, 128
+// threads.  P: workspace of one 128 x 32 tile of (hi, lo) pairs per CTA,
+// [tile][split][column][row].
 __global__ void __launch_bounds__(128) k_oz_mode(const __grid_constant__ CUtensorMap tA,
-                                                 const double* __restrict__ X,
-                                                 const int* __restrict__ fA, double* __restrict__ Y,
-                                                 int m, long long R, int KS, double scale,
-                                                 int* __restrict__ err) {
+                                                 const OzKArgs a) {
+  const double* __restrict__ X = a.X;
+  const int* __restrict__ fA = a.fA;
+  double* __restrict__ Y = a.Y;
+  longlong2* __restrict__ P = a.P;
+  const int KS = a.KS, m = a.mp;
+  const long long R = a.R;
+  const double scale = a.scale;
+  int* __restrict__ err = a.err;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   int* pmax = (int*)(smem + Z_EXP);        // this split's row maxima (exponent fields)
@@ -379,12 +435,16 @@ __global__ void __launch_bounds__(128) k_oz_mode(const __grid_constant__ CUtenso
     const long long r = r0 + rr;
     const int ib = i0 + 8 * c;
     const bool in = r < R && ib < m;   // m % 8 == 0: a chunk is all in or all out
-    const double2* src = reinterpret_cast<const double2*>(X + ((long long)q * R + r) * m + ib);
+    const double2* src = reinterpret_cast<const double2*>(X + q * a.xq + r * a.ldx + ib);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const double2 t = in ? src[u] : make_double2(0.0, 0.0);
       xv[2 * u] = t.x;
       xv[2 * u + 1] = t.y;
+    }
+    if (a.xs) {   // per-contraction-index scale (exact products are not needed: X rounded once)
+#pragma unroll
+      for (int u = 0; u < 8; ++u) xv[u] *= ib + u < a.xsn ? a.xs[q * a.xsq + ib + u] : 0.0;
     }
   }
   int E = 0;
@@ -399,8 +459,13 @@ __global__ void __launch_bounds__(128) k_oz_mode(const __grid_constant__ CUtenso
   const uint32_t sbase = tc::smem_u32(smem);
   if (tid < Z_N) {
     const uint32_t a = tc::smem_u32(pmax + tid);
+    int ev[Z_MAXKS];
+#pragma unroll
+    for (int src = 0; src < Z_MAXKS; ++src)   // all loads in flight before the max
+      ev[src] = src < KS ? ld_cluster_s32(map_cluster(a, (uint32_t)src)) : 0;
     int Em = 0;
-    for (int src = 0; src < KS; ++src) Em = max(Em, ld_cluster_s32(map_cluster(a, (uint32_t)src)));
+#pragma unroll
+    for (int src = 0; src < Z_MAXKS; ++src) Em = max(Em, ev[src]);
     emax[tid] = Em - 1022;   // max |X[r][:]| < 2^e
   }
   __syncthreads();
@@ -454,14 +519,17 @@ __global__ void __launch_bounds__(128) k_oz_mode(const __grid_constant__ CUtenso
 
   // 4. fold this thread's row into the exact pair
   //   hi = sum_{l < S/2} T_l 2^(8 (S/2 - 1 - l)),  lo = sum_{l >= S/2} T_l 2^(8 (S - 1 - l))
-  // and stage it (row warp 32 + lane, 16 bytes per column)
+  // (pairs of levels first in int32: |T_l 2^8 + T_l+1| < 2^31) and write it
+  // to the workspace, element (column, row): coalesced over the warp's rows
+  static_assert(OZ_S == 8, "the fold below is written for 8 levels");
+  const long long tile = ((long long)q * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  longlong2* Pt = P + tile * KS * Z_TILE;
   {
-    constexpr int H = OZ_S / 2;
-    unsigned char* srow = smem + (warp * 32 + lane) * Z_ROW;
+    longlong2* Pw = Pt + (long long)crank * Z_TILE + warp * 32 + lane;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
     for (int c16 = 0; c16 < Z_N / 16; ++c16) {
-      long long hi[16], lo[16];
+      int pr[4][16];   // level pairs (0,1), (2,3), (4,5), (6,7)
       uint32_t v[2][16];
       tc::tmem_ld16_async(trow + c16 * 16, v[0]);
       tc::tmem_wait_ld(v[0]);
@@ -471,63 +539,65 @@ __global__ void __launch_bounds__(128) k_oz_mode(const __grid_constant__ CUtenso
         if (l + 1 < OZ_S) tc::tmem_ld16_async(trow + (l + 1) * Z_N + c16 * 16, v[(l + 1) & 1]);
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-          const long long t = fin ? (long long)__float2int_rz(__uint_as_float(v[l & 1][e])) : 0;
-          if (l == 0) hi[e] = t;
-          else if (l < H) hi[e] = hi[e] * 256 + t;
-          else if (l == H) lo[e] = t;
-          else lo[e] = lo[e] * 256 + t;
+          // the exact integer T (|T| < 2^22) from its FP32 value: one add
+          const int t = fin ? (int)(__float_as_uint(__uint_as_float(v[l & 1][e]) + Z_MAGIC) -
+                                    0x4B400000u)
+                            : 0;
+          if (l & 1) pr[l >> 1][e] = pr[l >> 1][e] * 256 + t;
+          else pr[l >> 1][e] = t;
         }
         if (l + 1 < OZ_S) tc::tmem_wait_ld(v[(l + 1) & 1]);
       }
 #pragma unroll
-      for (int e = 0; e < 16; ++e)
-        *reinterpret_cast<longlong2*>(srow + (c16 * 16 + e) * 16) = make_longlong2(hi[e], lo[e]);
+      for (int e = 0; e < 16; ++e) {
+        const long long hi = (long long)pr[0][e] * 65536 + pr[1][e];
+        const long long lo = (long long)pr[2][e] * 65536 + pr[3][e];
+        __stcg(Pw + (c16 * 16 + e) * Z_M, make_longlong2(hi, lo));   // L2 only
+      }
     }
   }
   if (!fin && tid == 0) atomicExch(err, 1);
-  cluster_sync();   // every split's pairs are staged
+  cluster_sync();   // every split's pairs are written (release / acquire at cluster scope)
 
   // 5. this CTA's share of the tile (rows [rb, re), all columns), summed over
-  // the cluster in rank order
+  // the splits in order
   {
     const int rb = (int)((crank * Z_M) / KS), re = (int)(((crank + 1) * Z_M) / KS);
-    uint32_t rbase[Z_MAXKS];
+    const int nr = re - rb;
+    const long long MR = (long long)a.Mrows * R;
+    const int nit = nr * Z_N;
+    for (int it0 = 0; it0 < nit; it0 += 2 * 128) {
+      longlong2 pv[2][Z_MAXKS];
 #pragma unroll
-    for (int src = 0; src < Z_MAXKS; ++src) rbase[src] = src < KS ? map_cluster(sbase, src) : 0u;
-    const long long MR = (long long)m * R;
-    const int nit = (re - rb) * Z_N;
-    for (int it0 = 0; it0 < nit; it0 += 4 * 128) {
-      longlong2 pr[4][Z_MAXKS];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < 2; ++k) {
         const int it = it0 + k * 128 + tid;
-        const uint32_t off = it < nit ? (uint32_t)((rb + it / Z_N) * Z_ROW + (it % Z_N) * 16) : 0u;
+        const int off = it < nit ? (it / nr) * Z_M + rb + it % nr : 0;   // (column, row)
 #pragma unroll
         for (int src = 0; src < Z_MAXKS; ++src)
-          pr[k][src] = (src < KS && it < nit) ? ld_cluster_pair(rbase[src] + off) : make_longlong2(0, 0);
+          pv[k][src] = (src < KS && it < nit) ? __ldcg(Pt + (long long)src * Z_TILE + off)
+                                             : make_longlong2(0, 0);
       }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < 2; ++k) {
         const int it = it0 + k * 128 + tid;
         if (it >= nit) continue;
         long long hi = 0, lo = 0;
 #pragma unroll
         for (int src = 0; src < Z_MAXKS; ++src) {
-          hi += pr[k][src].x;
-          lo += pr[k][src].y;
+          hi += pv[k][src].x;
+          lo += pv[k][src].y;
         }
-        const int row = rb + it / Z_N, col = it % Z_N;
+        const int row = rb + it % nr, col = it / nr;
         const int j = j0 + row;
         const long long r = r0 + col;
-        if (j >= m || r >= R) continue;
+        if (j >= a.Mrows || r >= R) continue;
         const int ex = fA[j] + emax[col] - 2 * OZ_P + 8 * (OZ_S - 1);   // Y = (hi 2^32 + lo) 2^ex
-        const double v = fma((double)hi, 4294967296.0, (double)lo);
-        const double p2 = ex > -1023 ? __longlong_as_double((long long)(ex + 1023) << 52) : 0.0;
-        Y[(long long)q * MR + (long long)j * R + r] = scale * (v * p2);
+        const double v = exact_to_double(hi, lo, ex);
+        const long long o = a.ytrans ? r * a.Mrows + j : (long long)j * R + r;
+        Y[(long long)q * MR + o] = scale == 1.0 ? v : scale * v;
       }
     }
   }
-  cluster_sync();   // the other CTAs have read this CTA's pairs
   tc::fence_before();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, 256);
@@ -535,11 +605,16 @@ __global__ void __launch_bounds__(128) k_oz_mode(const __grid_constant__ CUtenso
 
 }  // namespace
 
-int oz_slice_factor(dski_handle h, const double* K, int m, uint16_t* Ad, int* fA) {
-  StageScope sc(h, ST_KRON, h->stream);
-  k_oz_slice_factor<<<(m + 127) / 128, 128, 0, h->stream>>>(K, m, Ad, fA);
+int oz_slice(dski_handle h, const double* A, int rows, int cols, int lda, int mp, uint16_t* Ad,
+             int* fA, int stage) {
+  StageScope sc(h, stage, h->stream);
+  k_oz_slice_factor<<<(rows + 127) / 128, 128, 0, h->stream>>>(A, rows, cols, lda, mp, Ad, fA);
   DSKI_LAUNCHED();
   return DSKI_OK;
+}
+
+int oz_slice_factor(dski_handle h, const double* K, int m, uint16_t* Ad, int* fA) {
+  return oz_slice(h, K, m, m, m, m, Ad, fA, ST_KRON);
 }
 
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -559,22 +634,20 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// One mode product on the tensor cores (FP64_TC).  K's digit planes are a
-// 3-D TMA tensor (m x m x 8, innermost first), box 32 x 128 x 1 with 64-byte
-// swizzling.
-int mode_tc_oz(dski_handle h, const double* X, const uint16_t* Ad, const int* fA, double* Y,
-               int m, long long R, int s, double scale) {
-  if (m % 8 != 0 || m > 256)
-    return set_error(DSKI_ERR_ARG, "FP64_TC mode products need m_k %% 8 == 0 and m_k <= 256 (got %d)", m);
+// Y_q = scale A X_q^T on the tensor cores (FP64-accurate; see OzGemm).
+int oz_gemm(dski_handle h, const OzGemm& g, int stage) {
+  if (g.mp % 8 != 0 || g.mp > 256 || g.mp < 8 || g.Mrows < 1 || g.R < 1 || g.s < 1 ||
+      g.ldx < g.mp || g.ldx % 2 != 0)
+    return set_error(DSKI_ERR_ARG, "FP64_TC product: contraction %d (needs %% 8 == 0, <= 256)", g.mp);
   auto enc = tensor_map_encoder();
   if (!enc) return set_error(DSKI_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
   CUtensorMap tA;
   {
-    const cuuint64_t dims[3] = {(cuuint64_t)m, (cuuint64_t)m, (cuuint64_t)OZ_S};
-    const cuuint64_t str[2] = {(cuuint64_t)m * 2, (cuuint64_t)m * m * 2};
+    const cuuint64_t dims[3] = {(cuuint64_t)g.mp, (cuuint64_t)g.Mrows, (cuuint64_t)OZ_S};
+    const cuuint64_t str[2] = {(cuuint64_t)g.mp * 2, (cuuint64_t)g.Mrows * g.mp * 2};
     const cuuint32_t box[3] = {(cuuint32_t)Z_KC, (cuuint32_t)Z_M, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = enc(&tA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(Ad),
+    const CUresult r = enc(&tA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(g.Ad),
                            dims, str, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -586,10 +659,30 @@ int mode_tc_oz(dski_handle h, const double* X, const uint16_t* Ad, const int* fA
     cudaFuncSetAttribute(k_oz_mode, cudaFuncAttributeMaxDynamicSharedMemorySize, Z_SMEM);
     attr_set = true;
   }
-  const int KS = (m + Z_KC - 1) / Z_KC;   // <= 8 for m <= 256
+  OzKArgs a{};
+  a.X = g.X;
+  a.ldx = g.ldx;
+  a.xq = g.xq;
+  a.R = g.R;
+  a.xs = g.xs;
+  a.xsq = g.xsq;
+  a.xsn = g.xsn;
+  a.fA = g.fA;
+  a.Y = g.Y;
+  a.ytrans = g.ytrans ? 1 : 0;
+  a.Mrows = g.Mrows;
+  a.mp = g.mp;
+  a.KS = (g.mp + Z_KC - 1) / Z_KC;   // <= 8
+  a.scale = g.scale;
+  a.err = h->dev_err.as<int>();
+  const long long tiles = (long long)g.s * ((g.Mrows + Z_M - 1) / Z_M) * ((g.R + Z_N - 1) / Z_N);
+  DevBuf& ws = g.workspace ? *g.workspace : h->ozP;
+  if (ws.ensure((size_t)tiles * a.KS * Z_TILE * sizeof(longlong2)))
+    return set_error(DSKI_ERR_ALLOC, "FP64_TC workspace allocation failed");
+  a.P = ws.as<longlong2>();
   cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3((unsigned)((m + Z_M - 1) / Z_M), (unsigned)((R + Z_N - 1) / Z_N),
-                     (unsigned)(s * KS));
+  cfg.gridDim = dim3((unsigned)((g.Mrows + Z_M - 1) / Z_M), (unsigned)((g.R + Z_N - 1) / Z_N),
+                     (unsigned)(g.s * a.KS));
   cfg.blockDim = dim3(128);
   cfg.dynamicSmemBytes = Z_SMEM;
   cfg.stream = h->stream;
@@ -597,19 +690,38 @@ int mode_tc_oz(dski_handle h, const double* X, const uint16_t* Ad, const int* fA
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 1;
   attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = (unsigned)KS;
-  // let a cluster's CTAs share SMs, so that every cluster of a mode product
-  // can be resident at once
+  attr[0].val.clusterDim.z = (unsigned)a.KS;
+  // let a cluster's CTAs share SMs, so that every cluster of a product can
+  // be resident at once
   attr[1].id = cudaLaunchAttributeClusterSchedulingPolicyPreference;
   attr[1].val.clusterSchedulingPolicyPreference = cudaClusterSchedulingPolicyLoadBalancing;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  StageScope sc(h, ST_KRON, h->stream);
-  if (cudaLaunchKernelEx(&cfg, k_oz_mode, tA, X, fA, Y, m, R, KS, scale, h->dev_err.as<int>()) !=
-      cudaSuccess)
-    return set_error(DSKI_ERR_CUDA, "FP64_TC mode product launch: %s",
+  StageScope sc(h, stage, h->stream);
+  if (cudaLaunchKernelEx(&cfg, k_oz_mode, tA, a) != cudaSuccess)
+    return set_error(DSKI_ERR_CUDA, "FP64_TC product launch: %s",
                      cudaGetErrorString(cudaGetLastError()));
   return DSKI_OK;
+}
+
+// One mode product Y_q[j][r] = scale sum_i K[j][i] X_q[r][i] (FP64_TC).
+int mode_tc_oz(dski_handle h, const double* X, const uint16_t* Ad, const int* fA, double* Y,
+               int m, long long R, int s, double scale) {
+  if (m % 8 != 0 || m > 256)
+    return set_error(DSKI_ERR_ARG, "FP64_TC mode products need m_k %% 8 == 0 and m_k <= 256 (got %d)", m);
+  OzGemm g{};
+  g.Ad = Ad;
+  g.fA = fA;
+  g.Mrows = m;
+  g.mp = m;
+  g.X = X;
+  g.ldx = m;
+  g.xq = R * m;
+  g.R = R;
+  g.Y = Y;
+  g.scale = scale;
+  g.s = s;
+  return oz_gemm(h, g, ST_KRON);
 }
 
 }  // namespace dski

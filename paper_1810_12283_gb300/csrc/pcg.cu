@@ -47,6 +47,7 @@ struct ColState {
 };
 
 constexpr int CG_THREADS = 256;
+constexpr int CG_UNROLL = 4;   // elements per thread and step in the streaming kernels
 
 __device__ __forceinline__ bool cg_last(unsigned* ticket) {
   return last_block(ticket, gridDim.x * gridDim.y);
@@ -137,6 +138,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_z(
   }
   __syncthreads();
   double acc = 0.0;
+#pragma unroll 4
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
     const long long o = (long long)c * N + i;
@@ -243,12 +245,24 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_alpha(const double* __restric
   __shared__ double sh[32];
   const int c = blockIdx.y;
   double acc = 0.0;
-  if (cs.active[c])
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-         i += (long long)gridDim.x * blockDim.x) {
-      const long long o = (long long)c * N + i;
-      acc = fma(p[o], (double)q[o], acc);
+  if (cs.active[c]) {
+    const long long st = (long long)gridDim.x * blockDim.x;
+    const double* pc = p + (long long)c * N;
+    const TQ* qc = q + (long long)c * N;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // CG_UNROLL independent elements per thread and step: all loads in flight
+    for (; i + (CG_UNROLL - 1) * st < N; i += CG_UNROLL * st) {
+      double pv[CG_UNROLL], qv[CG_UNROLL];
+#pragma unroll
+      for (int u = 0; u < CG_UNROLL; ++u) {
+        pv[u] = pc[i + u * st];
+        qv[u] = (double)qc[i + u * st];
+      }
+#pragma unroll
+      for (int u = 0; u < CG_UNROLL; ++u) acc = fma(pv[u], qv[u], acc);
     }
+    for (; i < N; i += st) acc = fma(pc[i], (double)qc[i], acc);
+  }
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) part[(long long)c * gridDim.x + blockIdx.x] = acc;
   if (cg_last(ticket)) {
@@ -282,16 +296,40 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_update(
   const int c = blockIdx.y;
   const double al = cs.alpha[c];
   double acc = 0.0;
-  if (cs.active[c])
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-         i += (long long)gridDim.x * blockDim.x) {
-      const long long o = (long long)c * N + i;
+  if (cs.active[c]) {
+    const long long st = (long long)gridDim.x * blockDim.x;
+    const long long off = (long long)c * N;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + (CG_UNROLL - 1) * st < N; i += CG_UNROLL * st) {
+      double xv[CG_UNROLL], pv[CG_UNROLL], qv[CG_UNROLL], rv[CG_UNROLL], dv[CG_UNROLL];
+#pragma unroll
+      for (int u = 0; u < CG_UNROLL; ++u) {
+        const long long o = off + i + u * st;
+        xv[u] = x[o];
+        pv[u] = p[o];
+        qv[u] = (double)q[o];
+        rv[u] = r[o];
+        dv[u] = y ? dis[i + u * st] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < CG_UNROLL; ++u) {
+        const long long o = off + i + u * st;
+        x[o] = fma(al, pv[u], xv[u]);
+        const double ri = fma(-al, qv[u], rv[u]);
+        r[o] = ri;
+        if (y) y[o] = dv[u] * ri;
+        acc = fma(ri, ri, acc);
+      }
+    }
+    for (; i < N; i += st) {
+      const long long o = off + i;
       x[o] = fma(al, p[o], x[o]);
       const double ri = fma(-al, (double)q[o], r[o]);
       r[o] = ri;
       if (y) y[o] = dis[i] * ri;
       acc = fma(ri, ri, acc);
     }
+  }
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) part[(long long)c * gridDim.x + blockIdx.x] = acc;
   if (cg_last(ticket)) {
@@ -342,6 +380,13 @@ int cg_run(dski_handle h, CgRun& run) {
   // at most 16 blocks per SM over all columns
   const int nbx = (int)std::min<long long>((N + CG_THREADS - 1) / CG_THREADS,
                                            std::max(1, 16 * h->sm_count / std::max(1, s)));
+  // the streaming kernels (dots, updates): ~2 blocks per SM over all columns,
+  // CG_UNROLL elements per thread and step -- few blocks keep the
+  // last-block reduction (one ticket atomic per block, a sum over the
+  // blocks' partials) short
+  const int nbv = (int)std::min<long long>(
+      std::max<long long>(1, (N + (long long)CG_THREADS * CG_UNROLL - 1) / (CG_THREADS * CG_UNROLL)),
+      std::max(1, 2 * h->sm_count / std::max(1, s)));
   double* part = wbuf(h->s_part, (size_t)nbx * s * 2 + 16);
   unsigned* tk = tickets(h, 1);
   if (!R || !Z || !P || !Q || (run.pc && !Y) || (rank && !C) || (mixed && (!P32 || !Q32)) ||
@@ -371,6 +416,7 @@ int cg_run(dski_handle h, CgRun& run) {
   const double eta2 = mixed ? 1e-8 : 0.0;   // inner reduction target (1e-4)^2 in the mixed modes
   const double* dis = run.pc ? run.pc->dis.as<double>() : nullptr;
   const dim3 grd(nbx, s);
+  const dim3 grv(std::min(nbv, nbx), s);
   const size_t zsmem = (size_t)std::max(rank, 1) * sizeof(double);
 
   const bool split = run.pc && run.pc->split;
@@ -380,7 +426,7 @@ int cg_run(dski_handle h, CgRun& run) {
     if (gridf) {
       DSKI_TRY(grid_precond_apply(h, run.pc, R, Z, s));
       StageScope sc(h, ST_PCGVEC, st);
-      k_cg_z<false><<<grd, CG_THREADS, zsmem, st>>>(R, nullptr, nullptr, nullptr, nullptr, Z, 0,
+      k_cg_z<false><<<grv, CG_THREADS, zsmem, st>>>(R, nullptr, nullptr, nullptr, nullptr, Z, 0,
                                                    nullptr, nullptr, Z, P, P32, N, init, cs, part,
                                                    tk);
       DSKI_LAUNCHED();
@@ -417,7 +463,7 @@ int cg_run(dski_handle h, CgRun& run) {
     h->kron_exact = false;
     DSKI_TRY(mrc);
     StageScope sc(h, ST_PCGVEC, st);
-    k_cg_init<<<grd, CG_THREADS, 0, st>>>(run.B, Q, R, Y, dis, N, first, tol2, eta2, cs, part,
+    k_cg_init<<<grv, CG_THREADS, 0, st>>>(run.B, Q, R, Y, dis, N, first, tol2, eta2, cs, part,
                                           tk);
     DSKI_LAUNCHED();
     return DSKI_OK;
@@ -431,16 +477,16 @@ int cg_run(dski_handle h, CgRun& run) {
     if (mixed) {
       DSKI_TRY(mvm_internal(h, P32, Q32, s, false));
       StageScope sc(h, ST_PCGVEC, st, 2);
-      k_cg_alpha<float><<<grd, CG_THREADS, 0, st>>>(P, Q32, N, cs, part, tk);
-      k_cg_update<float><<<grd, CG_THREADS, 0, st>>>(run.X, R, Y, P, Q32, dis, N, cs, part, tk);
+      k_cg_alpha<float><<<grv, CG_THREADS, 0, st>>>(P, Q32, N, cs, part, tk);
+      k_cg_update<float><<<grv, CG_THREADS, 0, st>>>(run.X, R, Y, P, Q32, dis, N, cs, part, tk);
     } else {
       // fused: the previous iteration's p = z + beta p happens in the MVM's
       // first pass (after an (re)start beta = 0 and p = z already)
       if (fused) DSKI_TRY(mvm_pcg_fused(h, P, Z, cs.beta, Q, s));
       else DSKI_TRY(mvm_internal(h, P, Q, s, true));
       StageScope sc(h, ST_PCGVEC, st, 2);
-      k_cg_alpha<double><<<grd, CG_THREADS, 0, st>>>(P, Q, N, cs, part, tk);
-      k_cg_update<double><<<grd, CG_THREADS, 0, st>>>(run.X, R, Y, P, Q, dis, N, cs, part, tk);
+      k_cg_alpha<double><<<grv, CG_THREADS, 0, st>>>(P, Q, N, cs, part, tk);
+      k_cg_update<double><<<grv, CG_THREADS, 0, st>>>(run.X, R, Y, P, Q, dis, N, cs, part, tk);
     }
     DSKI_LAUNCHED();
     DSKI_TRY(precond_z(0));

@@ -356,6 +356,10 @@ void free_pc(pivchol_handle pc) {
   pc->Hf.release();
   pc->H1T.release();
   pc->Sg.release();
+  pc->ozH1.release();
+  pc->ozH1T.release();
+  pc->ozE.release();
+  pc->H0Tp.release();
   pc->gwork.release();
   pc->dis.release();
   pc->ds.release();

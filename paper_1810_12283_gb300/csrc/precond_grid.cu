@@ -184,6 +184,15 @@ __global__ void k_grid_x(const double* __restrict__ S, const double* __restrict_
   if (lane == 0) x[(long long)q * r + a] = v;
 }
 
+// Y (cols x rp) = X^T (X: rows x cols), zero in columns rows..rp-1.
+__global__ void k_transpose_pad(const double* __restrict__ X, int rows, int cols, int rp,
+                                double* __restrict__ Y) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= cols * rp) return;
+  const int b = idx / rp, a = idx % rp;
+  Y[idx] = a < rows ? X[(long long)a * cols + b] : 0.0;
+}
+
 __global__ void k_transpose(const double* __restrict__ X, int rows, int cols,
                             double* __restrict__ Y) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -225,6 +234,27 @@ int grid_precond_build(dski_handle h, pivchol_handle pc, const int* piv_dev, con
   LP.release();
   W.release();
   if (rc == DSKI_OK) pc->grid_form = true;
+  // FP64_TC: digit planes for the two products of the apply
+  if (rc == DSKI_OK && h->prec == DSKI_FP64_TC && r <= 256 && m1 % 8 == 0 && m1 <= 256) {
+    const int rp = (r + 7) / 8 * 8;
+    if (pc->ozH1.ensure((size_t)kOzDigits * r * m1 * 2) ||
+        pc->ozH1T.ensure((size_t)kOzDigits * m1 * rp * 2) ||
+        pc->ozE.ensure((size_t)(r + m1) * 4) || pc->H0Tp.ensure((size_t)m0 * rp * 8))
+      return set_error(DSKI_ERR_ALLOC, "pivchol_build: FP64_TC preconditioner allocation failed");
+    const double* H1 = pc->Hf.as<double>() + (size_t)r * m0;
+    DSKI_TRY(oz_slice(h, H1, r, m1, m1, m1, pc->ozH1.as<uint16_t>(), pc->ozE.as<int>(),
+                      ST_PIVCHOL));
+    DSKI_TRY(oz_slice(h, pc->H1T.as<double>(), m1, r, r, rp, pc->ozH1T.as<uint16_t>(),
+                      pc->ozE.as<int>() + r, ST_PIVCHOL));
+    {
+      StageScope sc(h, ST_PIVCHOL, st);
+      k_transpose_pad<<<(m0 * rp + 255) / 256, 256, 0, st>>>(pc->Hf.as<double>(), r, m0, rp,
+                                                              pc->H0Tp.as<double>());
+    }
+    DSKI_LAUNCHED();
+    pc->rp = rp;
+    pc->oz = true;
+  }
   return rc;
 }
 
@@ -247,7 +277,43 @@ int grid_precond_apply(dski_handle h, pivchol_handle pc, const double* R, double
     // g = B^T D^-1 R
     DSKI_TRY(scatter_scaled(h, R + (size_t)c0 * N, g, q, true, nullptr, 1.0 / pc->nv,
                             1.0 / pc->ng));
-    {
+    if (pc->oz) {
+      // the two products on the tensor cores (FP64-accurate digit products)
+      OzGemm g1;   // Y[q][k][u0] = sum_u1 H1[k][u1] g[q][u0][u1]
+      g1.Ad = pc->ozH1.as<uint16_t>();
+      g1.fA = pc->ozE.as<int>();
+      g1.Mrows = r;
+      g1.mp = m1;
+      g1.X = g;
+      g1.ldx = m1;
+      g1.xq = M;
+      g1.R = m0;
+      g1.Y = Yb;
+      g1.s = q;
+      DSKI_TRY(oz_gemm(h, g1, ST_PRECOND));
+      {
+        StageScope sc(h, ST_PRECOND, st, 2);
+        k_grid_c<<<(q * r * 32 + 255) / 256, 256, 0, st>>>(pc->Hf.as<double>(), Yb, r, m0, q, cb);
+        k_grid_x<<<(q * r * 32 + 255) / 256, 256, 0, st>>>(pc->Sg.as<double>(), cb, r, q, xb);
+      }
+      DSKI_LAUNCHED();
+      OzGemm g2;   // h'[q][u0][u1] = sum_k H1T[u1][k] x_k H0T[u0][k]
+      g2.Ad = pc->ozH1T.as<uint16_t>();
+      g2.fA = pc->ozE.as<int>() + r;
+      g2.Mrows = m1;
+      g2.mp = pc->rp;
+      g2.X = pc->H0Tp.as<double>();
+      g2.ldx = pc->rp;
+      g2.xq = 0;
+      g2.R = m0;
+      g2.xs = xb;
+      g2.xsq = r;
+      g2.xsn = r;
+      g2.Y = hp;
+      g2.ytrans = true;
+      g2.s = q;
+      DSKI_TRY(oz_gemm(h, g2, ST_PRECOND));
+    } else {
       StageScope sc(h, ST_PRECOND, st, 4);
       // Y[q][k][u0] = sum_u1 H1[k][u1] g[q][u0][u1]
       k_gemm_nt<false><<<dim3((m0 + GT - 1) / GT, (r + GT - 1) / GT, q), GT * GT, 0, st>>>(

@@ -34,6 +34,12 @@ struct pivchol_ {
   // H1T = the second block transposed) and S = T T^T (r x r)
   bool grid_form = false;
   dski::DevBuf Hf, H1T, Sg, gwork;
+  // FP64_TC: the grid form's two products on the tensor cores -- digit planes
+  // of H1 (r x m1) and of H1^T (m1 x rp, rp = r rounded up to 8), their row
+  // exponents (r + m1 ints) and H0^T padded to m0 x rp (FP64)
+  bool oz = false;
+  int rp = 0;
+  dski::DevBuf ozH1, ozH1T, ozE, H0Tp;
   dski::DevBuf dis;       // D^-1/2 per internal row
   dski::DevBuf ds;        // D^1/2 per internal row
   std::vector<int> piv;   // internal row of pivot k

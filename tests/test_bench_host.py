@@ -58,3 +58,9 @@ def test_algorithmic_byte_counts():
     N = n * (d + 1)
     assert bench.mvm_bytes(n, d, M, 1, 8) == 3 * N * 8 + 2 * M * 8 + 2 * n * (4 + 8 * 8 * d)
     assert bench.precond_bytes(N, 100, 1) == 2 * N * 100 * 8 + 3 * N * 8
+
+
+def test_scatter_byte_count():
+    import bench
+    n, d, M = 100_000, 2, 65_536
+    assert bench.scatter_bytes(n, d, M, 1, 8) == 3 * n * 8 + n * (4 + 16 * 8) + M * 8
