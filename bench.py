@@ -175,6 +175,76 @@ def cpu_baseline(p, iters_gpu, budget_s=12.0):
                        f"{per_it * 1e3:.1f} ms each), scaled to the GPU's {iters_gpu} iterations")}
 
 
+def gather_bytes(n, d, M, s, elem):
+    """HBM model of one gather with the noise term: the grid (M s) and v
+    (N s) read, the per-point weights and cell id read, out (N s) written."""
+    N = n * (d + 1)
+    return M * s * elem + 2 * N * s * elem + n * (4 + 8 * d * elem)
+
+
+SWEEP = ((100_000, 256), (1_000_000, 256), (10_000_000, 1024), (30_000_000, 1024))
+
+
+def run_sweep(args):
+    """Scatter and gather bandwidth against the HBM model at growing n (the
+    terrain shape: points uniform in [0,1]^2, grid over [-0.05, 1.05]^2,
+    l = 0.05), FP64 and FP32 (mixed) vectors, s = 1 and 8.  Inputs are made
+    on the device (seeded); the values do not change the work."""
+    import torch
+    from paper_1810_12283_gb300 import DSKI
+    dev = torch.device("cuda", 0)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    pts = []
+    reps = 10
+    for n, g in SWEEP:
+        if n > args.sweep_max_n:
+            continue
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(n)
+        X = torch.rand((n, 2), generator=gen, device=dev, dtype=torch.float64)
+        M = g * g
+        for prec in ("fp64", "mixed_3xtf32"):
+            op = DSKI(X, [g, g], [-0.05, -0.05], [1.05, 1.05], [0.05, 0.05], 1.0, 1e-3, 1e-3,
+                      prec=prec)
+            elem = 8 if prec == "fp64" else 4
+            for s in (1, 8):
+                v = torch.randn((s, op.N), generator=gen, device=dev, dtype=torch.float64).to(op.dtype)
+                out = torch.empty_like(v)
+                for _ in range(3):
+                    op.mvm(v, out=out)
+                torch.cuda.synchronize()
+                op.profile_start()
+                for i in range(reps):
+                    flush.fill_(i & 255)
+                    op.mvm(v, out=out)
+                st = op.profile_stop()[0]
+                t_sc = st["scatter"][0] / reps / 1e3
+                t_ga = st["gather"][0] / reps / 1e3
+                bs = scatter_bytes(n, 2, M, s, elem)
+                bg = gather_bytes(n, 2, M, s, elem)
+                pts.append({"n": n, "grid": g, "prec": prec, "s": s,
+                            "scatter_us": round(t_sc * 1e6, 2), "gather_us": round(t_ga * 1e6, 2),
+                            "scatter_gbs": round(bs / t_sc / 1e9, 1),
+                            "gather_gbs": round(bg / t_ga / 1e9, 1),
+                            "scatter_frac": round(bs / t_sc / 1e9 / hbm, 3),
+                            "gather_frac": round(bg / t_ga / 1e9 / hbm, 3)})
+                del v, out
+            op.close()
+        del X
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "D-SKI scatter / gather bandwidth vs the HBM model (sweep over n)",
+                      "unit": "GB/s", "peak_hbm_gbs": hbm,
+                      "l2": "flushed before each timed MVM (256 MiB write)", "reps": reps,
+                      "points": pts}), flush=True)
+    return 0
+
+
 def run_reference(args, p):
     rank, ws, dist = dist_init()
     if rank != 0:
@@ -216,12 +286,17 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=120126,
                     help="reference arm: PCG iterations to scale the oracle's per-iteration time to")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="instead of the solve step: scatter / gather bandwidth at n = 1e5 .. 3e7")
+    ap.add_argument("--sweep-max-n", type=int, default=30_000_000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     args.steps = max(args.steps, 1)
 
     from synth import workloads as W
     p = W.terrain2d(n=args.n)
+    if args.sweep:
+        return run_sweep(args)
     if args.impl == "reference":
         return run_reference(args, p)
 

@@ -224,9 +224,11 @@ long long dski_launch_count(void);
  * whose host forbids device allocation after start-up.  Same arguments,
  * layouts and result as dski_mvm, but it calls no cudaMalloc, cudaFree or
  * allocating library routine: its temporaries (the permuted input and output,
- * N x s each, two grids, M x s each, in the mode's element size, and in FP64
- * mode with d >= 2 and s <= 4 the scatter's per-point coefficients, 8 (d = 2)
- * or 32 (d = 3) doubles per point and column) live in one fixed device array
+ * N x s each, two grids, M x s each, in the mode's element size, and the
+ * scatter's intermediate: in the MIXED modes with d = 2 its per-cell stencil
+ * sums, 16 floats per cell of the grid and column; in FP64 mode with d >= 2
+ * and s <= 4 its per-point coefficients, 8 (d = 2) or 32 (d = 3) doubles per
+ * point and column) live in one fixed device array
  * of DSKI_NOALLOC_SCRATCH_BYTES (32 MiB) that the library reserves on every
  * GPU that loads it, until the process exits.
  *   - Sizes that do not fit (each part padded to 256 bytes) are rejected with
@@ -238,7 +240,7 @@ long long dski_launch_count(void);
  *     other handles, other host threads) race on it: serialise them.
  *   - The handle must live on the current device (else DSKI_ERR_ARG).
  *   - FP64 and MIXED handles only: an FP64_TC handle is rejected with
- *     DSKI_ERR_ARG (its mode products need a digit workspace).
+ *     DSKI_ERR_ARG (its mode products need a split-contraction workspace).
  * Errors: ARG, CUDA. */
 #define DSKI_NOALLOC_SCRATCH_BYTES (32u << 20)
 int dski_mvm_noalloc(dski_handle h, const void* v_dev, void* out_dev, int s);

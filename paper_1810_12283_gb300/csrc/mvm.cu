@@ -23,6 +23,13 @@ struct MvmGeo {
   double invh[DSKI_MAXD];
 };
 
+template <class T>
+const T* wt_table(dski_handle h);
+template <>
+const double* wt_table<double>(dski_handle h) { return h->W64.as<double>(); }
+template <>
+const float* wt_table<float>(dski_handle h) { return h->W32.as<float>(); }
+
 static MvmGeo make_geo(dski_handle h) {
   MvmGeo g{};
   g.d = h->d;
@@ -264,6 +271,129 @@ __global__ void __launch_bounds__(256) k_scatter_ab(MvmGeo g, const int* __restr
     for (int q = 0; q < CB; ++q)
       if (q0 + q < s) grid[(long long)(q0 + q) * M + u] = acc[q];
   }
+}
+
+// ------------------------------------------------- scatter, d = 2, by cell ----
+// Two passes, both deterministic (fixed summation orders, no atomics):
+//   1. per cell: S[q][a][b][cell] = sum over the cell's points j of
+//        w0_a w1_b v0_j + w0'_a w1_b v1_j + w0_a w1'_b v2_j
+//      (the point's contribution to stencil node (c0 + a, c1 + b)); a group
+//      of G lanes takes one cell, each lane a stride-G subset of its points
+//      (read once, coalesced, sorted by cell), and a fixed butterfly over the
+//      group adds the lanes' sums.  G follows the mean points per cell.
+//   2. per node: g[q][u0][u1] = sum_{a, b} S[q][a][b][(u0 - a, u1 - b)] over
+//      the (up to) 16 cells whose stencil holds the node; consecutive nodes
+//      read consecutive cells of one plane.
+// Each point is read once (the node-owned pull above reads it 16 times);
+// the per-cell planes hold 16 values per cell and column.
+// Optional, as in k_scatter_prep: v0 scaled by sv, v1, v2 by sg; with z,
+// p = z + beta p is formed first and written back (fused PCG direction).
+template <class T, int CB, int G>
+__global__ void __launch_bounds__(256) k_scatter_cells(const int* __restrict__ cell_start,
+                                                       const T* __restrict__ wt, T* __restrict__ v,
+                                                       T* __restrict__ S, int s, long long N,
+                                                       int ncell, T sv, T sg,
+                                                       const double* __restrict__ z,
+                                                       const double* __restrict__ beta) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = (int)(t / G), g = (int)(t % G);
+  const bool live = c < ncell;   // whole groups: ncell groups, G | 32
+  const int q0 = blockIdx.y * CB;
+  T acc[CB][16];
+#pragma unroll
+  for (int q = 0; q < CB; ++q)
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc[q][k] = T(0);
+  if (live) {
+    const int js = cell_start[c], je = cell_start[c + 1];
+    for (int j = js + g; j < je; j += G) {
+      T w[16];
+      const T* wj = wt + (long long)j * 16;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) w[k] = wj[k];
+#pragma unroll
+      for (int q = 0; q < CB; ++q) {
+        if (q0 + q >= s) break;
+        T* vj = v + (long long)(q0 + q) * N + (long long)j * 3;
+        T v0 = vj[0], v1 = vj[1], v2 = vj[2];
+        if (z) {   // p = z + beta p (double vectors only)
+          const double* zj = z + (long long)(q0 + q) * N + (long long)j * 3;
+          const double be = beta[q0 + q];
+          v0 = (T)fma(be, (double)v0, zj[0]);
+          v1 = (T)fma(be, (double)v1, zj[1]);
+          v2 = (T)fma(be, (double)v2, zj[2]);
+          vj[0] = v0;
+          vj[1] = v1;
+          vj[2] = v2;
+        }
+        v0 *= sv;
+        v1 *= sg;
+        v2 *= sg;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const T ca = fma(w[a], v0, w[4 + a] * v1);   // sum-factorised over dimension 0
+          const T ea = w[a] * v2;
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+            acc[q][a * 4 + b] = fma(w[8 + b], ca, fma(w[12 + b], ea, acc[q][a * 4 + b]));
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1)
+#pragma unroll
+    for (int q = 0; q < CB; ++q)
+#pragma unroll
+      for (int k = 0; k < 16; ++k) acc[q][k] += __shfl_xor_sync(0xffffffffu, acc[q][k], o);
+  if (!live) return;
+#pragma unroll
+  for (int q = 0; q < CB; ++q) {
+    if (q0 + q >= s) break;
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (k % G == g) S[((long long)(q0 + q) * 16 + k) * ncell + c] = acc[q][k];
+  }
+}
+
+template <class T, int CB>
+__global__ void __launch_bounds__(256) k_scatter_nodes(MvmGeo geo, const T* __restrict__ S,
+                                                       T* __restrict__ grid, int s, long long M,
+                                                       int ncell) {
+  const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= M) return;
+  const int u0 = (int)(u / geo.m[1]), u1 = (int)(u % geo.m[1]);
+  const int q0 = blockIdx.y * CB;
+  T acc[CB];
+#pragma unroll
+  for (int q = 0; q < CB; ++q) acc[q] = T(0);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int c0 = u0 - a;
+    if (c0 < 0 || c0 >= geo.mc[0]) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int c1 = u1 - b;
+      if (c1 < 0 || c1 >= geo.mc[1]) continue;
+      const long long cell = (long long)c0 * geo.mc[1] + c1;
+#pragma unroll
+      for (int q = 0; q < CB; ++q)
+        if (q0 + q < s) acc[q] += S[((long long)(q0 + q) * 16 + a * 4 + b) * ncell + cell];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < CB; ++q)
+    if (q0 + q < s) grid[(long long)(q0 + q) * M + u] = acc[q];
+}
+
+template <class T, int CB, int G>
+void launch_scatter_cells(dski_handle h, T* v, T* S, int s, T sv, T sg, const double* z,
+                          const double* beta, cudaStream_t st) {
+  const int ncell = h->mc[0] * h->mc[1];
+  const long long threads = (long long)ncell * G;
+  const dim3 grd((unsigned)((threads + 255) / 256), (unsigned)((s + CB - 1) / CB));
+  k_scatter_cells<T, CB, G><<<grd, 256, 0, st>>>(h->cell_start.as<int>(), wt_table<T>(h), v, S, s,
+                                                  h->N, ncell, sv, sg, z, beta);
 }
 
 // -------------------------------------------------------------- gather ----
@@ -589,9 +719,28 @@ void mode_simt(dski_handle h, const T* X, const T* K, T* Y, int m, long long R, 
 void set_no_tune(bool on) { g_no_tune = on; }
 
 size_t scatter_ws_bytes(dski_handle h, int s, bool prec64) {
+  if (h->d == 2 && !prec64) return (size_t)s * 16 * h->mc[0] * h->mc[1] * 4;
   if (!(prec64 && h->d >= 2 && s <= 4)) return 0;
   return (size_t)s * h->n * (h->d == 2 ? 8 : 32) * 8;
 }
+
+namespace {
+// d = 2: the per-cell pass with the group size that fits the mean points per
+// cell, then the per-node pass
+template <class T, int CB>
+void scatter_cells_d2(dski_handle h, T* v, T* S, T* grid, int s, T sv, T sg, const double* z,
+                      const double* beta, cudaStream_t st) {
+  const int ncell = h->mc[0] * h->mc[1];
+  const double per = (double)h->n / std::max(1, ncell);
+  if (per <= 2.0) launch_scatter_cells<T, CB, 2>(h, v, S, s, sv, sg, z, beta, st);
+  else if (per <= 4.0) launch_scatter_cells<T, CB, 4>(h, v, S, s, sv, sg, z, beta, st);
+  else if (per <= 8.0) launch_scatter_cells<T, CB, 8>(h, v, S, s, sv, sg, z, beta, st);
+  else if (per <= 16.0) launch_scatter_cells<T, CB, 16>(h, v, S, s, sv, sg, z, beta, st);
+  else launch_scatter_cells<T, CB, 32>(h, v, S, s, sv, sg, z, beta, st);
+  const dim3 gn((unsigned)((h->M + 255) / 256), (unsigned)((s + CB - 1) / CB));
+  k_scatter_nodes<T, CB><<<gn, 256, 0, st>>>(make_geo(h), S, grid, s, h->M, ncell);
+}
+}  // namespace
 
 int scatter_internal(dski_handle h, const void* vin, void* g, int s, bool prec64) {
   return scatter_internal_ws(h, vin, g, s, prec64, nullptr);
@@ -610,6 +759,30 @@ int scatter_fused(dski_handle h, const void* vin, void* g, int s, bool prec64, v
                   double sv, double sg, const double* z, const double* beta) {
   const MvmGeo geo = make_geo(h);
   cudaStream_t st = h->stream;
+  // FP32 vectors, d = 2: the per-cell two-pass scatter.  FP64 keeps the
+  // point-parallel prep + node pass below: on GB300 one warp-wide FP64
+  // instruction holds an SM sub-partition for ~64 cycles (ncu: FP64 pipe 83%
+  // active), and with ~1.5 points per cell the per-cell groups issue ~7 FP64
+  // warp instructions per point against ~1.4 there.
+  if (h->d == 2 && !prec64) {
+    if (z || sv != 1.0 || sg != 1.0)
+      return set_error(DSKI_ERR_ARG, "scaled / fused scatter needs FP64 vectors");
+    void* S = ws;
+    if (!S) {
+      if (h->scat_ab.ensure(scatter_ws_bytes(h, s, prec64)))
+        return set_error(DSKI_ERR_ALLOC, "scatter workspace allocation failed");
+      S = h->scat_ab.ptr;
+    }
+    StageScope sc(h, ST_SCATTER, st, 2);
+    if (s == 1)
+      scatter_cells_d2<float, 1>(h, (float*)vin, (float*)S, (float*)g, s, 1.f, 1.f, nullptr,
+                                 nullptr, st);
+    else
+      scatter_cells_d2<float, 4>(h, (float*)vin, (float*)S, (float*)g, s, 1.f, 1.f, nullptr,
+                                 nullptr, st);
+    DSKI_LAUNCHED();
+    return DSKI_OK;
+  }
   if (prec64 && h->d >= 2 && s <= 4) {
     double* ab = static_cast<double*>(ws);
     if (!ab) {
@@ -624,15 +797,19 @@ int scatter_fused(dski_handle h, const void* vin, void* g, int s, bool prec64, v
     if (h->d == 2) {
       k_scatter_prep<2><<<gp, 256, 0, st>>>(wt, (double*)vin, s, h->n, h->N, sv, sg, z, beta, ab);
       if (s == 1)
-        k_scatter_ab<2, 1><<<gs, 256, 0, st>>>(geo, h->cell_start.as<int>(), h->cell.as<int>(), wt, ab, (double*)g, s, h->n, h->M);
+        k_scatter_ab<2, 1><<<gs, 256, 0, st>>>(geo, h->cell_start.as<int>(), h->cell.as<int>(),
+                                               wt, ab, (double*)g, s, h->n, h->M);
       else
-        k_scatter_ab<2, 4><<<gs, 256, 0, st>>>(geo, h->cell_start.as<int>(), h->cell.as<int>(), wt, ab, (double*)g, s, h->n, h->M);
+        k_scatter_ab<2, 4><<<gs, 256, 0, st>>>(geo, h->cell_start.as<int>(), h->cell.as<int>(),
+                                               wt, ab, (double*)g, s, h->n, h->M);
     } else {
       k_scatter_prep<3><<<gp, 256, 0, st>>>(wt, (double*)vin, s, h->n, h->N, sv, sg, z, beta, ab);
       if (s == 1)
-        k_scatter_ab<3, 1><<<gs, 256, 0, st>>>(geo, h->cell_start.as<int>(), h->cell.as<int>(), wt, ab, (double*)g, s, h->n, h->M);
+        k_scatter_ab<3, 1><<<gs, 256, 0, st>>>(geo, h->cell_start.as<int>(), h->cell.as<int>(),
+                                               wt, ab, (double*)g, s, h->n, h->M);
       else
-        k_scatter_ab<3, 4><<<gs, 256, 0, st>>>(geo, h->cell_start.as<int>(), h->cell.as<int>(), wt, ab, (double*)g, s, h->n, h->M);
+        k_scatter_ab<3, 4><<<gs, 256, 0, st>>>(geo, h->cell_start.as<int>(), h->cell.as<int>(),
+                                               wt, ab, (double*)g, s, h->n, h->M);
     }
     DSKI_LAUNCHED();
     return DSKI_OK;
@@ -644,13 +821,14 @@ int scatter_fused(dski_handle h, const void* vin, void* g, int s, bool prec64, v
     switch (h->d) {
       case 1: scatter_dispatch<double, 1>(h, geo, fr, (const double*)vin, (double*)g, s, st); break;
       case 2: scatter_dispatch<double, 2>(h, geo, fr, (const double*)vin, (double*)g, s, st); break;
+
       default: scatter_dispatch<double, 3>(h, geo, fr, (const double*)vin, (double*)g, s, st); break;
     }
   } else {
     const float* fr = h->W32.as<float>();
     switch (h->d) {
       case 1: scatter_dispatch<float, 1>(h, geo, fr, (const float*)vin, (float*)g, s, st); break;
-      case 2: scatter_dispatch<float, 2>(h, geo, fr, (const float*)vin, (float*)g, s, st); break;
+
       default: scatter_dispatch<float, 3>(h, geo, fr, (const float*)vin, (float*)g, s, st); break;
     }
   }

@@ -15,7 +15,7 @@
 
 namespace {
 
-// Layout of one call: [vin | vout | gridA | gridB | scatter coefficients],
+// Layout of one call: [vin | vout | gridA | gridB | scatter intermediate],
 // each part padded to 256 bytes.
 constexpr size_t kScratchBytes = size_t(32) << 20;   // DSKI_NOALLOC_SCRATCH_BYTES
 static_assert(kScratchBytes == (size_t)DSKI_NOALLOC_SCRATCH_BYTES, "keep dski.h in sync");
@@ -59,7 +59,7 @@ extern "C" int dski_mvm_noalloc(dski_handle h, const void* v_dev, void* out_dev,
   if (s < 1) return set_error(DSKI_ERR_ARG, "dski_mvm_noalloc: s must be >= 1");
   if (h->prec == DSKI_FP64_TC)
     return set_error(DSKI_ERR_ARG,
-                     "dski_mvm_noalloc: FP64_TC mode needs digit workspace; use FP64 or MIXED");
+                     "dski_mvm_noalloc: FP64_TC mode needs a split-contraction workspace; use FP64 or MIXED");
   const bool f64 = f64_vectors(h);
   const size_t es = f64 ? 8 : 4;
   const size_t vbytes = (size_t)h->N * s * es;
@@ -69,7 +69,7 @@ extern "C" int dski_mvm_noalloc(dski_handle h, const void* v_dev, void* out_dev,
   if (need > kScratchBytes)
     return set_error(DSKI_ERR_ARG,
                      "dski_mvm_noalloc: needs %zu scratch bytes for s = %d, the fixed limit is %zu "
-                     "(2 N s + 2 M s elements and the scatter coefficients); use dski_mvm or "
+                     "(2 N s + 2 M s elements and the scatter intermediate); use dski_mvm or "
                      "fewer columns",
                      need, s, kScratchBytes);
   const char* a = (const char*)v_dev;

@@ -292,6 +292,8 @@ int grid_precond_apply(dski_handle h, pivchol_handle pc, const double* R, double
       g1.s = q;
       DSKI_TRY(oz_gemm(h, g1, ST_PRECOND));
       {
+        // two launches spread over ~13 SMs each: one block doing both ran the
+        // 36k FP64 FMAs on a single SM (~3x slower at GB300's FP64 rate)
         StageScope sc(h, ST_PRECOND, st, 2);
         k_grid_c<<<(q * r * 32 + 255) / 256, 256, 0, st>>>(pc->Hf.as<double>(), Yb, r, m0, q, cb);
         k_grid_x<<<(q * r * 32 + 255) / 256, 256, 0, st>>>(pc->Sg.as<double>(), cb, r, q, xb);

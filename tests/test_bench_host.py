@@ -64,3 +64,9 @@ def test_scatter_byte_count():
     import bench
     n, d, M = 100_000, 2, 65_536
     assert bench.scatter_bytes(n, d, M, 1, 8) == 3 * n * 8 + n * (4 + 16 * 8) + M * 8
+
+
+def test_gather_byte_count():
+    import bench
+    n, d, M = 100_000, 2, 65_536
+    assert bench.gather_bytes(n, d, M, 1, 4) == M * 4 + 2 * 3 * n * 4 + n * (4 + 16 * 4)
