@@ -62,6 +62,21 @@ def scatter_bytes(n, d, M, s, elem):
     return N * s * elem + n * (4 + 8 * d * elem) + M * s * elem
 
 
+OZ_PAIRS = 36   # digit pairs (a, b), a + b < 8, of the FP64_TC mode product
+# DRAM bytes (read + write) of one k_oz_mode mode product on the 256 x 256
+# terrain grid, from one ncu capture of the current kernel
+# (profiles/k_oz_mode_terrain2d_ncu.md): 1,626,880 read, 0 written
+OZ_MODE_TRAFFIC = 1_626_880
+
+
+def scatter_flops(n, d):
+    """Algorithmic FP64 flops of one d = 2 scatter in its sum-factorised form,
+    per point: 3 scalings, 4 c_a = w_a v0 + w'_a v1 (3 flops each), 4 e_a =
+    w_a v2, then 16 stencil nodes x (w1_b c_a + w1'_b e_a) (2 FMAs)."""
+    assert d == 2
+    return n * (3 + 4 * 3 + 4 + 16 * 4)
+
+
 def precond_bytes(N, r, s):
     """Algorithmic bytes of one preconditioner apply: Q1 (8 bytes per entry,
     FP64 or an FP32 hi/lo pair) read twice (Q1^T y, then y - Q1 c), r read
@@ -440,23 +455,41 @@ def main():
     stage_total_ms = {k: per_launch_ms[k] * v[1] for k, v in st.items()}
     # roofline of the dominant kernel (the ncu launch list of this command
     # ranks it first).  FP64: the Kronecker mode product k_mode_simt, one
-    # launch per mode product, 2 M m_k FP64 flops on the FP64 units.  FP64_TC
-    # and the mixed modes: the scatter's node pass k_scatter_ab, timed as one
-    # scatter (k_scatter_prep + k_scatter_ab, one stage scope of 2 launches)
-    # against the HBM model of one scatter (v read, per-point weights and
-    # cell ids read, grid written).
+    # launch per mode product, 2 M m_k FP64 flops on the FP64 units.  FP64_TC:
+    # the digit-product kernel k_oz_mode, one launch per mode product (the
+    # kron stage), OZ_PAIRS digit-pair BF16 products of 2 M m_k flops each
+    # against the measured sustained BF16 peak (timed inside a long step).
+    # The FP64 scatter is reported beside it against its FP64 flops.
+    # Mixed modes: the FP32 scatter against its HBM model.
+    fp64_peak_src = "nominal GB300 FP64 1.25 TFLOP/s (MEASURED_PEAKS has no FP64 entry; a DGEMM probe measured 1.05)"
+    roof_scatter = None
+    traffic = None
+    if args.prec in ("fp64", "fp64_tc"):
+        per_sc = 2 * per_launch_ms["scatter"] / 1e3
+        fl = scatter_flops(n, d)
+        roof_scatter = {"kernel": "k_scatter_prep + k_scatter_ab (scatter)", "bound": "alu",
+                        "achieved": fl / per_sc / 1e12, "peak": 1.25, "unit": "TFLOP/s",
+                        "frac": fl / per_sc / 1e12 / 1.25, "peak_source": fp64_peak_src,
+                        "algo_per_launch": fl}
     if args.prec == "fp64":
         per_s = per_launch_ms["kron"] / 1e3
         algo = 2 * M * p["m"][0]
         achieved = algo / per_s / 1e12
-        kern, bound, unit, peak = "k_mode_simt (kron)", "alu", "TFLOP/s", 1.25
-        peak_src = "nominal GB300 FP64 1.25 TFLOP/s (measured DGEMM 1.05)"
+        kern, bound, unit, peak, peak_src = "k_mode_simt (kron)", "alu", "TFLOP/s", 1.25, fp64_peak_src
+    elif args.prec == "fp64_tc":
+        per_s = per_launch_ms["kron"] / 1e3
+        algo = OZ_PAIRS * 2 * M * p["m"][0]
+        achieved = algo / per_s / 1e12
+        bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
+        kern, bound, unit, peak = "k_oz_mode (kron, one mode product)", "tensor", "TFLOP/s", bf16
+        traffic = OZ_MODE_TRAFFIC if M == 65_536 else None
+        peak_src = ("measured" if peaks.get("bf16_tflops_sustained") else "fallback") + \
+            " sustained dense BF16 (cuBLAS)"
     else:
         per_s = 2 * per_launch_ms["scatter"] / 1e3
-        elem = 8 if args.prec == "fp64_tc" else 4
-        algo = scatter_bytes(n, d, M, 1, elem)
+        algo = scatter_bytes(n, d, M, 1, 4)
         achieved = algo / per_s / 1e9
-        kern, bound, unit, peak, peak_src = ("k_scatter_prep + k_scatter_ab (scatter)", "hbm",
+        kern, bound, unit, peak, peak_src = ("k_scatter_cells + k_scatter_nodes (scatter)", "hbm",
                                              "GB/s", hbm, hbm_src + " HBM copy bandwidth")
     line = {
         "metric": METRIC, "value": t_step, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -472,9 +505,10 @@ def main():
         "stage_us_per_launch": {k: round(1e3 * v, 2) for k, v in per_launch_ms.items()},
         "stage_launches": {k: v[1] for k, v in st.items()},
         "mvm": mvm,
+        "roofline_scatter": roof_scatter,
         "roofline": {"kernel": kern, "bound": bound, "achieved": achieved,
                      "peak": peak, "peak_source": peak_src, "unit": unit,
-                     "frac": achieved / peak, "traffic": None, "algo_per_launch": algo},
+                     "frac": achieved / peak, "traffic": traffic, "algo_per_launch": algo},
         "e2e": {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": (n * d + N) * 8,
                 "d2h_bytes_per_step": N * 8, "iters": it_e, "relres": rr_e},
         "gpu_launches": launches // args.steps,

@@ -194,6 +194,28 @@ int dski_logdet_slq(dski_handle h, pivchol_handle pc, int probes, int depth, uin
 int dski_mll_grad(dski_handle h, pivchol_handle pc, const double* y_dev, int probes,
                   uint64_t seed, double* mll_host, double* grad_host);
 
+/* Prediction at n_star test points (Sec. 5: the mean, and the fast
+ * predictive-variance estimate, that Bayesian optimisation evaluates at many
+ * points).  The D-SKI cross-covariance of the test values / gradients with
+ * the training data is [W*; dW*] K_UU [W; dW]^T (Sec. 3.1), so
+ *   mean:      mu_star = [W*; dW*] K_UU [W; dW]^T alpha,
+ *   variance:  v_hat(x) = s_f^2 - k_x^T M^-1 k_x,  k_x = [W; dW] K_UU w*(x)^T,
+ * M = D + L L^T the pivoted-Cholesky preconditioner of `pc` (Sec. 5's first
+ * approach: K~^-1 replaced by the preconditioner solve).  M <= K~, so v_hat
+ * is at most the D-SKI variance s_f^2 - k_x^T K~^-1 k_x.
+ *   alpha_dev: N = n (d+1) FP64, caller block order (K~^-1 y, e.g. the x of
+ *              dski_pcg_solve with b = y); needed for the mean.
+ *   Xs_dev:    n_star x d FP64, row-major; every test point needs a full
+ *              stencil inside the grid (else DSKI_ERR_OUT_OF_GRID).
+ *   with_grad: 0: mean_dev holds n_star values; 1: n_star (d + 1) values in
+ *              block order [mean; its x_1 derivative; ...; its x_d derivative].
+ *   mean_dev / var_dev: device outputs (n_star FP64 for the variance); either
+ *              may be NULL (then that part is skipped).  var_dev needs pc.
+ * All arithmetic is FP64 whatever the handle's mode.  Synchronises the
+ * handle's stream.  Errors: ARG, OUT_OF_GRID, ALLOC, CUDA. */
+int dski_predict(dski_handle h, pivchol_handle pc, const double* alpha_dev, const double* Xs_dev,
+                 int n_star, int with_grad, double* mean_dev, double* var_dev);
+
 /* Profiling aid (the paper has no counterpart): per-stage device timers.
  * Stages, in order: 0 permute (user block order <-> internal layout),
  * 1 scatter, 2 Kronecker mode products, 3 gather (+ noise), 4 preconditioner

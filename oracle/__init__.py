@@ -21,6 +21,8 @@ solve   dense Cholesky, pivoted Cholesky, QR-form preconditioner, PCG (Sec. 2, 3
 slq     Lanczos-from-CG tridiagonals and stochastic Lanczos quadrature (Sec. 2)
 mll     log marginal likelihood and its hyperparameter gradient (Eq. 1)
 probes  counter-based SplitMix64 Rademacher probes (the random draws of SLQ)
+predict D-SKI predictive mean / gradient and the preconditioner variance
+        estimate, exact GP mean and D-SKI variance for the pins (Sec. 5)
 
 Pins: every routine is pinned in ``tests/test_oracle_*.py`` against closed
 forms, finite differences, invariants or brute force; none is "parity

@@ -189,6 +189,27 @@ class DSKI:
                                              C.c_uint64(seed), C.byref(mll), g))
         return mll.value, list(g)
 
+    def predict(self, alpha, Xs, pc=None, with_grad=True, variance=True):
+        """Mean (and gradient, block order) at the test points Xs (n* x d
+        CUDA float64) from alpha = K~^-1 y; with pc, the preconditioner
+        variance estimate as well.  Returns (mean, var or None)."""
+        Xs = Xs.to(device=self.device, dtype=torch.float64).contiguous()
+        if Xs.dim() != 2 or Xs.shape[1] != self.d:
+            raise ValueError(f"Xs must be n* x {self.d}")
+        ns = Xs.shape[0]
+        A = None if alpha is None else self._cols(alpha, torch.float64)
+        mean = None
+        if A is not None:
+            mean = torch.empty(ns * (self.d + 1) if with_grad else ns, device=self.device,
+                               dtype=torch.float64)
+        var = torch.empty(ns, device=self.device, dtype=torch.float64) if (pc is not None and variance) else None
+        _lib.check(_lib.load().dski_predict(self.h, pc.ptr if pc is not None else None,
+                                            _dptr(A) if A is not None else None, _dptr(Xs), ns,
+                                            1 if with_grad else 0,
+                                            _dptr(mean) if mean is not None else None,
+                                            _dptr(var) if var is not None else None))
+        return mean, var
+
 
 def launch_count():
     """Kernels the CUDA library has launched in this process."""

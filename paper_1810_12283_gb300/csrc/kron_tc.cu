@@ -179,11 +179,204 @@ __global__ void __launch_bounds__(128) k_mode_tc_tf32(const float* __restrict__ 
   if (warp == 0) tc::tmem_dealloc(tmem, TC_N);
 }
 
+__device__ __forceinline__ uint32_t cluster_rank_tf() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_tf() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+
+// The same product with the contraction split over a thread-block cluster:
+// CTA (j tile of 128, r tile of 32, column q, split ks of 32); K's hi (and
+// lo) planes of the split arrive by TMA (128-byte swizzle), the threads
+// split their slice of X into TF32 hi / lo, one thread issues 4 (x NMMA)
+// MMAs, each thread writes its row's 32 FP32 partials to an L2 workspace,
+// and after a cluster barrier every CTA sums a 1/KS share of the tile over
+// the splits in a fixed order (deterministic).  Grid (m/128, R/32, s KS),
+// cluster (1, 1, KS), KS = ceil(m / 32) <= 8.
+constexpr int TS_SMEM = 2 * A_BYTES + 2 * B_BYTES + 1024 + 64;
+template <int NMMA>
+__global__ void __launch_bounds__(128) k_mode_tc_tf32_split(
+    const __grid_constant__ CUtensorMap tHi, const __grid_constant__ CUtensorMap tLo,
+    const float* __restrict__ X, float* __restrict__ Y, float* __restrict__ P, int m, long long R,
+    int KS, float scale, int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sAh = smem;
+  unsigned char* sAl = sAh + A_BYTES;
+  unsigned char* sBh = sAl + A_BYTES;
+  unsigned char* sBl = sBh + B_BYTES;
+  uint64_t* full = (uint64_t*)(sBl + B_BYTES);
+  uint64_t* done = full + 1;
+  uint32_t* tslot = (uint32_t*)(full + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int j0 = blockIdx.x * TC_M;
+  const long long r0 = (long long)blockIdx.y * TC_N;
+  const int q = blockIdx.z / KS;
+  const uint32_t crank = cluster_rank_tf();
+  const int i0 = (int)crank * TC_KC;
+
+  if (warp == 0) tc::tmem_alloc(tslot, TC_N);
+  if (tid == 0) {
+    tc::mbar_init(full, 1);
+    tc::mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tslot;
+  if (tid == 0) {
+    tc::mbar_expect_tx(full, (uint32_t)(NMMA > 1 ? 2 * A_BYTES : A_BYTES));
+    tc::tma_load_2d(sAh, &tHi, i0, j0, full);
+    if (NMMA > 1) tc::tma_load_2d(sAl, &tLo, i0, j0, full);
+  }
+  // B: thread (row tid / 4, chunks 2 (tid % 4), +1) of the 32 x 32 slice
+  {
+    const int row = tid >> 2, c0 = (tid & 3) * 2;
+    const long long r = r0 + row;
+    const float* xr = X + ((long long)q * R + r) * m;
+#pragma unroll
+    for (int c = c0; c < c0 + 2; ++c) {
+      float4 h4, l4;
+      float* hv = &h4.x;
+      float* lv = &l4.x;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = i0 + 4 * c + e;
+        const float x = (r < R && i < m) ? xr[i] : 0.f;
+        const float hi = tc::rna_tf32(x);
+        hv[e] = hi;
+        lv[e] = tc::rna_tf32(x - hi);
+      }
+      *(float4*)(sBh + tc::sw128_off(row, c)) = h4;
+      if (NMMA > 1) *(float4*)(sBl + tc::sw128_off(row, c)) = l4;
+    }
+  }
+  tc::fence_proxy_async();
+  __syncthreads();
+  constexpr uint32_t idesc = tc::instr_desc(tc::kFmtTF32, TC_M, TC_N);
+  int ok = 1;
+  if (tid == 0) {
+    if (tc::mbar_wait(full, 0, WAIT_LIMIT)) {
+      tc::fence_after();
+      const uint32_t aH = tc::smem_u32(sAh), aL = tc::smem_u32(sAl);
+      const uint32_t bH = tc::smem_u32(sBh), bL = tc::smem_u32(sBl);
+#pragma unroll
+      for (int kk = 0; kk < TC_KC / 8; ++kk) {
+        const uint32_t ko = kk * 32;   // 8 TF32 = 32 bytes per MMA
+        tc::mma_tf32(tmem, tc::sw128_desc(aH + ko), tc::sw128_desc(bH + ko), idesc, kk > 0 ? 1u : 0u);
+        if (NMMA > 1) {
+          tc::mma_tf32(tmem, tc::sw128_desc(aH + ko), tc::sw128_desc(bL + ko), idesc, 1u);
+          tc::mma_tf32(tmem, tc::sw128_desc(aL + ko), tc::sw128_desc(bH + ko), idesc, 1u);
+        }
+      }
+    } else {
+      ok = 0;
+      tc::mbar_wait(full, 0, WAIT_LIMIT);   // let the loads land (bounded)
+    }
+    tc::commit(done);
+  }
+  __syncthreads();
+  int fin = tc::mbar_wait(done, 0, WAIT_LIMIT) ? 1 : 0;
+  fin = __syncthreads_and(fin && (tid != 0 || ok));
+  tc::fence_after();
+  const long long tile = ((long long)q * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  float* Pt = P + tile * KS * (TC_M * TC_N);
+  {
+    float* Pw = Pt + (long long)crank * (TC_M * TC_N) + warp * 32 + lane;   // (column, row)
+#pragma unroll
+    for (int c16 = 0; c16 < TC_N / 16; ++c16) {
+      uint32_t v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c16 * 16, v);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) __stcg(Pw + (c16 * 16 + e) * TC_M, fin ? __uint_as_float(v[e]) : 0.f);
+    }
+  }
+  if (!fin && tid == 0) atomicExch(err, 1);
+  cluster_sync_tf();   // every split's partials are written
+  {
+    const int rb = (int)((crank * TC_M) / KS), re = (int)(((crank + 1) * TC_M) / KS);
+    const int nr = re - rb;
+    const long long MR = (long long)m * R;
+    for (int it = tid; it < nr * TC_N; it += 128) {
+      const int row = rb + it % nr, col = it / nr;
+      const int off = col * TC_M + row;
+      float sum = 0.f;
+#pragma unroll
+      for (int src = 0; src < 8; ++src)
+        if (src < KS) sum += __ldcg(Pt + (long long)src * (TC_M * TC_N) + off);
+      const int j = j0 + row;
+      const long long r = r0 + col;
+      if (j < m && r < R) Y[(long long)q * MR + (long long)j * R + r] = scale * sum;
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, TC_N);
+}
+
 }  // namespace
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 
 // One mode product on the tensor cores (mixed modes).  Returns DSKI_OK or CUDA.
 int mode_tc_tf32(dski_handle h, const float* X, const float* Khi, const float* Klo, float* Y,
                  int m, long long R, int s, float scale, bool three) {
+  auto enc = tensor_map_encoder();
+  if (enc && m % 4 == 0 && m <= 256) {
+    // split contraction over a cluster, K by TMA
+    CUtensorMap tHi, tLo;
+    const cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)m};
+    const cuuint64_t str[1] = {(cuuint64_t)m * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)TC_KC, (cuuint32_t)TC_M};
+    const cuuint32_t estr[2] = {1, 1};
+    for (int t = 0; t < 2; ++t) {
+      const CUresult r = enc(t ? &tLo : &tHi, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                             const_cast<float*>(t ? Klo : Khi), dims, str, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS)
+        return set_error(DSKI_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    }
+    static bool attr_split = false;
+    if (!attr_split) {
+      cudaFuncSetAttribute(k_mode_tc_tf32_split<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TS_SMEM);
+      cudaFuncSetAttribute(k_mode_tc_tf32_split<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, TS_SMEM);
+      attr_split = true;
+    }
+    const int KS = (m + TC_KC - 1) / TC_KC;
+    const long long tiles = (long long)s * ((m + TC_M - 1) / TC_M) * ((R + TC_N - 1) / TC_N);
+    if (h->ozP.ensure((size_t)tiles * KS * TC_M * TC_N * 4))
+      return set_error(DSKI_ERR_ALLOC, "tensor-core workspace allocation failed");
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)((m + TC_M - 1) / TC_M), (unsigned)((R + TC_N - 1) / TC_N),
+                       (unsigned)(s * KS));
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = TS_SMEM;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = (unsigned)KS;
+    attr[1].id = cudaLaunchAttributeClusterSchedulingPolicyPreference;
+    attr[1].val.clusterSchedulingPolicyPreference = cudaClusterSchedulingPolicyLoadBalancing;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    StageScope sc(h, ST_KRON, h->stream);
+    const cudaError_t e =
+        three ? cudaLaunchKernelEx(&cfg, k_mode_tc_tf32_split<3>, tHi, tLo, X, Y, h->ozP.as<float>(),
+                                   m, R, KS, scale, h->dev_err.as<int>())
+              : cudaLaunchKernelEx(&cfg, k_mode_tc_tf32_split<1>, tHi, tLo, X, Y, h->ozP.as<float>(),
+                                   m, R, KS, scale, h->dev_err.as<int>());
+    if (e != cudaSuccess)
+      return set_error(DSKI_ERR_CUDA, "TF32 mode product launch: %s", cudaGetErrorString(e));
+    return DSKI_OK;
+  }
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_mode_tc_tf32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);

@@ -70,3 +70,8 @@ def test_gather_byte_count():
     import bench
     n, d, M = 100_000, 2, 65_536
     assert bench.gather_bytes(n, d, M, 1, 4) == M * 4 + 2 * 3 * n * 4 + n * (4 + 16 * 4)
+
+
+def test_scatter_flop_count():
+    import bench
+    assert bench.scatter_flops(100_000, 2) == 100_000 * 83
