@@ -28,6 +28,7 @@ void clear_error() { g_err[0] = '\0'; }
 static std::atomic<long long> g_launches{0};
 
 void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 struct Profiler {
   static constexpr size_t kMaxPairs = 1u << 18;
@@ -72,6 +73,8 @@ struct Profiler {
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
   }
 };
+
+bool profiling_on(dski_handle h) { return h && h->prof && h->prof->active; }
 
 void stage_begin(dski_handle h, int stage, cudaStream_t st) {
   Profiler* p = h ? h->prof : nullptr;
@@ -347,6 +350,12 @@ int check_device_error(dski_handle h) {
 extern "C" void dski_destroy(dski_handle h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  if (h->pstream) {
+    cudaStreamSynchronize(h->pstream);
+    cudaStreamDestroy(h->pstream);
+  }
+  if (h->pev_in) cudaEventDestroy(h->pev_in);
+  if (h->pev_out) cudaEventDestroy(h->pev_out);
   delete h->prof;
   h->prof = nullptr;
   release_all(h);

@@ -50,6 +50,8 @@ static_assert(ST_COUNT == DSKI_NSTAGES, "stage table out of sync with dski.h");
 
 struct Profiler;   // defined in capi.cu
 void count_launches(int k);   // adds to the process-wide launch counter
+long long launches_so_far();  // the process-wide launch counter
+bool profiling_on(dski_handle h);   // stage timers recording
 void stage_begin(dski_handle h, int stage, cudaStream_t st);
 void stage_end(dski_handle h, int stage, cudaStream_t st, int launches);
 
@@ -90,6 +92,10 @@ struct dski_handle_ {
   // FP64_TC: run the mode products on the FP64 units instead (true residuals)
   bool kron_exact = false;
   cudaStream_t stream = nullptr;
+  // private non-blocking stream for the captured PCG chunks (the legacy
+  // default stream cannot be captured), ordered against `stream` by events
+  cudaStream_t pstream = nullptr;
+  cudaEvent_t pev_in = nullptr, pev_out = nullptr;
   int M = 0;        // grid size prod m_k
   int ncell = 0;    // prod mc_k
   int sm_count = 0;

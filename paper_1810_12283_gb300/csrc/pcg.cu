@@ -498,6 +498,59 @@ int cg_run(dski_handle h, CgRun& run) {
     return DSKI_OK;
   };
 
+  // A CUDA graph of one 16-iteration chunk, captured once the first chunk
+  // has run (its launches allocate the workspaces and run the tile tuner)
+  // and replayed for every later full chunk: the chunk's ~250 launches then
+  // cost one.  Off while the stage timers record (their events) and while
+  // Lanczos coefficients are recorded (the depth travels in the kernels'
+  // arguments), and on a stream that cannot be captured.
+  cudaGraphExec_t gexec = nullptr;
+  long long glaunches = 0;
+  bool gtried = false;
+  int chunks_run = 0;
+  struct GraphGuard {
+    cudaGraphExec_t* g;
+    ~GraphGuard() {
+      if (*g) cudaGraphExecDestroy(*g);
+    }
+  } gguard{&gexec};
+  auto run_chunk = [&](int chunk) -> int {
+    const bool can = chunk == 16 && depth == 0 && chunks_run >= 1 && !profiling_on(h) &&
+                     st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
+    if (can && !gexec && !gtried) {
+      gtried = true;
+      const long long l0 = launches_so_far();
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        int rc = DSKI_OK;
+        for (int k = 0; k < chunk && rc == DSKI_OK; ++k) rc = iteration();
+        const cudaError_t ce = cudaStreamEndCapture(st, &g);
+        const long long captured = launches_so_far() - l0;
+        count_launches((int)-captured);   // recorded into the graph, not run
+        if (rc == DSKI_OK && ce == cudaSuccess && g &&
+            cudaGraphInstantiate(&gexec, g, 0) == cudaSuccess)
+          glaunches = captured;
+        else
+          gexec = nullptr;
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        clear_error();
+      } else {
+        cudaGetLastError();
+      }
+    }
+    ++chunks_run;
+    if (gexec) {
+      if (cudaGraphLaunch(gexec, st) != cudaSuccess)
+        return set_error(DSKI_ERR_CUDA, "dski_pcg_solve: graph launch: %s",
+                         cudaGetErrorString(cudaGetLastError()));
+      count_launches((int)glaunches);
+      return DSKI_OK;
+    }
+    for (int k = 0; k < chunk; ++k) DSKI_TRY(iteration());
+    return DSKI_OK;
+  };
+
   int its = 0, restarts = 0, nact = 0;
   const int max_restarts = mixed ? 200 : 64;
   DSKI_TRY(true_residual(1));
@@ -506,7 +559,7 @@ int cg_run(dski_handle h, CgRun& run) {
     DSKI_TRY(precond_z(1));   // p = M^-1 r
     while (its < run.maxit) {
       const int chunk = std::min(16, run.maxit - its);
-      for (int k = 0; k < chunk; ++k) DSKI_TRY(iteration());
+      DSKI_TRY(run_chunk(chunk));
       its += chunk;
       DSKI_TRY(read_nactive(&nact));
       if (nact == 0) break;
@@ -567,6 +620,29 @@ extern "C" int dski_pcg_solve(dski_handle h, pivchol_handle pc, const double* b_
   if (s < 1 || s > 256) return set_error(DSKI_ERR_ARG, "dski_pcg_solve: s must be in 1..256");
   if (!(rtol > 0.0) || maxit < 1) return set_error(DSKI_ERR_ARG, "dski_pcg_solve: need rtol > 0, maxit >= 1");
   if (pc && pc->h != h) return set_error(DSKI_ERR_ARG, "dski_pcg_solve: preconditioner of another handle");
+  // run on the handle's private stream (capturable), ordered after the
+  // caller's stream by an event and before its later work by another
+  cudaStream_t user = h->stream;
+  if (!h->pstream) {
+    if (cudaStreamCreateWithFlags(&h->pstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->pev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->pev_out, cudaEventDisableTiming) != cudaSuccess)
+      return set_error(DSKI_ERR_CUDA, "dski_pcg_solve: stream creation failed: %s",
+                       cudaGetErrorString(cudaGetLastError()));
+  }
+  if (cudaEventRecord(h->pev_in, user) != cudaSuccess ||
+      cudaStreamWaitEvent(h->pstream, h->pev_in, 0) != cudaSuccess)
+    return set_error(DSKI_ERR_CUDA, "dski_pcg_solve: %s", cudaGetErrorString(cudaGetLastError()));
+  h->stream = h->pstream;
+  struct StreamBack {
+    dski_handle h;
+    cudaStream_t user;
+    ~StreamBack() {
+      cudaEventRecord(h->pev_out, h->pstream);
+      cudaStreamWaitEvent(user, h->pev_out, 0);
+      h->stream = user;
+    }
+  } back{h, user};
   const size_t Ns = (size_t)h->N * s;
   double* Bi = wbuf(h->s_vec[8], Ns);
   double* Xi = wbuf(h->s_vec[9], Ns);
