@@ -38,6 +38,7 @@ import numpy as np  # noqa: E402
 METRIC = "PCG solve time to rel. residual 1e-8, terrain n=100k d=2 (GB300, tensor-core FP64_TC vs FP64)"
 UNIT = "s"
 RANK = 100
+PROF_ITERS = 3000   # PCG iterations of the profiled (untimed) step
 RTOL = 1e-8
 
 
@@ -403,19 +404,23 @@ def main():
                 "stages_us": {k: round(1e3 * v[0] / max(v[2], 1) * v[1] / reps, 2)
                               for k, v in st.items() if v[1]}}
 
+    # timed steps with the stage timers off: the PCG chunks then replay as
+    # CUDA graphs (the timers' events would disable them)
     with ClockSampler(local) as clk:
-        ms, its, rrs, stages, launches = timed_steps(args.prec, args.warmup, args.steps, True)
+        ms, its, rrs, _, launches = timed_steps(args.prec, args.warmup, args.steps, False)
     clocks = clk.summary()
+    # stage data from one more, untimed step with the timers on, its PCG
+    # capped at PROF_ITERS iterations
+    prof_iters = min(PROF_ITERS, max(its[-1], 1))
+    _, _, _, stages, _ = timed_steps(args.prec, 0, 1, True, maxit=prof_iters)
     compare = {}
     for mode in [m for m in args.compare.split(",") if m and m != args.prec]:
         try:
             cap = args.maxit if mode in ("fp64", "fp64_tc") else min(int(1.5 * its[-1]) + 100, 30000)
-            msc, itc, rrc, stc, _ = timed_steps(mode, 0, 1, True, maxit=cap)
+            msc, itc, rrc, _, _ = timed_steps(mode, 0, 1, False, maxit=cap)
             compare[mode] = {"s_per_step": msc[-1] / 1e3, "iters": itc[-1], "relres": rrc[-1],
                              "reached_rtol": rrc[-1] <= RTOL,
-                             "s_per_iter": msc[-1] / 1e3 / max(itc[-1], 1),
-                             "stages_ms": {k: round(v[0] / max(v[2], 1) * v[1], 1)
-                                           for k, v in stc.items() if v[1]}}
+                             "s_per_iter": msc[-1] / 1e3 / max(itc[-1], 1)}
         except Exception as e:   # noqa: BLE001 -- reported, not fatal
             compare[mode] = {"error": str(e)}
     mvm = {prec: mvm_rate(prec) for prec in ("fp64", "fp64_tc", "mixed_3xtf32")}
@@ -448,11 +453,12 @@ def main():
     hbm = peaks.get("hbm_gbs") or 6800.0
     hbm_src = "measured" if peaks.get("hbm_gbs") else "fallback"
     it_last = its[-1]
-    # per stage: mean device time per launch (over the timed launches) and the
-    # step's total, extrapolated to every launch of the stage
+    # per stage (profiled step: set-up + prof_iters PCG iterations): mean
+    # device time per launch, and per PCG iteration for the iteration stages
     st = {k: v for k, v in stages.items() if v[1]}
     per_launch_ms = {k: v[0] / max(v[2], 1) for k, v in st.items()}
     stage_total_ms = {k: per_launch_ms[k] * v[1] for k, v in st.items()}
+    iter_stages = ("scatter", "kron", "gather", "precond", "pcg_vec")
     # roofline of the dominant kernel (the ncu launch list of this command
     # ranks it first).  FP64: the Kronecker mode product k_mode_simt, one
     # launch per mode product, 2 M m_k FP64 flops on the FP64 units.  FP64_TC:
@@ -501,9 +507,12 @@ def main():
         "solve": {"iters": its, "relres": rrs, "s_per_iter": t_step / it_last,
                   "reached_rtol": all(r <= RTOL for r in rrs)},
         "compare": compare,
-        "stages_ms": {k: round(v, 1) for k, v in stage_total_ms.items()},
-        "stage_us_per_launch": {k: round(1e3 * v, 2) for k, v in per_launch_ms.items()},
-        "stage_launches": {k: v[1] for k, v in st.items()},
+        "profiled_step": {"pcg_iters": prof_iters,
+                          "note": "stage timers on (CUDA graphs off); not part of value",
+                          "stage_us_per_launch": {k: round(1e3 * v, 2) for k, v in per_launch_ms.items()},
+                          "stage_launches": {k: v[1] for k, v in st.items()},
+                          "stage_us_per_iter": {k: round(1e3 * stage_total_ms[k] / prof_iters, 1)
+                                                for k in iter_stages if k in stage_total_ms}},
         "mvm": mvm,
         "roofline_scatter": roof_scatter,
         "roofline": {"kernel": kern, "bound": bound, "achieved": achieved,

@@ -158,6 +158,7 @@ static void release_all(dski_handle h) {
   h->dev_err.release();
   h->scat_ab.release();
   h->ozP.release();
+  h->s_dpart.release();
   h->s_part.release();
   h->s_tnpart.release();
   h->s_ticket.release();

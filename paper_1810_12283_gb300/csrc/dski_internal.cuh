@@ -112,6 +112,8 @@ struct dski_handle_ {
   dski::DevBuf Kdig[DSKI_MAXD], Kexp[DSKI_MAXD];
   // FP64_TC: split-K partial sums of the mode products (workspace)
   dski::DevBuf ozP;
+  // PCG: per-block partial sums of the dots fused into other kernels
+  dski::DevBuf s_dpart;
   // FP64 scatter: per-point sum-factorised coefficients (workspace)
   dski::DevBuf scat_ab;
   // workspace
@@ -143,19 +145,35 @@ int scatter_internal(dski_handle h, const void* vin, void* g, int s, bool prec64
 // `ws` (scatter_ws_bytes bytes; NULL = the handle's workspace)
 int scatter_internal_ws(dski_handle h, const void* vin, void* g, int s, bool prec64, void* ws);
 size_t scatter_ws_bytes(dski_handle h, int s, bool prec64);
+// A CG update fused into the scatter's point pass (FP64, d >= 2, s <= 4):
+// for every active column q, x += alpha_q p and r -= alpha_q q on the scattered
+// vector r (written back) before it is scattered, and per-block partial sums
+// of ||r||^2 to dpart[q nblocks + block] (nblocks = ceil(n / 256)).
+struct CgUpdate {
+  double* x = nullptr;   // NULL: no update
+  const double* p = nullptr;
+  const double* q = nullptr;
+  const double* alpha = nullptr;
+  const int* active = nullptr;
+  double* dpart = nullptr;
+};
 // FP64 scatter of (sv v^0, sg v^1..d) (FP64, d >= 2, s <= 4 when scaled)
 int scatter_scaled(dski_handle h, const void* vin, void* g, int s, bool prec64, void* ws,
-                   double sv, double sg);
+                   double sv, double sg, const CgUpdate* up = nullptr);
 // as scatter_scaled; with z != NULL first v <- z + beta_q v (written back)
 int scatter_fused(dski_handle h, const void* vin, void* g, int s, bool prec64, void* ws,
-                  double sv, double sg, const double* z, const double* beta);
-// PCG: P <- Z + beta P fused into the FP64 MVM Q = K~ P (when pcg_fusable)
+                  double sv, double sg, const double* z, const double* beta,
+                  const CgUpdate* up = nullptr);
+// PCG: P <- Z + beta P fused into the FP64 MVM Q = K~ P (when pcg_fusable);
+// with dpart, the gather leaves per-block partial sums of p^T q there
 bool pcg_fusable(dski_handle h, int s);
 int mvm_pcg_fused(dski_handle h, double* P, const double* Z, const double* beta, double* Q,
-                  int s);
-// FP64 gather: vout^0 = av (B grid)^0 + nv vin^0, vout^p = ag (B grid)^p + ng vin^p
+                  int s, double* dpart = nullptr);
+// FP64 gather: vout^0 = av (B grid)^0 + nv vin^0, vout^p = ag (B grid)^p + ng vin^p;
+// with dpart, per-block partial sums of vin^T vout per column
+// (dpart[q nblocks + block], nblocks = ceil(n / 256))
 int gather_scaled(dski_handle h, const double* grid, const double* vin, double* vout, int s,
-                  double av, double ag, double nv, double ng, int stage);
+                  double av, double ag, double nv, double ng, int stage, double* dpart = nullptr);
 int kron_internal(dski_handle h, void* g, void* tmp, int s, bool prec64, int dfactor,
                   const void* dK, void** result);
 
@@ -174,6 +192,8 @@ int mode_tc_tf32(dski_handle h, const float* X, const float* Khi, const float* K
 // and one mode product;
 // a factor's digit planes take kOzDigits x m x m BF16 values
 constexpr int kOzDigits = 8;
+// smallest mode size whose FP64_TC products take the tensor cores
+constexpr int kOzMinM = 64;
 int oz_slice_factor(dski_handle h, const double* K, int m, uint16_t* Ad, int* fA);
 int mode_tc_oz(dski_handle h, const double* X, const uint16_t* Ad, const int* fA, double* Y,
                int m, long long R, int s, double scale);

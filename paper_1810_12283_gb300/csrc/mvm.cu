@@ -166,18 +166,34 @@ __global__ void __launch_bounds__(256) k_scatter_prep(const double* __restrict__
                                                       int n, long long N, double sv, double sg,
                                                       const double* __restrict__ z,
                                                       const double* __restrict__ beta,
-                                                      double* __restrict__ ab) {
+                                                      double* __restrict__ ab, CgUpdate up) {
   constexpr int NC = D == 2 ? 8 : 32;   // coefficients per point and column
-  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+  const long long jt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = jt < n;
+  double rsum[4] = {0.0, 0.0, 0.0, 0.0};   // ||r||^2 partials (fused CG update, s <= 4)
+  const long long j = live ? jt : 0;
   const double* wj = wt + j * (8 * D);
-  for (int q = 0; q < s; ++q) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {   // s <= 4 on this path
+    if (q >= s || !live) break;
     double* vq0 = v + (long long)q * N + j * (D + 1);
     if (z) {
       const double* zq = z + (long long)q * N + j * (D + 1);
       const double be = beta[q];
 #pragma unroll
       for (int c = 0; c <= D; ++c) vq0[c] = fma(be, vq0[c], zq[c]);
+    }
+    if (up.x && up.active[q]) {
+      // x += alpha p, r -= alpha q (v is r), ||r||^2
+      const long long o = (long long)q * N + j * (D + 1);
+      const double al = up.alpha[q];
+#pragma unroll
+      for (int c = 0; c <= D; ++c) {
+        up.x[o + c] = fma(al, up.p[o + c], up.x[o + c]);
+        const double ri = fma(-al, up.q[o + c], vq0[c]);
+        vq0[c] = ri;
+        rsum[q] = fma(ri, ri, rsum[q]);
+      }
     }
     double vq[D + 1];
     vq[0] = sv * vq0[0];
@@ -204,7 +220,25 @@ __global__ void __launch_bounds__(256) k_scatter_prep(const double* __restrict__
       }
     }
   }
+  if (up.x) {
+    __shared__ double red[8][4];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      double t = rsum[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) red[w][q] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4 && (int)threadIdx.x < s) {
+      double t = 0.0;
+      for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t += red[ww][threadIdx.x];
+      up.dpart[(long long)threadIdx.x * gridDim.x + blockIdx.x] = t;
+    }
+  }
 }
+
 
 template <int D, int CB>
 __global__ void __launch_bounds__(256) k_scatter_ab(MvmGeo g, const int* __restrict__ cell_start,
@@ -407,10 +441,14 @@ __global__ void __launch_bounds__(256) k_gather(MvmGeo g, const int* __restrict_
                                                 const T* __restrict__ grid,
                                                 const T* __restrict__ v, T* __restrict__ out,
                                                 int s, int n, long long N, long long M, T nv,
-                                                T ng, T av, T ag) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+                                                T ng, T av, T ag, double* __restrict__ dpart) {
+  const int jt = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = jt < n;
+  const int j = live ? jt : n - 1;   // dead threads redo the last point, write nothing
   const int q0 = blockIdx.y * CB;
+  double dsum[CB];
+#pragma unroll
+  for (int q = 0; q < CB; ++q) dsum[q] = 0.0;
   int f[3] = {0, 0, 0};
   {
     int t = cell[j];
@@ -490,9 +528,36 @@ __global__ void __launch_bounds__(256) k_gather(MvmGeo g, const int* __restrict_
     }
     const T* vq = v + (long long)(q0 + q) * N + e;
     T* oq = out + (long long)(q0 + q) * N + e;
-    oq[0] = av * r[0] + nv * vq[0];
+    T o[D + 1];
+    o[0] = av * r[0] + nv * vq[0];
 #pragma unroll
-    for (int cc = 1; cc <= D; ++cc) oq[cc] = ag * r[cc] + ng * vq[cc];
+    for (int cc = 1; cc <= D; ++cc) o[cc] = ag * r[cc] + ng * vq[cc];
+    if (live) {
+#pragma unroll
+      for (int cc = 0; cc <= D; ++cc) oq[cc] = o[cc];
+      if (dpart)
+#pragma unroll
+        for (int cc = 0; cc <= D; ++cc) dsum[q] = fma((double)vq[cc], (double)o[cc], dsum[q]);
+    }
+  }
+  // optional: per-block partial sums of v^T out per column (fixed tree),
+  // dpart[q gridDim.x + block] -- the CG dot fused into the gather
+  if (dpart) {
+    __shared__ double red[8][CB];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < CB; ++q) {
+      double t = dsum[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) red[w][q] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < CB && q0 + (int)threadIdx.x < s) {
+      double t = 0.0;
+      for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t += red[ww][threadIdx.x];
+      dpart[(long long)(q0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+    }
   }
 }
 
@@ -593,6 +658,7 @@ struct GatherScale {
   double av = 1.0, ag = 1.0;   // multiply B h on value / gradient rows
   double nv = 0.0, ng = 0.0;   // multiply v on value / gradient rows
   int stage = ST_GATHER;
+  double* dpart = nullptr;     // per-block partial sums of v^T out (FP64 only)
 };
 
 template <class T, int D, int CB>
@@ -602,7 +668,7 @@ void launch_gather(dski_handle h, const MvmGeo& g, const T* wt, const T* grid, c
   StageScope sc(h, gs.stage, st);
   k_gather<T, D, CB><<<grd, 256, 0, st>>>(g, h->cell.as<int>(), wt, grid, v, out, s, h->n,
                                           (long long)h->N, (long long)h->M, (T)gs.nv, (T)gs.ng,
-                                          (T)gs.av, (T)gs.ag);
+                                          (T)gs.av, (T)gs.ag, gs.dpart);
 }
 
 template <class T, int D>
@@ -751,12 +817,13 @@ int scatter_internal_ws(dski_handle h, const void* vin, void* g, int s, bool pre
 }
 
 int scatter_scaled(dski_handle h, const void* vin, void* g, int s, bool prec64, void* ws,
-                   double sv, double sg) {
-  return scatter_fused(h, vin, g, s, prec64, ws, sv, sg, nullptr, nullptr);
+                   double sv, double sg, const CgUpdate* up) {
+  return scatter_fused(h, vin, g, s, prec64, ws, sv, sg, nullptr, nullptr, up);
 }
 
 int scatter_fused(dski_handle h, const void* vin, void* g, int s, bool prec64, void* ws,
-                  double sv, double sg, const double* z, const double* beta) {
+                  double sv, double sg, const double* z, const double* beta, const CgUpdate* up) {
+  const CgUpdate upd = up ? *up : CgUpdate{};
   const MvmGeo geo = make_geo(h);
   cudaStream_t st = h->stream;
   // FP32 vectors, d = 2: the per-cell two-pass scatter.  FP64 keeps the
@@ -764,6 +831,8 @@ int scatter_fused(dski_handle h, const void* vin, void* g, int s, bool prec64, v
   // instruction holds an SM sub-partition for ~64 cycles (ncu: FP64 pipe 83%
   // active), and with ~1.5 points per cell the per-cell groups issue ~7 FP64
   // warp instructions per point against ~1.4 there.
+  if (up && !(prec64 && h->d >= 2 && s <= 4))
+    return set_error(DSKI_ERR_ARG, "fused CG update needs FP64, d >= 2 and s <= 4");
   if (h->d == 2 && !prec64) {
     if (z || sv != 1.0 || sg != 1.0)
       return set_error(DSKI_ERR_ARG, "scaled / fused scatter needs FP64 vectors");
@@ -795,7 +864,7 @@ int scatter_fused(dski_handle h, const void* vin, void* g, int s, bool prec64, v
     const dim3 gs((unsigned)((h->M * 4 + 255) / 256), 1);
     StageScope sc(h, ST_SCATTER, st, 2);
     if (h->d == 2) {
-      k_scatter_prep<2><<<gp, 256, 0, st>>>(wt, (double*)vin, s, h->n, h->N, sv, sg, z, beta, ab);
+      k_scatter_prep<2><<<gp, 256, 0, st>>>(wt, (double*)vin, s, h->n, h->N, sv, sg, z, beta, ab, upd);
       if (s == 1)
         k_scatter_ab<2, 1><<<gs, 256, 0, st>>>(geo, h->cell_start.as<int>(), h->cell.as<int>(),
                                                wt, ab, (double*)g, s, h->n, h->M);
@@ -803,7 +872,7 @@ int scatter_fused(dski_handle h, const void* vin, void* g, int s, bool prec64, v
         k_scatter_ab<2, 4><<<gs, 256, 0, st>>>(geo, h->cell_start.as<int>(), h->cell.as<int>(),
                                                wt, ab, (double*)g, s, h->n, h->M);
     } else {
-      k_scatter_prep<3><<<gp, 256, 0, st>>>(wt, (double*)vin, s, h->n, h->N, sv, sg, z, beta, ab);
+      k_scatter_prep<3><<<gp, 256, 0, st>>>(wt, (double*)vin, s, h->n, h->N, sv, sg, z, beta, ab, upd);
       if (s == 1)
         k_scatter_ab<3, 1><<<gs, 256, 0, st>>>(geo, h->cell_start.as<int>(), h->cell.as<int>(),
                                                wt, ab, (double*)g, s, h->n, h->M);
@@ -848,7 +917,10 @@ int kron_internal(dski_handle h, void* g, void* tmp, int s, bool prec64, int dfa
     const long long R = h->M / h->m[k];
     const bool last = t == h->d - 1;
     const double scale = last ? h->sf * h->sf : 1.0;
-    if (prec64 && h->prec == DSKI_FP64_TC && dfactor < 0 && !h->kron_exact) {
+    // FP64_TC: the tensor-core product from m_k = 64 on; below, its fixed
+    // per-CTA latency (~10 us) exceeds the FP64 product (~8 us at m_k = 24)
+    if (prec64 && h->prec == DSKI_FP64_TC && dfactor < 0 && !h->kron_exact &&
+        h->m[k] >= kOzMinM) {
       DSKI_TRY(mode_tc_oz(h, (const double*)cur, h->Kdig[k].as<uint16_t>(), h->Kexp[k].as<int>(),
                           (double*)nxt, h->m[k], R, s, scale));
     } else if (prec64) {
@@ -902,7 +974,7 @@ int mvm_internal(dski_handle h, const void* vin, void* vout, int s, bool prec64)
 }
 
 int gather_scaled(dski_handle h, const double* grid, const double* vin, double* vout, int s,
-                  double av, double ag, double nv, double ng, int stage) {
+                  double av, double ag, double nv, double ng, int stage, double* dpart) {
   const MvmGeo geo = make_geo(h);
   GatherScale gs;
   gs.av = av;
@@ -910,6 +982,7 @@ int gather_scaled(dski_handle h, const double* grid, const double* vin, double* 
   gs.nv = nv;
   gs.ng = ng;
   gs.stage = stage;
+  gs.dpart = dpart;
   const double* fr = h->W64.as<double>();
   switch (h->d) {
     case 1: gather_dispatch<double, 1>(h, geo, fr, grid, vin, vout, s, h->stream, &gs); break;
@@ -946,14 +1019,16 @@ int gather_internal(dski_handle h, const void* grid, const void* vin, void* vout
 bool pcg_fusable(dski_handle h, int s) { return f64_vectors(h) && h->d >= 2 && s <= 4; }
 
 int mvm_pcg_fused(dski_handle h, double* P, const double* Z, const double* beta, double* Q,
-                  int s) {
+                  int s, double* dpart) {
   const size_t gbytes = (size_t)h->M * s * 8;
   if (h->gridA.ensure(gbytes) || h->gridB.ensure(gbytes))
     return set_error(DSKI_ERR_ALLOC, "grid workspace allocation failed (%zu bytes)", gbytes);
-  DSKI_TRY(scatter_fused(h, P, h->gridA.ptr, s, true, nullptr, 1.0, 1.0, Z, beta));
+  DSKI_TRY(scatter_fused(h, P, h->gridA.ptr, s, true, nullptr, 1.0, 1.0, Z, beta, nullptr));
   void* res = nullptr;
   DSKI_TRY(kron_internal(h, h->gridA.ptr, h->gridB.ptr, s, true, -1, nullptr, &res));
-  return gather_internal(h, res, P, Q, s, true);
+  if (!dpart) return gather_internal(h, res, P, Q, s, true);
+  // the gather also leaves per-block partial sums of p^T q
+  return gather_scaled(h, (const double*)res, P, Q, s, 1.0, 1.0, h->nv, h->ng, ST_GATHER, dpart);
 }
 
 int permute_in(dski_handle h, const void* v_user, void* v_int, int s, bool f64, cudaStream_t st) {

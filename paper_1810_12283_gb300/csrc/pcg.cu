@@ -116,6 +116,64 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_init(
   }
 }
 
+// From the column sums tot[c] = r^T z: at (re)start rz (and rz0 once), else
+// beta = (r^T z)_new / rz for active columns (recorded), 0 for the others.
+__device__ void beta_finish(const double* tot, ColState& cs, int init) {
+  for (int cc = threadIdx.x; cc < cs.s; cc += blockDim.x) {
+    const double t = tot[cc];
+    if (init) {
+      cs.rz[cc] = t;
+      cs.beta[cc] = 0.0;
+      if (cs.rz0[cc] == 0.0) cs.rz0[cc] = t;
+    } else if (cs.active[cc]) {
+      const double be = t / cs.rz[cc];
+      cs.beta[cc] = be;
+      cs.rz[cc] = t;
+      const int k = cs.iters[cc] - 1;
+      if (cs.bhist && k >= 0 && k < cs.depth) cs.bhist[(long long)k * cs.s + cc] = be;
+    } else {
+      cs.beta[cc] = 0.0;
+    }
+  }
+}
+
+// From tot[c] = p^T q: alpha = r^T z / p^T q for active columns (recorded),
+// breakdown (non-positive or non-finite) deactivates a column.
+__device__ void alpha_finish(const double* tot, ColState& cs) {
+  for (int cc = threadIdx.x; cc < cs.s; cc += blockDim.x) {
+    double al = 0.0;
+    if (cs.active[cc]) {
+      const double t = tot[cc];
+      if (!(t > 0.0) || !isfinite(t) || !isfinite(cs.rz[cc])) {
+        cs.bd[cc] = 1;
+        cs.active[cc] = 0;
+      } else {
+        al = cs.rz[cc] / t;
+        const int k = cs.iters[cc];
+        if (cs.ahist && k < cs.depth) cs.ahist[(long long)k * cs.s + cc] = al;
+      }
+    }
+    cs.alpha[cc] = al;
+  }
+}
+
+// From tot[c] = ||r||^2 after the update: record it, count the iteration,
+// deactivate the columns that met their target; the active count.
+__device__ void update_finish(const double* tot, ColState& cs, double* sh) {
+  int nact = 0;
+  for (int cc = threadIdx.x; cc < cs.s; cc += blockDim.x) {
+    if (cs.active[cc]) {
+      const double t = tot[cc];
+      cs.rn2[cc] = t;
+      cs.iters[cc] += 1;
+      if (!(t > cs.target[cc])) cs.active[cc] = 0;
+    }
+    nact += cs.active[cc];
+  }
+  nact = (int)block_sum((double)nact, sh);
+  if (threadIdx.x == 0) *cs.nactive = nact;
+}
+
 // z = dis .* (y - Q1 C) (preconditioned) or z = r (plain); r^T z.
 // init: p = z (and its float copy), r^T z becomes rz and rz0.
 // else: beta = (r^T z)_new / rz for active columns, recorded.
@@ -191,22 +249,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_z(
   if (cg_last(ticket)) {
     __shared__ double tot[CG_MAXS];
     sum_columns(part, gridDim.x, cs.s, 1, 0, tot, sh);
-    for (int cc = threadIdx.x; cc < cs.s; cc += blockDim.x) {
-      const double t = tot[cc];
-      if (init) {
-        cs.rz[cc] = t;
-        cs.beta[cc] = 0.0;
-        if (cs.rz0[cc] == 0.0) cs.rz0[cc] = t;
-      } else if (cs.active[cc]) {
-        const double be = t / cs.rz[cc];
-        cs.beta[cc] = be;
-        cs.rz[cc] = t;
-        const int k = cs.iters[cc] - 1;
-        if (cs.bhist && k >= 0 && k < cs.depth) cs.bhist[(long long)k * cs.s + cc] = be;
-      } else {
-        cs.beta[cc] = 0.0;
-      }
-    }
+    beta_finish(tot, cs, init);
   }
 }
 
@@ -268,21 +311,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_alpha(const double* __restric
   if (cg_last(ticket)) {
     __shared__ double tot[CG_MAXS];
     sum_columns(part, gridDim.x, cs.s, 1, 0, tot, sh);
-    for (int cc = threadIdx.x; cc < cs.s; cc += blockDim.x) {
-      double al = 0.0;
-      if (cs.active[cc]) {
-        const double t = tot[cc];
-        if (!(t > 0.0) || !isfinite(t) || !isfinite(cs.rz[cc])) {
-          cs.bd[cc] = 1;
-          cs.active[cc] = 0;
-        } else {
-          al = cs.rz[cc] / t;
-          const int k = cs.iters[cc];
-          if (cs.ahist && k < cs.depth) cs.ahist[(long long)k * cs.s + cc] = al;
-        }
-      }
-      cs.alpha[cc] = al;
-    }
+    alpha_finish(tot, cs);
   }
 }
 
@@ -335,19 +364,21 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_update(
   if (cg_last(ticket)) {
     __shared__ double tot[CG_MAXS];
     sum_columns(part, gridDim.x, cs.s, 1, 0, tot, sh);
-    int nact = 0;
-    for (int cc = threadIdx.x; cc < cs.s; cc += blockDim.x) {
-      if (cs.active[cc]) {
-        const double t = tot[cc];
-        cs.rn2[cc] = t;
-        cs.iters[cc] += 1;
-        if (!(t > cs.target[cc])) cs.active[cc] = 0;
-      }
-      nact += cs.active[cc];
-    }
-    nact = (int)block_sum((double)nact, sh);
-    if (threadIdx.x == 0) *cs.nactive = nact;
+    update_finish(tot, cs, sh);
   }
+}
+
+// One-block finishers of the fused path: the block partials come from the
+// MVM's gather (p^T q), the preconditioner's scatter pass (||r||^2 after the
+// update) and its gather (r^T z); kind 0: alpha, 1: update, 2: beta.
+__global__ void __launch_bounds__(CG_THREADS) k_cg_finish(const double* __restrict__ part,
+                                                          int nb, int kind, ColState cs) {
+  __shared__ double sh[32];
+  __shared__ double tot[CG_MAXS];
+  sum_columns(part, nb, cs.s, 1, 0, tot, sh);
+  if (kind == 0) alpha_finish(tot, cs);
+  else if (kind == 1) update_finish(tot, cs, sh);
+  else beta_finish(tot, cs, 0);
 }
 
 }  // namespace
@@ -473,7 +504,40 @@ int cg_run(dski_handle h, CgRun& run) {
       return set_error(DSKI_ERR_CUDA, "dski_pcg_solve: %s", cudaGetErrorString(cudaGetLastError()));
     return check_device_error(h);   // synchronises
   };
+  // FP64 grid-form path: the three CG vector passes fold into the kernels
+  // around them (p^T q into the MVM's gather, x += alpha p, r -= alpha q
+  // and ||r||^2 into the preconditioner's scatter pass, r^T z into its
+  // gather); one-block kernels finish the sums
+  const bool fusedg = fused && gridf && s <= 4;
+  const int nbp = (h->n + 255) / 256;
+  double* dpA = fusedg ? wbuf(h->s_dpart, (size_t)3 * nbp * 4 + 16) : nullptr;
+  if (fusedg && !dpA) return set_error(DSKI_ERR_ALLOC, "dski_pcg_solve: workspace allocation failed");
+  double* dpU = fusedg ? dpA + (size_t)nbp * 4 : nullptr;
+  double* dpZ = fusedg ? dpU + (size_t)nbp * 4 : nullptr;
   auto iteration = [&]() -> int {
+    if (fusedg) {
+      DSKI_TRY(mvm_pcg_fused(h, P, Z, cs.beta, Q, s, dpA));
+      {
+        StageScope sc(h, ST_PCGVEC, st);
+        k_cg_finish<<<1, CG_THREADS, 0, st>>>(dpA, nbp, 0, cs);
+      }
+      DSKI_LAUNCHED();
+      CgUpdate up;
+      up.x = run.X;
+      up.p = P;
+      up.q = Q;
+      up.alpha = cs.alpha;
+      up.active = cs.active;
+      up.dpart = dpU;
+      DSKI_TRY(grid_precond_apply(h, run.pc, R, Z, s, &up, dpZ));
+      {
+        StageScope sc(h, ST_PCGVEC, st, 2);
+        k_cg_finish<<<1, CG_THREADS, 0, st>>>(dpU, nbp, 1, cs);
+        k_cg_finish<<<1, CG_THREADS, 0, st>>>(dpZ, nbp, 2, cs);
+      }
+      DSKI_LAUNCHED();
+      return DSKI_OK;
+    }
     if (mixed) {
       DSKI_TRY(mvm_internal(h, P32, Q32, s, false));
       StageScope sc(h, ST_PCGVEC, st, 2);

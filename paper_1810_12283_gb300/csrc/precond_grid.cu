@@ -235,7 +235,8 @@ int grid_precond_build(dski_handle h, pivchol_handle pc, const int* piv_dev, con
   W.release();
   if (rc == DSKI_OK) pc->grid_form = true;
   // FP64_TC: digit planes for the two products of the apply
-  if (rc == DSKI_OK && h->prec == DSKI_FP64_TC && r <= 256 && m1 % 8 == 0 && m1 <= 256) {
+  if (rc == DSKI_OK && h->prec == DSKI_FP64_TC && r <= 256 && m1 % 8 == 0 && m1 <= 256 &&
+      m1 >= kOzMinM) {
     const int rp = (r + 7) / 8 * 8;
     if (pc->ozH1.ensure((size_t)kOzDigits * r * m1 * 2) ||
         pc->ozH1T.ensure((size_t)kOzDigits * m1 * rp * 2) ||
@@ -259,7 +260,10 @@ int grid_precond_build(dski_handle h, pivchol_handle pc, const int* piv_dev, con
 }
 
 // Z = M^-1 R for s columns (internal layout) through the grid form.
-int grid_precond_apply(dski_handle h, pivchol_handle pc, const double* R, double* Z, int s) {
+int grid_precond_apply(dski_handle h, pivchol_handle pc, const double* R, double* Z, int s,
+                       const CgUpdate* up, double* dpart_rz) {
+  if ((up || dpart_rz) && s > 4)
+    return set_error(DSKI_ERR_ARG, "fused CG steps in the preconditioner need s <= 4");
   const int r = pc->rank;
   const int m0 = h->m[0], m1 = h->m[1];
   const long long M = h->M, N = h->N;
@@ -276,7 +280,7 @@ int grid_precond_apply(dski_handle h, pivchol_handle pc, const double* R, double
     if (!g || !hp) return DSKI_ERR_ALLOC;
     // g = B^T D^-1 R
     DSKI_TRY(scatter_scaled(h, R + (size_t)c0 * N, g, q, true, nullptr, 1.0 / pc->nv,
-                            1.0 / pc->ng));
+                            1.0 / pc->ng, up));
     if (pc->oz) {
       // the two products on the tensor cores (FP64-accurate digit products)
       OzGemm g1;   // Y[q][k][u0] = sum_u1 H1[k][u1] g[q][u0][u1]
@@ -330,7 +334,7 @@ int grid_precond_apply(dski_handle h, pivchol_handle pc, const double* R, double
     DSKI_LAUNCHED();
     // Z = (R - B h') ./ noise
     DSKI_TRY(gather_scaled(h, hp, R + (size_t)c0 * N, Z + (size_t)c0 * N, q, -1.0 / pc->nv,
-                           -1.0 / pc->ng, 1.0 / pc->nv, 1.0 / pc->ng, ST_PRECOND));
+                           -1.0 / pc->ng, 1.0 / pc->nv, 1.0 / pc->ng, ST_PRECOND, dpart_rz));
   }
   return DSKI_OK;
 }

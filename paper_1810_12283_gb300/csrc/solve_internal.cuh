@@ -143,7 +143,11 @@ int split_q1(dski_handle h, pivchol_handle pc);
 // (no-op where it does not apply), and apply to s internal-layout columns
 int grid_precond_build(dski_handle h, pivchol_handle pc, const int* piv_dev, const double* R1i,
                        const double* R2i);
-int grid_precond_apply(dski_handle h, pivchol_handle pc, const double* R, double* Z, int s);
+// with up, the CG update of R runs in the scatter's point pass first (R is
+// updated in place); with dpart_rz, the final gather leaves per-block partial
+// sums of R^T Z (s <= 4 for either)
+int grid_precond_apply(dski_handle h, pivchol_handle pc, const double* R, double* Z, int s,
+                       const CgUpdate* up = nullptr, double* dpart_rz = nullptr);
 // Noise diagonal of the internal layout: D[e] = nv (value rows) or ng.
 int noise_diag(dski_handle h, double nv, double ng, double* D_dev);
 // M^-1 for s columns: Z = D^-1/2 (Y - Q1 Q1^T Y), Y = D^-1/2 R.

@@ -42,11 +42,15 @@ def test_mvm_parity(name, make, prec, s):
     op.close()
 
 
+# FP64_TC takes the tensor cores for modes of at least 64 nodes (the FP64
+# units below); these grids mix both, with two 128-row tiles and ragged
+# tails in j and r, contraction splits of 2..5, and an operand of one row
 TC_CASES = [
-    ("1d-m40", lambda: problem_1d(300, m=40)),
-    ("2d-24x32", lambda: dict(W.small2d(700, m=24, seed=5), m=(24, 32))),
-    ("3d-16x24x16", lambda: dict(W.small3d(400, m=16, seed=6), m=(16, 24, 16))),
-    ("sine2d", lambda: W.sine2d()),
+    ("1d-m64", lambda: problem_1d(300, m=64)),
+    ("2d-136x72", lambda: dict(W.small2d(700, m=24, seed=5), m=(136, 72))),
+    ("3d-64x16x24", lambda: dict(W.small3d(400, m=16, seed=6), m=(64, 16, 24))),
+    ("2d-24x32-fp64-units", lambda: dict(W.small2d(700, m=24, seed=5), m=(24, 32))),
+    ("sine2d-64", lambda: dict(W.sine2d(), m=(64, 64))),
 ]
 
 

@@ -215,6 +215,40 @@ def test_pcg_fp64_tc_matches_fp64_path():
     op.close()
 
 
+def test_pcg_fp64_tc_tensor_core_preconditioner():
+    """FP64_TC where the grid-form preconditioner's two products also take
+    the tensor cores (d = 2, M < N, m_1 >= 64): the first iterates agree with
+    the oracle's PCG, and the final residual is as low as the FP64 path's on
+    the same system (whose attainable accuracy is near 1e-8; the residual
+    FP64_TC reports is checked against the dense matrix)."""
+    need_gpu()
+    from oracle.solve import pcg, pivoted_cholesky
+    p = dict(W.small2d(2000, m=56, seed=7, nv=1e-2, ng=1e-2), m=(56, 64))   # M < N
+    op = gpu_op(p, "fp64_tc")
+    orc = oracle_op(p)
+    pc = op.pivchol(30)
+    _, piv = pc.export()
+    Lo, _, _ = pivoted_cholesky(orc.kgrad_diag(), orc.kgrad_row, 30, pivots=piv)
+    Pc = _oracle_pc(orc, Lo)
+    b = torch.tensor(p["y"], device="cuda")
+    for k in (1, 4):
+        x, it, rr = op.solve(b, pc, rtol=1e-10, maxit=k, allow_not_converged=True)
+        run = pcg(orc.mvm, p["y"], Pc.solve, rtol=0.0, maxit=k)
+        assert rel(x.cpu().numpy(), run["x"]) <= 1e-9, (k, rel(x.cpu().numpy(), run["x"]))
+    xt, it_t, rr_t = op.solve(b, pc, rtol=1e-9, maxit=20000, allow_not_converged=True)
+    op64 = gpu_op(p, "fp64")
+    pc64 = op64.pivchol(30)
+    _, it_6, rr_6 = op64.solve(b, pc64, rtol=1e-9, maxit=20000, allow_not_converged=True)
+    assert rr_t[0] <= max(1e-9, 3.0 * rr_6[0]), (rr_t, rr_6)
+    A = orc.dense()
+    true_rr = np.linalg.norm(p["y"] - A @ xt.cpu().numpy()) / np.linalg.norm(p["y"])
+    assert true_rr <= 1.5 * rr_t[0] + 1e-12, (true_rr, rr_t)
+    pc64.close()
+    op64.close()
+    pc.close()
+    op.close()
+
+
 def test_pcg_mixed_refinement_reaches_fp64_tolerance():
     """MIXED_3XTF32 on a problem whose conditioning the FP32 operator
     resolves (noise 1e-2, coarse grid): FP32 inner solves with FP64
