@@ -428,7 +428,8 @@ static int qr_form(dski_handle h, pivchol_handle pc, int* flag_dev, double* smal
     // FP64_TC keep it in FP64: the QR-form apply cancels in the top
     // eigen-directions, amplifying its rounding by ~1 + lambda_max / sigma^2
     // (2^-44 double-float stalled PCG at 1.5e-6 where FP64 reached 2.5e-9)
-    if (!f64_vectors(h)) {
+    // (the grid form, where it applies, replaces the Q1 apply in every mode)
+    if (!f64_vectors(h) && !pc->grid_form) {
       rc = split_q1(h, pc);
       if (rc) break;
     }

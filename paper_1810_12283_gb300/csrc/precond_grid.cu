@@ -206,7 +206,9 @@ __global__ void k_transpose(const double* __restrict__ X, int rows, int cols,
 int grid_precond_build(dski_handle h, pivchol_handle pc, const int* piv_dev, const double* R1i,
                        const double* R2i) {
   const int r = pc->rank;
-  if (!(h->d == 2 && (long long)h->M < h->N && f64_vectors(h) && r >= 1)) return DSKI_OK;
+  // every mode: the PCG's r and z are FP64 in the mixed modes too, and the
+  // grid form runs in FP64 (its scatter and gather read the FP64 weights)
+  if (!(h->d == 2 && (long long)h->M < h->N && r >= 1)) return DSKI_OK;
   const int m0 = h->m[0], m1 = h->m[1];
   cudaStream_t st = h->stream;
   DevBuf LP, W;
