@@ -216,6 +216,22 @@ int dski_mll_grad(dski_handle h, pivchol_handle pc, const double* y_dev, int pro
 int dski_predict(dski_handle h, pivchol_handle pc, const double* alpha_dev, const double* Xs_dev,
                  int n_star, int with_grad, double* mean_dev, double* var_dev);
 
+/* Unbiased predictive variance at n_star test points by Sec. 5's second
+ * approach: the randomized diagonal estimator (Bekas et al.) with the
+ * preconditioner estimate v_hat as control variate,
+ *   v = v_hat - diag(K_*X (K~^-1 - M^-1) K_X*),
+ *   diag(A) ~ (1/P) sum_j z_j .* (A z_j),
+ * z_j Rademacher over the test points: entry (i, j) is the sign of output
+ * number j n_star + i + 1 of the SplitMix64 stream seeded with `seed`
+ * (the convention of dski_logdet_slq).  The P probe solves K~ a = K_X* z_j
+ * run as one batched PCG (rtol, maxit).  Xs_dev: n_star x d FP64 row-major;
+ * var_dev: n_star FP64 (device).  The test-point scatter adds with FP64
+ * atomics where test points share grid nodes, so results are reproducible
+ * to rounding, not bitwise.  Errors: ARG, OUT_OF_GRID, NOT_CONVERGED (var_dev
+ * still filled), ALLOC, CUDA. */
+int dski_predict_var_cv(dski_handle h, pivchol_handle pc, const double* Xs_dev, int n_star,
+                        int probes, uint64_t seed, double rtol, int maxit, double* var_dev);
+
 /* Profiling aid (the paper has no counterpart): per-stage device timers.
  * Stages, in order: 0 permute (user block order <-> internal layout),
  * 1 scatter, 2 Kronecker mode products, 3 gather (+ noise), 4 preconditioner

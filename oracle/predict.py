@@ -66,3 +66,18 @@ def exact_mean(X, y, Xs, lengthscale, outputscale, noise):
     Kst = Kall[np.ix_(test_rows, train_cols)]
     Ktt = Kall[np.ix_(train_cols, train_cols)] + np.diag(noise)
     return Kst @ np.linalg.solve(Ktt, np.asarray(y, np.float64))
+
+
+def variance_cv(op, Xs, precond, Z):
+    """The randomized predictive variance of Sec. 5 with the preconditioner
+    estimate as control variate:
+        v = v_hat - diag(K_*X (K~^-1 - M^-1) K_X*),
+        diag(A) ~ (1/P) sum_j z_j .* (A z_j)      (Bekas et al.'s estimator),
+    for the probe columns Z (n* x P, entries +-1).  K_*X = K_X*^T for the
+    value rows of the test points (oracle.predict.dski_cross)."""
+    Kx = dski_cross(op, Xs)                        # N x n*
+    U = Kx @ Z                                     # N x P
+    A = np.linalg.solve(op.dense(), U)
+    Bm = precond.solve(U)
+    Wz = Kx.T @ (A - Bm)                           # n* x P
+    return variance_estimate(op, Xs, precond) - np.mean(Z * Wz, axis=1)

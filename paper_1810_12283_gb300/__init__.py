@@ -210,6 +210,16 @@ class DSKI:
                                             _dptr(var) if var is not None else None))
         return mean, var
 
+    def predict_variance_cv(self, Xs, pc, probes=64, seed=777, rtol=1e-8, maxit=20000):
+        """Unbiased predictive variance (randomized estimator with the
+        preconditioner estimate as control variate) at Xs (n* x d)."""
+        Xs = Xs.to(device=self.device, dtype=torch.float64).contiguous()
+        var = torch.empty(Xs.shape[0], device=self.device, dtype=torch.float64)
+        _lib.check(_lib.load().dski_predict_var_cv(self.h, pc.ptr, _dptr(Xs), Xs.shape[0],
+                                                   int(probes), C.c_uint64(seed), float(rtol),
+                                                   int(maxit), _dptr(var)))
+        return var
+
 
 def launch_count():
     """Kernels the CUDA library has launched in this process."""

@@ -19,7 +19,7 @@ PREC = {"fp64": 0, "mixed_3xtf32": 1, "mixed_tf32": 2, "fp64_tc": 3}
 EXPORTS = ["dski_create", "dski_set_hypers", "dski_mvm", "pivchol_build", "dski_pcg_solve",
            "dski_logdet_slq", "dski_mll_grad", "dski_destroy", "pivchol_destroy",
            "dski_last_error", "dski_profile", "dski_launch_count", "pivchol_export",
-           "pivchol_logdet", "dski_mvm_noalloc", "dski_predict"]
+           "pivchol_logdet", "dski_mvm_noalloc", "dski_predict", "dski_predict_var_cv"]
 NSTAGES = 8
 STAGES = ["permute", "scatter", "kron", "gather", "precond", "pcg_vec", "pivchol", "lanczos"]
 
@@ -63,6 +63,8 @@ def load(path=LIB_PATH):
     lib.dski_logdet_slq.argtypes = [vp, vp, C.c_int, C.c_int, C.c_uint64, dp, dp]
     lib.dski_mll_grad.argtypes = [vp, vp, vp, C.c_int, C.c_uint64, dp, dp]
     lib.dski_predict.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, vp, vp]
+    lib.dski_predict_var_cv.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_uint64, C.c_double,
+                                        C.c_int, vp]
     lib.dski_destroy.argtypes = [vp]
     lib.dski_destroy.restype = None
     lib.pivchol_destroy.argtypes = [vp]

@@ -137,6 +137,99 @@ __global__ void k_pred_var(const double* __restrict__ dots, int s, double sf2,
   if (c < s) var[c] = sf2 - dots[c];
 }
 
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// Rademacher probe entry (test point i, probe j): the sign of output number
+// j n* + i + 1 of the SplitMix64 stream seeded with `seed` (Steele, Lea and
+// Flood, OOPSLA 2014; the top bit 0 gives +1).
+__device__ __forceinline__ double test_probe(unsigned long long seed, long long ns, int j, int i) {
+  const unsigned long long k = (unsigned long long)j * (unsigned long long)ns + (unsigned long long)i + 1ULL;
+  return (mix64(seed + k * 0x9E3779B97F4A7C15ULL) >> 63) ? -1.0 : 1.0;
+}
+
+// G[j][:] (M x P, zeroed) = sum_i z_ij w*_i: thread (test point, probe),
+// FP64 atomics where test points share grid nodes.
+template <int D>
+__global__ void k_pred_scatter_z(const double* __restrict__ Xs, int ns, int P,
+                                 unsigned long long seed, PredGeo g, long long M,
+                                 double* __restrict__ G, int* __restrict__ bad) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)ns * P) return;
+  const int i = (int)(t % ns), j = (int)(t / ns);
+  int first[D];
+  double w[D][4], dw[D][4];
+  if (!pred_stencil<D>(Xs + (long long)i * D, g, first, w, dw)) {
+    if (j == 0) atomicAdd(bad, 1);
+    return;
+  }
+  const double z = test_probe(seed, ns, j, i);
+  constexpr int NS = D == 1 ? 4 : (D == 2 ? 16 : 64);
+  for (int s4 = 0; s4 < NS; ++s4) {
+    int o[D];
+    int r = s4;
+#pragma unroll
+    for (int k = D - 1; k >= 0; --k) {
+      o[k] = r & 3;
+      r >>= 2;
+    }
+    long long idx = 0;
+    double wp = z;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      idx += (long long)(first[k] + o[k]) * g.stride[k];
+      wp *= w[k][o[k]];
+    }
+    atomicAdd(&G[(long long)j * M + idx], wp);
+  }
+}
+
+// var[i] -= (1/P) sum_j z_ij (w*_i . H[j]): one thread per test point.
+template <int D>
+__global__ void k_pred_cv(const double* __restrict__ Xs, int ns, int P, unsigned long long seed,
+                          PredGeo g, long long M, const double* __restrict__ H,
+                          double* __restrict__ var) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ns) return;
+  int first[D];
+  double w[D][4], dw[D][4];
+  if (!pred_stencil<D>(Xs + (long long)i * D, g, first, w, dw)) return;
+  constexpr int NS = D == 1 ? 4 : (D == 2 ? 16 : 64);
+  double acc = 0.0;
+  for (int j = 0; j < P; ++j) {
+    const double* hj = H + (long long)j * M;
+    double dot = 0.0;
+    for (int s4 = 0; s4 < NS; ++s4) {
+      int o[D];
+      int r = s4;
+#pragma unroll
+      for (int k = D - 1; k >= 0; --k) {
+        o[k] = r & 3;
+        r >>= 2;
+      }
+      long long idx = 0;
+      double wp = 1.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        idx += (long long)(first[k] + o[k]) * g.stride[k];
+        wp *= w[k][o[k]];
+      }
+      dot = fma(wp, hj[idx], dot);
+    }
+    acc = fma(test_probe(seed, ns, j, i), dot, acc);
+  }
+  var[i] -= acc / P;
+}
+
+__global__ void k_axpy_neg(const double* __restrict__ a, const double* __restrict__ b,
+                           long long n, double* __restrict__ c) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) c[t] = a[t] - b[t];
+}
+
 PredGeo pred_geo(dski_handle h) {
   PredGeo g{};
   g.d = h->d;
@@ -235,4 +328,90 @@ extern "C" int dski_predict(dski_handle h, pivchol_handle pc, const double* alph
     return set_error(DSKI_ERR_CUDA, "dski_predict: %s", cudaGetErrorString(cudaGetLastError()));
   if (hb) return set_error(DSKI_ERR_OUT_OF_GRID, "dski_predict: %d test point(s) lack a full interpolation stencil", hb);
   return check_device_error(h);
+}
+
+extern "C" int dski_predict_var_cv(dski_handle h, pivchol_handle pc, const double* Xs_dev,
+                                   int n_star, int probes, uint64_t seed, double rtol, int maxit,
+                                   double* var_dev) {
+  clear_error();
+  if (!h || !pc || !Xs_dev || !var_dev || n_star < 1)
+    return set_error(DSKI_ERR_ARG, "dski_predict_var_cv: NULL argument or n_star < 1");
+  if (pc->h != h) return set_error(DSKI_ERR_ARG, "dski_predict_var_cv: preconditioner of another handle");
+  if (probes < 1 || probes > 256) return set_error(DSKI_ERR_ARG, "dski_predict_var_cv: probes in 1..256");
+  if (!(rtol > 0.0) || maxit < 1) return set_error(DSKI_ERR_ARG, "dski_predict_var_cv: need rtol > 0, maxit >= 1");
+  // v_hat first (the control variate)
+  DSKI_TRY(dski_predict(h, pc, nullptr, Xs_dev, n_star, 0, nullptr, var_dev));
+  cudaStream_t st = h->stream;
+  const int d = h->d, P = probes;
+  const long long N = h->N, M = h->M;
+  const PredGeo g = pred_geo(h);
+  DevBuf bad, G1, G2, U, A, Bm;
+  if (bad.ensure(16) || G1.ensure((size_t)M * P * 8) || G2.ensure((size_t)M * P * 8) ||
+      U.ensure((size_t)N * P * 8) || A.ensure((size_t)N * P * 8) || Bm.ensure((size_t)N * P * 8))
+    return set_error(DSKI_ERR_ALLOC, "dski_predict_var_cv: allocation failed");
+  if (cudaMemsetAsync(bad.ptr, 0, 16, st) != cudaSuccess ||
+      cudaMemsetAsync(G1.ptr, 0, (size_t)M * P * 8, st) != cudaSuccess ||
+      cudaMemsetAsync(U.ptr, 0, (size_t)N * P * 8, st) != cudaSuccess ||
+      cudaMemsetAsync(A.ptr, 0, (size_t)N * P * 8, st) != cudaSuccess)
+    return set_error(DSKI_ERR_CUDA, "dski_predict_var_cv: memset failed");
+  int* badp = bad.as<int>();
+  // U = K_X* Z: the probes' test weights on the grid, K_UU, gather at the training points
+  {
+    StageScope sc(h, ST_SCATTER, st);
+    const long long th = (long long)n_star * P;
+    const unsigned nb = (unsigned)((th + 255) / 256);
+    switch (d) {
+      case 1: k_pred_scatter_z<1><<<nb, 256, 0, st>>>(Xs_dev, n_star, P, seed, g, M, G1.as<double>(), badp); break;
+      case 2: k_pred_scatter_z<2><<<nb, 256, 0, st>>>(Xs_dev, n_star, P, seed, g, M, G1.as<double>(), badp); break;
+      default: k_pred_scatter_z<3><<<nb, 256, 0, st>>>(Xs_dev, n_star, P, seed, g, M, G1.as<double>(), badp); break;
+    }
+  }
+  DSKI_LAUNCHED();
+  void* res = nullptr;
+  DSKI_TRY(kron_internal(h, G1.ptr, G2.ptr, P, true, -1, nullptr, &res));
+  DSKI_TRY(gather_scaled(h, (const double*)res, U.as<double>(), U.as<double>(), P, 1.0, 1.0, 0.0,
+                         0.0, ST_GATHER));
+  // A = K~^-1 U (PCG), Bm = M^-1 U, U <- A - Bm
+  CgRun run;
+  run.s = P;
+  run.rtol = rtol;
+  run.maxit = maxit;
+  run.pc = pc;
+  run.B = U.as<double>();
+  run.X = A.as<double>();
+  int rc = cg_run(h, run);
+  if (rc != DSKI_OK && rc != DSKI_ERR_NOT_CONVERGED) return rc;
+  const int crc = rc;
+  DSKI_TRY(precond_apply(h, pc, U.as<double>(), Bm.as<double>(), P));
+  {
+    StageScope sc(h, ST_PCGVEC, st);
+    const long long tot = N * P;
+    k_axpy_neg<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(A.as<double>(), Bm.as<double>(), tot,
+                                                           U.as<double>());
+  }
+  DSKI_LAUNCHED();
+  // K_*X (A - Bm): scatter at the training points, K_UU, then per test point
+  // the probe-weighted mean of its value interpolation
+  DSKI_TRY(scatter_internal(h, U.ptr, G1.ptr, P, true));
+  DSKI_TRY(kron_internal(h, G1.ptr, G2.ptr, P, true, -1, nullptr, &res));
+  {
+    StageScope sc(h, ST_GATHER, st);
+    const unsigned nb = (unsigned)((n_star + 127) / 128);
+    switch (d) {
+      case 1: k_pred_cv<1><<<nb, 128, 0, st>>>(Xs_dev, n_star, P, seed, g, M, (const double*)res, var_dev); break;
+      case 2: k_pred_cv<2><<<nb, 128, 0, st>>>(Xs_dev, n_star, P, seed, g, M, (const double*)res, var_dev); break;
+      default: k_pred_cv<3><<<nb, 128, 0, st>>>(Xs_dev, n_star, P, seed, g, M, (const double*)res, var_dev); break;
+    }
+  }
+  DSKI_LAUNCHED();
+  int hb = 0;
+  if (cudaMemcpyAsync(&hb, badp, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return set_error(DSKI_ERR_CUDA, "dski_predict_var_cv: %s", cudaGetErrorString(cudaGetLastError()));
+  if (hb) return set_error(DSKI_ERR_OUT_OF_GRID, "dski_predict_var_cv: %d test point(s) lack a full stencil", hb);
+  rc = check_device_error(h);
+  if (rc != DSKI_OK) return rc;
+  if (crc == DSKI_ERR_NOT_CONVERGED)
+    return set_error(DSKI_ERR_NOT_CONVERGED, "dski_predict_var_cv: probe solves missed rtol %.3g", rtol);
+  return DSKI_OK;
 }

@@ -105,3 +105,32 @@ def test_out_of_grid_test_point_is_reported():
         op.predict(alpha, Xs)
     assert "OUT_OF_GRID" in str(e.value)
     op.close()
+
+
+def test_control_variate_variance_matches_oracle():
+    """Sec. 5's randomized variance with the preconditioner estimate as
+    control variate: with the same SplitMix64 probes the GPU equals the
+    oracle (exact dense solves) to the PCG tolerance's effect, and it moves
+    the preconditioner estimate toward the D-SKI variance."""
+    need_gpu()
+    from oracle.predict import variance_cv, variance_dski, variance_estimate
+    from oracle.probes import rademacher
+    from oracle.solve import QRPreconditioner, pivoted_cholesky
+    p = W.small2d(300, m=24, seed=4, nv=1e-2, ng=1e-2)
+    orc = oracle_op(p)
+    op = gpu_op(p, "fp64")
+    pc = op.pivchol(12)
+    _, piv = pc.export()
+    L, _, _ = pivoted_cholesky(orc.kgrad_diag(), orc.kgrad_row, 12, pivots=piv)
+    Pc = QRPreconditioner(L, orc.noise)
+    Xs = _test_points(p, 40, 13)
+    P, seed = 64, 99
+    got = op.predict_variance_cv(torch.tensor(Xs, device="cuda"), pc, probes=P, seed=seed,
+                                 rtol=1e-11, maxit=20000).cpu().numpy()
+    want = variance_cv(orc, Xs, Pc, rademacher(seed, len(Xs), P))
+    assert np.max(np.abs(got - want)) <= 1e-9, np.max(np.abs(got - want))
+    exact = variance_dski(orc, Xs)
+    vhat = variance_estimate(orc, Xs, Pc)
+    assert np.mean(np.abs(got - exact)) < np.mean(np.abs(vhat - exact))
+    pc.close()
+    op.close()

@@ -69,3 +69,27 @@ def test_variance_estimate_brackets_and_full_rank_equality():
     L, _, _ = pivoted_cholesky(diag, row, op.N)
     vh = variance_estimate(op, Xs, QRPreconditioner(L, op.noise))
     assert np.allclose(vh, v, rtol=1e-6, atol=1e-10)
+
+
+def test_control_variate_estimator_is_exact_with_hadamard_probes():
+    # with the n* columns of a Hadamard matrix as probes, sum_j z_j z_j^T = P I,
+    # so the diagonal estimator is exact and v equals the D-SKI variance
+    from scipy.linalg import hadamard
+    from oracle.predict import variance_cv
+    X, y = _data(25, seed=5)
+    op = DSKI(X, Grid((32, 32), (-0.15, -0.15), (1.15, 1.15)), [0.3, 0.3], 1.0, 1e-3, 1e-3)
+    Xs = np.random.default_rng(6).uniform(0.1, 0.9, (8, 2))
+    Kg = op.dense_kgrad()
+    L, _, _ = pivoted_cholesky(np.diag(Kg).copy(), lambda j: Kg[:, j], 10)
+    Pc = QRPreconditioner(L, op.noise)
+    H = hadamard(8).astype(np.float64)
+    v = variance_cv(op, Xs, Pc, H)
+    want = variance_dski(op, Xs)
+    # v ~ 1e-4 is the difference of O(1) terms evaluated through K~^-1
+    # (kappa ~ 1e6): rounding shows at ~1e-16 kappa ~ 1e-10 absolute
+    assert np.allclose(v, want, rtol=0.0, atol=1e-9), (v, want)
+    # Rademacher probes: unbiased, within the estimator's spread
+    from oracle.probes import rademacher
+    Z = rademacher(123, 8, 4000)
+    vr = variance_cv(op, Xs, Pc, Z)
+    assert np.all(np.abs(vr - want) <= 0.1 * np.abs(variance_estimate(op, Xs, Pc) - want) + 1e-9)
