@@ -592,6 +592,9 @@ __global__ void __launch_bounds__(128) k_oz_mode(const __grid_constant__ CUtenso
   const long long R = a.R;
   const double scale = a.scale;
   int* __restrict__ err = a.err;
+  // programmatic dependent launch: a following product may start its
+  // set-up now; it waits (griddepcontrol.wait below) before reading ours
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   int* pmax = (int*)(smem + Z_EXP);        // this split's row maxima (exponent fields)
@@ -620,6 +623,10 @@ __global__ void __launch_bounds__(128) k_oz_mode(const __grid_constant__ CUtenso
     tc::mbar_expect_tx(full, (uint32_t)(OZ_S * Z_A));
     for (int b = 0; b < OZ_S; ++b) tc::tma_load_3d(smem + b * Z_A, &tA, i0, j0, b, full);
   }
+  // everything above touches only this CTA's resources and A's digit planes
+  // (written when the factors were built); X, the workspace and Y may belong
+  // to the kernel before this one in the stream
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 
   // 1. this thread's 8 operand values: row rr, columns i0 + 8 c .. + 7
   const int rr = tid >> 2, c = tid & 3;
@@ -879,7 +886,7 @@ int oz_gemm(dski_handle h, const OzGemm& g, int stage) {
   cfg.blockDim = dim3(128);
   cfg.dynamicSmemBytes = Z_SMEM;
   cfg.stream = h->stream;
-  cudaLaunchAttribute attr[2];
+  cudaLaunchAttribute attr[3];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 1;
   attr[0].val.clusterDim.y = 1;
@@ -888,8 +895,11 @@ int oz_gemm(dski_handle h, const OzGemm& g, int stage) {
   // be resident at once
   attr[1].id = cudaLaunchAttributeClusterSchedulingPolicyPreference;
   attr[1].val.clusterSchedulingPolicyPreference = cudaClusterSchedulingPolicyLoadBalancing;
+  // programmatic dependent launch (the kernel waits before reading inputs)
+  attr[2].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[2].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 2;
+  cfg.numAttrs = 3;
   StageScope sc(h, stage, h->stream);
   if (cudaLaunchKernelEx(&cfg, k_oz_mode, tA, a) != cudaSuccess)
     return set_error(DSKI_ERR_CUDA, "FP64_TC product launch: %s",

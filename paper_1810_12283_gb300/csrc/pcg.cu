@@ -369,16 +369,23 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_update(
 }
 
 // One-block finishers of the fused path: the block partials come from the
-// MVM's gather (p^T q), the preconditioner's scatter pass (||r||^2 after the
-// update) and its gather (r^T z); kind 0: alpha, 1: update, 2: beta.
+// MVM's gather (p^T q; kind 0: alpha), and from the preconditioner's scatter
+// pass (||r||^2 after the update) with its gather (r^T z, at part2; kind 1:
+// the update's bookkeeping, then beta).
 __global__ void __launch_bounds__(CG_THREADS) k_cg_finish(const double* __restrict__ part,
+                                                          const double* __restrict__ part2,
                                                           int nb, int kind, ColState cs) {
   __shared__ double sh[32];
   __shared__ double tot[CG_MAXS];
   sum_columns(part, nb, cs.s, 1, 0, tot, sh);
-  if (kind == 0) alpha_finish(tot, cs);
-  else if (kind == 1) update_finish(tot, cs, sh);
-  else beta_finish(tot, cs, 0);
+  if (kind == 0) {
+    alpha_finish(tot, cs);
+    return;
+  }
+  update_finish(tot, cs, sh);
+  __syncthreads();   // active flags settled before beta reads them
+  sum_columns(part2, nb, cs.s, 1, 0, tot, sh);
+  beta_finish(tot, cs, 0);
 }
 
 }  // namespace
@@ -519,7 +526,7 @@ int cg_run(dski_handle h, CgRun& run) {
       DSKI_TRY(mvm_pcg_fused(h, P, Z, cs.beta, Q, s, dpA));
       {
         StageScope sc(h, ST_PCGVEC, st);
-        k_cg_finish<<<1, CG_THREADS, 0, st>>>(dpA, nbp, 0, cs);
+        k_cg_finish<<<1, CG_THREADS, 0, st>>>(dpA, nullptr, nbp, 0, cs);
       }
       DSKI_LAUNCHED();
       CgUpdate up;
@@ -531,9 +538,8 @@ int cg_run(dski_handle h, CgRun& run) {
       up.dpart = dpU;
       DSKI_TRY(grid_precond_apply(h, run.pc, R, Z, s, &up, dpZ));
       {
-        StageScope sc(h, ST_PCGVEC, st, 2);
-        k_cg_finish<<<1, CG_THREADS, 0, st>>>(dpU, nbp, 1, cs);
-        k_cg_finish<<<1, CG_THREADS, 0, st>>>(dpZ, nbp, 2, cs);
+        StageScope sc(h, ST_PCGVEC, st);
+        k_cg_finish<<<1, CG_THREADS, 0, st>>>(dpU, dpZ, nbp, 1, cs);
       }
       DSKI_LAUNCHED();
       return DSKI_OK;
