@@ -288,3 +288,25 @@ def test_autograd_function_returns_the_adjoint_gradient():
     assert np.allclose(g.numpy(), g2, rtol=1e-12, atol=0)
     pc.close()
     op.close()
+
+
+def test_graph_replay_matches_direct_launches():
+    """The PCG chunks replay as CUDA graphs unless the stage timers record;
+    both run the same kernels in the same order, so the iterates agree
+    bitwise (FP64 and FP64_TC, the fused grid-form path and restarts)."""
+    need_gpu()
+    for prec, make in (("fp64", lambda: W.sine2d()),
+                       ("fp64_tc", lambda: dict(W.small2d(2000, m=56, seed=7, nv=1e-2, ng=1e-2),
+                                                m=(56, 64)))):
+        p = make()
+        op = gpu_op(p, prec)
+        pc = op.pivchol(20)
+        b = torch.tensor(p["y"], device="cuda")
+        x1, it1, rr1 = op.solve(b, pc, rtol=1e-12, maxit=200, allow_not_converged=True)
+        op.profile_start()
+        x2, it2, rr2 = op.solve(b, pc, rtol=1e-12, maxit=200, allow_not_converged=True)
+        op.profile_stop()
+        assert it1 == it2 and rr1 == rr2, (prec, it1, it2, rr1, rr2)
+        assert torch.equal(x1, x2), prec
+        pc.close()
+        op.close()
