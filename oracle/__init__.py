@@ -15,6 +15,7 @@ the paper it follows.
 Modules
 -------
 keys    Keys cubic-convolution kernel, its derivative, 1-D stencils (Sec. 3.1)
+quintic six-point quintic kernel (Meijering et al.), its derivative, 1-D stencils (Sec. 3.1)
 dse     exact derivative SE kernel matrix K^grad (Sec. 2, App. A, App. B)
 dski    D-SKI: grid, Kronecker factors, explicit sparse [W; dW], K~ (Sec. 3.1)
 solve   dense Cholesky, pivoted Cholesky, QR-form preconditioner, PCG (Sec. 2, 3.3)

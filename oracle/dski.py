@@ -5,8 +5,10 @@
 * K_UU = s_f^2 K_1 (x) ... (x) K_d with K_k[a, b] = exp(-(u_a - u_b)^2 / 2 l_k^2):
   the SE kernel of App. A is a product over dimensions, so on a tensor grid
   it is a Kronecker product.
-* W holds tensor-product Keys weights w_i(u) = prod_k omega(t_ik - u_k);
-  dW_p differentiates them in dimension p only (omega'/h_p there).
+* W holds tensor-product interpolation weights w_i(u) = prod_k phi(t_ik - u_k)
+  with phi Keys' cubic kernel (4 nodes per dimension) or the paper's
+  six-point quintic kernel (6 nodes per dimension), as the grid's ``interp``
+  says; dW_p differentiates them in dimension p only (phi'/h_p there).
 * K~ = B K_UU B^T + diag(noise) with B = [W; dW_1; ...; dW_d] (N x m,
   N = n(d+1)), noise sigma_v^2 on value rows and sigma_g^2 on gradient rows.
 
@@ -19,13 +21,21 @@ import numpy as np
 import scipy.sparse as sp
 
 from .keys import omega, domega
+from .quintic import omega5, domega5
 
 
 @dataclass(frozen=True)
 class Grid:
+    """Regular grid plus the interpolation scheme on it ("cubic" or "quintic")."""
     m: tuple
     lo: tuple
     hi: tuple
+    interp: str = "cubic"
+
+    @property
+    def stencil(self):
+        """(nodes per dimension S, offset of the first node below floor(t))."""
+        return (6, 2) if self.interp == "quintic" else (4, 1)
 
     @property
     def d(self):
@@ -82,23 +92,26 @@ def kuu_apply(grid, lengthscale, outputscale, G):
 
 
 def stencils(X, grid):
-    """Per point and dimension: first node c_k - 1, weights and derivative
-    weights of the four stencil nodes (t = (x - lo)/h, c = floor(t))."""
+    """Per point and dimension: first node c_k - lead, weights and derivative
+    weights of the S stencil nodes (t = (x - lo)/h, c = floor(t); S = 4,
+    lead = 1 for the cubic kernel, S = 6, lead = 2 for the quintic)."""
     X = np.asarray(X, np.float64)
     n, d = X.shape
+    S, lead = grid.stencil
+    phi, dphi = (omega5, domega5) if grid.interp == "quintic" else (omega, domega)
     first = np.empty((n, d), np.int64)
-    w = np.empty((n, d, 4))
-    dw = np.empty((n, d, 4))
+    w = np.empty((n, d, S))
+    dw = np.empty((n, d, S))
     for k in range(d):
         h = grid.h[k]
         t = (X[:, k] - grid.lo[k]) / h
         c = np.floor(t).astype(np.int64)
-        if np.any(c < 1) or np.any(c > grid.m[k] - 3):
+        if np.any(c < lead) or np.any(c > grid.m[k] - S + lead):
             raise ValueError("point outside the interpolation grid")
-        first[:, k] = c - 1
-        s = t[:, None] - (c[:, None] - 1 + np.arange(4)[None, :])
-        w[:, k, :] = omega(s)
-        dw[:, k, :] = domega(s) / h
+        first[:, k] = c - lead
+        s = t[:, None] - (c[:, None] - lead + np.arange(S)[None, :])
+        w[:, k, :] = phi(s)
+        dw[:, k, :] = dphi(s) / h
     return first, w, dw
 
 
@@ -109,7 +122,7 @@ def interp_matrix(X, grid):
     strides = [int(np.prod(grid.m[k + 1:])) for k in range(d)]
     rows, cols, vals = [], [], []
     pts = np.arange(n)
-    for offs in itertools.product(range(4), repeat=d):
+    for offs in itertools.product(range(w.shape[2]), repeat=d):
         col = np.zeros(n, np.int64)
         for k in range(d):
             col += (first[:, k] + offs[k]) * strides[k]
