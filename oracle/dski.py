@@ -91,6 +91,49 @@ def kuu_apply(grid, lengthscale, outputscale, G):
     return outputscale**2 * kron_apply(facs, G)
 
 
+def circulant_size(m):
+    """Smallest power of two L >= 2 m - 1: an m x m Toeplitz matrix embeds in
+    the leading block of an L x L circulant."""
+    L = 1
+    while L < 2 * m - 1:
+        L *= 2
+    return L
+
+
+def toeplitz_fft_apply(col, X):
+    """T X for the symmetric Toeplitz T with first column col (m entries), by
+    circulant embedding and the FFT (Sec. 3.1: on a regular grid the SE
+    factors are Toeplitz, and FFTs give O(m log m) products with K_UU).
+    The circulant's first column is [col, 0 ..., col reversed without col[0]];
+    its eigenvalues are the DFT of that column, so T x is the first m entries
+    of IFFT(DFT(c) * FFT(x zero-padded to L))."""
+    col = np.asarray(col, np.float64)
+    X = np.asarray(X, np.float64)
+    m = col.shape[0]
+    L = circulant_size(m)
+    c = np.zeros(L)
+    c[:m] = col
+    if m > 1:
+        c[L - m + 1:] = col[1:][::-1]
+    Xp = np.zeros((L,) + X.shape[1:])
+    Xp[:m] = X
+    lam = np.fft.fft(c)
+    spec = np.fft.fft(Xp, axis=0) * lam.reshape((L,) + (1,) * (X.ndim - 1))
+    return np.fft.ifft(spec, axis=0).real[:m]
+
+
+def kuu_apply_fft(grid, lengthscale, outputscale, G):
+    """K_UU G with each Kronecker factor applied by its circulant embedding
+    (the same product as kuu_apply, in O(M sum_k log m_k))."""
+    m = list(grid.m)
+    s = G.shape[1]
+    T = np.asarray(G, np.float64).reshape(*m, s)
+    for k in range(grid.d):
+        col = kfactor(grid, k, lengthscale[k])[:, 0]
+        T = np.moveaxis(toeplitz_fft_apply(col, np.moveaxis(T, k, 0)), 0, k)
+    return outputscale**2 * T.reshape(-1, s)
+
+
 def stencils(X, grid):
     """Per point and dimension: first node c_k - lead, weights and derivative
     weights of the S stencil nodes (t = (x - lo)/h, c = floor(t); S = 4,

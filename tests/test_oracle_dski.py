@@ -104,3 +104,29 @@ def test_abs_mvm_bounds_the_product():
     want = Ba @ kuu_dense(g, op.ell, op.sf) @ Ba.T @ np.abs(v) + op.noise * np.abs(v)
     assert np.allclose(op.abs_mvm(v), want, rtol=1e-13, atol=0)
     assert np.all(op.abs_mvm(v) >= np.abs(op.mvm(v)) * (1 - 1e-13))
+
+
+def test_circulant_embedding_sizes():
+    from oracle.dski import circulant_size
+    assert [circulant_size(m) for m in (1, 2, 3, 4, 5, 256, 257, 1024, 1027)] == \
+        [1, 4, 8, 8, 16, 512, 1024, 2048, 4096]
+
+
+@pytest.mark.parametrize("m", [1, 2, 5, 17, 64])
+def test_toeplitz_fft_apply_equals_dense(m):
+    # the FFT product of a symmetric Toeplitz matrix equals the dense one
+    from oracle.dski import toeplitz_fft_apply
+    from scipy.linalg import toeplitz
+    rng = np.random.default_rng(m)
+    col = rng.normal(size=m)
+    X = rng.normal(size=(m, 3))
+    assert np.allclose(toeplitz_fft_apply(col, X), toeplitz(col) @ X, rtol=0, atol=1e-12 * m)
+
+
+def test_kuu_apply_fft_equals_kronecker():
+    from oracle.dski import kuu_apply_fft
+    g = Grid(m=(9, 14, 6), lo=(0, -1, 0.5), hi=(1, 2, 1.5))
+    ell = np.array([0.3, 0.9, 0.2])
+    G = np.random.default_rng(8).normal(size=(g.size, 2))
+    ref = kuu_apply(g, ell, 1.3, G)
+    assert np.allclose(kuu_apply_fft(g, ell, 1.3, G), ref, rtol=0, atol=1e-13 * np.abs(ref).max() * 10)
