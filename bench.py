@@ -42,25 +42,31 @@ PROF_ITERS = 3000   # PCG iterations of the profiled (untimed) step
 RTOL = 1e-8
 
 
-def workload_name(n):
-    return f"terrain2d n={n} d=2 N={3 * n} grid=256x256 rank={RANK} rtol={RTOL:g}"
+def workload_name(n, interp="cubic", kuu="dense"):
+    tail = ("" if interp == "cubic" else f" interp={interp}") + ("" if kuu == "dense" else f" kuu={kuu}")
+    return f"terrain2d n={n} d=2 N={3 * n} grid=256x256 rank={RANK} rtol={RTOL:g}{tail}"
 
 
-def mvm_bytes(n, d, M, s, elem):
+def stencil_nodes(interp):
+    """Nodes per dimension of the interpolation stencil."""
+    return 6 if interp == "quintic" else 4
+
+
+def mvm_bytes(n, d, M, s, elem, S=4):
     """Algorithmic HBM bytes of one MVM: v read by scatter and by the noise
     term, out written, the grid written by scatter and read by gather, and
-    the per-point geometry (cell id + 8 d weights) read by scatter and gather."""
+    the per-point geometry (cell id + 2 S d weights) read by scatter and gather."""
     N = n * (d + 1)
-    geo = n * (4 + elem * 8 * d)
+    geo = n * (4 + elem * 2 * S * d)
     return s * (3 * N * elem + 2 * M * elem) + 2 * geo
 
 
-def scatter_bytes(n, d, M, s, elem):
+def scatter_bytes(n, d, M, s, elem, S=4):
     """HBM model of one scatter: v (N s elements) read, the per-point weight
-    table (8 d elements) and cell id (4 B) read, the grid (M s elements)
+    table (2 S d elements) and cell id (4 B) read, the grid (M s elements)
     written."""
     N = n * (d + 1)
-    return N * s * elem + n * (4 + 8 * d * elem) + M * s * elem
+    return N * s * elem + n * (4 + 2 * S * d * elem) + M * s * elem
 
 
 OZ_PAIRS = 36   # digit pairs (a, b), a + b < 8, of the FP64_TC mode product
@@ -70,12 +76,12 @@ OZ_PAIRS = 36   # digit pairs (a, b), a + b < 8, of the FP64_TC mode product
 OZ_MODE_TRAFFIC = 1_626_880
 
 
-def scatter_flops(n, d):
+def scatter_flops(n, d, S=4):
     """Algorithmic FP64 flops of one d = 2 scatter in its sum-factorised form,
-    per point: 3 scalings, 4 c_a = w_a v0 + w'_a v1 (3 flops each), 4 e_a =
-    w_a v2, then 16 stencil nodes x (w1_b c_a + w1'_b e_a) (2 FMAs)."""
+    per point: 3 scalings, S c_a = w_a v0 + w'_a v1 (3 flops each), S e_a =
+    w_a v2, then S^2 stencil nodes x (w1_b c_a + w1'_b e_a) (2 FMAs)."""
     assert d == 2
-    return n * (3 + 4 * 3 + 4 + 16 * 4)
+    return n * (3 + S * 3 + S + S * S * 4)
 
 
 def precond_bytes(N, r, s):
@@ -170,8 +176,8 @@ def cpu_baseline(p, iters_gpu, budget_s=12.0):
     from oracle.dski import DSKI as ODSKI, Grid
     from oracle.solve import QRPreconditioner, pcg, pivoted_cholesky
     t0 = time.perf_counter()
-    op = ODSKI(p["X"], Grid(p["m"], p["lo"], p["hi"]), p["ell"], p["sf"], p["noise_value"],
-               p["noise_grad"])
+    op = ODSKI(p["X"], Grid(p["m"], p["lo"], p["hi"], p.get("interp", "cubic")), p["ell"],
+               p["sf"], p["noise_value"], p["noise_grad"])
     L, _, _ = pivoted_cholesky(op.kgrad_diag(), op.kgrad_row, RANK)
     Pc = QRPreconditioner(L, op.noise)
     t_setup = time.perf_counter() - t0
@@ -261,6 +267,60 @@ def run_sweep(args):
     return 0
 
 
+KUU_SWEEP = (256, 512, 1024)
+
+
+def run_kuu_sweep(args):
+    """The products with K_UU at growing grids (d = 2, g x g nodes over
+    [-0.05, 1.05]^2, l = 0.05 * 256 / g so that every grid resolves its kernel
+    alike, 200,000 points uniform in [0,1]^2): device time of the d mode
+    products per MVM (stage timers, kron stage), dense Kronecker factors on
+    the FP64 units, on the tensor cores (FP64_TC, m <= 256) and the
+    Toeplitz/FFT form, with the FFT MVM's relative difference from the dense
+    FP64 MVM.  Inputs are made on the device (seeded)."""
+    import torch
+    from paper_1810_12283_gb300 import DSKI
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    reps = 20
+    n = 200_000
+    pts = []
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(17)
+    X = torch.rand((n, 2), generator=gen, device=dev, dtype=torch.float64)
+    v = torch.randn(3 * n, generator=gen, device=dev, dtype=torch.float64)
+    for g in KUU_SWEEP:
+        ell = 0.05 * 256 / g
+        outs = {}
+        for prec, kuu in (("fp64", "dense"), ("fp64_tc", "dense"), ("fp64", "fft")):
+            if prec == "fp64_tc" and g > 256:
+                continue
+            op = DSKI(X, [g, g], [-0.05, -0.05], [1.05, 1.05], [ell, ell], 1.0, 1e-3, 1e-3,
+                      prec=prec, kuu=kuu)
+            out = torch.empty_like(v)
+            for _ in range(3):
+                op.mvm(v, out=out)
+            torch.cuda.synchronize()
+            op.profile_start()
+            for i in range(reps):
+                flush.fill_(i & 255)
+                op.mvm(v, out=out)
+            st = op.profile_stop()[0]
+            outs[(prec, kuu)] = out.clone()
+            op.close()
+            pts.append({"grid": g, "prec": prec, "kuu": kuu,
+                        "kron_us_per_mvm": round(1e3 * st["kron"][0] / reps, 2),
+                        "mvm_us": round(1e3 * sum(x[0] for x in st.values()) / reps, 2)})
+        ref = outs[("fp64", "dense")]
+        d = float(torch.linalg.norm(outs[("fp64", "fft")] - ref) / torch.linalg.norm(ref))
+        pts.append({"grid": g, "fft_vs_dense_fp64_rel": d})
+    print(json.dumps({"metric": "K_UU mode products per D-SKI MVM: dense Kronecker vs Toeplitz/FFT",
+                      "unit": "us", "n": n, "reps": reps,
+                      "l2": "flushed before each timed MVM (256 MiB write)", "points": pts}),
+          flush=True)
+    return 0
+
+
 def run_reference(args, p):
     rank, ws, dist = dist_init()
     if rank != 0:
@@ -278,7 +338,7 @@ def run_reference(args, p):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(p["X"].shape[0]), "l2": "n/a (CPU)"},
+            "config": {"workload": workload_name(p["X"].shape[0], p["interp"], p["kuu"]), "l2": "n/a (CPU)"},
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -302,17 +362,28 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=120126,
                     help="reference arm: PCG iterations to scale the oracle's per-iteration time to")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--interp", default="cubic", choices=["cubic", "quintic"],
+                    help="interpolation stencil (Keys cubic, 4^d; the paper's quintic, 6^d)")
     ap.add_argument("--sweep", action="store_true",
                     help="instead of the solve step: scatter / gather bandwidth at n = 1e5 .. 3e7")
     ap.add_argument("--sweep-max-n", type=int, default=30_000_000)
+    ap.add_argument("--kuu-sweep", action="store_true",
+                    help="instead of the solve step: K_UU products, dense vs FFT, grids 256..1024")
+    ap.add_argument("--kuu", default="dense", choices=["dense", "fft"],
+                    help="products with K_UU: dense Kronecker factors or Toeplitz/FFT")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     args.steps = max(args.steps, 1)
 
     from synth import workloads as W
     p = W.terrain2d(n=args.n)
+    p["interp"] = args.interp
+    p["kuu"] = args.kuu
+    SN = stencil_nodes(args.interp)
     if args.sweep:
         return run_sweep(args)
+    if args.kuu_sweep:
+        return run_kuu_sweep(args)
     if args.impl == "reference":
         return run_reference(args, p)
 
@@ -333,7 +404,7 @@ def main():
 
     def step(prec, X_, y_, prof=False, maxit=None):
         op = DSKI(X_, p["m"], p["lo"], p["hi"], p["ell"], p["sf"], p["noise_value"],
-                  p["noise_grad"], prec=prec)
+                  p["noise_grad"], prec=prec, interp=args.interp, kuu=args.kuu)
         if prof:
             op.profile_start()
         pc = op.pivchol(RANK)
@@ -380,7 +451,7 @@ def main():
 
     def mvm_rate(prec, reps=50):
         op = DSKI(X, p["m"], p["lo"], p["hi"], p["ell"], p["sf"], p["noise_value"],
-                  p["noise_grad"], prec=prec)
+                  p["noise_grad"], prec=prec, interp=args.interp, kuu=args.kuu)
         v = torch.randn(N, device=dev, dtype=op.dtype)
         out = torch.empty_like(v)
         for _ in range(5):
@@ -400,7 +471,7 @@ def main():
         op.close()
         per = tot / reps
         elem = 8 if prec in ("fp64", "fp64_tc") else 4
-        return {"ms_per_mvm": per, "gbs": mvm_bytes(n, d, M, 1, elem) / (per / 1e3) / 1e9,
+        return {"ms_per_mvm": per, "gbs": mvm_bytes(n, d, M, 1, elem, SN) / (per / 1e3) / 1e9,
                 "stages_us": {k: round(1e3 * v[0] / max(v[2], 1) * v[1] / reps, 2)
                               for k, v in st.items() if v[1]}}
 
@@ -423,7 +494,8 @@ def main():
                              "s_per_iter": msc[-1] / 1e3 / max(itc[-1], 1)}
         except Exception as e:   # noqa: BLE001 -- reported, not fatal
             compare[mode] = {"error": str(e)}
-    mvm = {prec: mvm_rate(prec) for prec in ("fp64", "fp64_tc", "mixed_3xtf32")}
+    mvm = {prec: mvm_rate(prec) for prec in ("fp64", "fp64_tc", "mixed_3xtf32")
+           if not (args.kuu == "fft" and prec.startswith("mixed"))}   # FFT: FP64 vectors only
 
     # end to end through the public calls with host buffers
     Xh = torch.tensor(p["X"]).pin_memory()
@@ -472,7 +544,7 @@ def main():
     traffic = None
     if args.prec in ("fp64", "fp64_tc"):
         per_sc = 2 * per_launch_ms["scatter"] / 1e3
-        fl = scatter_flops(n, d)
+        fl = scatter_flops(n, d, SN)
         roof_scatter = {"kernel": "k_scatter_prep + k_scatter_ab (scatter)", "bound": "alu",
                         "achieved": fl / per_sc / 1e12, "peak": 1.25, "unit": "TFLOP/s",
                         "frac": fl / per_sc / 1e12 / 1.25, "peak_source": fp64_peak_src,
@@ -493,7 +565,7 @@ def main():
             " sustained dense BF16 (cuBLAS)"
     else:
         per_s = 2 * per_launch_ms["scatter"] / 1e3
-        algo = scatter_bytes(n, d, M, 1, 4)
+        algo = scatter_bytes(n, d, M, 1, 4, SN)
         achieved = algo / per_s / 1e9
         kern, bound, unit, peak, peak_src = ("k_scatter_cells + k_scatter_nodes (scatter)", "hbm",
                                              "GB/s", hbm, hbm_src + " HBM copy bandwidth")
@@ -501,7 +573,7 @@ def main():
         "metric": METRIC, "value": t_step, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(n), "mode": args.prec,
+        "config": {"workload": workload_name(n, p["interp"], p["kuu"]), "mode": args.prec,
                    "l2": "flushed before each timed step (256 MiB write)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "solve": {"iters": its, "relres": rrs, "s_per_iter": t_step / it_last,

@@ -62,21 +62,48 @@ typedef enum {
  * MIXED_TF32: as MIXED_3XTF32 with a single TF32 product.  In the mixed
  * modes CG scalars, dot products, x and r stay FP64 (see dski_pcg_solve).
  * FP64_TC: FP64 vectors, scatter and gather as in FP64, Kronecker mode
- * products on the BF16 tensor cores with both operands split into six 7-bit
- * digits whose products accumulate exactly in FP32 (relative error ~2^-42
- * of |K| |g|); needs every m_k a multiple of 8 and <= 256.  Vectors are
+ * products (for m_k >= 64) on the BF16 tensor cores: each row of both
+ * operands is scaled to a 62-bit integer and split into eight signed 8-bit
+ * digits; the 36 leading digit-pair products accumulate exactly in FP32 and
+ * combine exactly in integers (error ~2^-61 of the row maxima's product
+ * per term); needs every m_k a multiple of 8 and <= 256.  Vectors are
  * double in FP64 and FP64_TC, float in the MIXED modes. */
 typedef enum { DSKI_FP64 = 0, DSKI_MIXED_3XTF32 = 1, DSKI_MIXED_TF32 = 2,
                DSKI_FP64_TC = 3 } dski_precision;
 
+/* Interpolation scheme of W and dW (Sec. 3.1): the rows of W hold the
+ * tensor products of a 1-D convolution kernel phi at the grid nodes, dW its
+ * derivatives.  CUBIC: Keys' cubic convolution (a = -1/2), 4 nodes per
+ * dimension (4^d per row).  QUINTIC: the six-point quintic kernel the paper
+ * uses (Meijering et al. 1999: even, piecewise quintic, interpolating, C^3,
+ * reproducing quadratics), 6 nodes per dimension (6^d per row).  A
+ * zero-initialised dski_params selects CUBIC. */
+typedef enum { DSKI_INTERP_CUBIC = 0, DSKI_INTERP_QUINTIC = 1 } dski_interp;
+
+/* How the products with K_UU are formed (Sec. 3.1).  DENSE: each Kronecker
+ * factor K_k is applied as a dense m_k x m_k matrix (FP64 units, or the
+ * tensor cores as the precision mode says).  FFT: each factor is a
+ * symmetric Toeplitz matrix on the regular grid and is applied through its
+ * embedding in an L x L circulant (L the smallest power of two >= 2 m_k - 1)
+ * with FP64 FFTs, O(m_k log m_k) per grid line instead of O(m_k^2); FP64 and
+ * FP64_TC modes only.  The FFT's rounding is normwise (~log2(L) u |Fc| |x|
+ * per product), so dski_pcg_solve forms its true residuals with the dense
+ * factors and its restarts refine x against the dense operator.  The
+ * gradient of Eq. 1 applies dK_k / dlog l_k densely in either case.  A
+ * zero-initialised dski_params selects DENSE. */
+typedef enum { DSKI_KUU_DENSE = 0, DSKI_KUU_FFT = 1 } dski_kuu;
+
 /* Problem statement of Sec. 2 / Sec. 3.1 / App. A.
  *   n, d          points and dimensions, n >= 1, 1 <= d <= 3.
- *   grid_m[d]     grid nodes per dimension, 4 <= m_k <= 1027; grid nodes are
+ *   grid_m[d]     grid nodes per dimension, S <= m_k <= 1027 (S = 4 for the
+ *                 cubic, 6 for the quintic stencil); grid nodes are
  *                 u_a = lo_k + a (hi_k - lo_k)/(m_k - 1), a = 0..m_k-1 (both
  *                 end points included); the grid is flattened in C order.
- *   grid_lo/hi[d] grid extent, lo_k < hi_k.  Every point needs
- *                 1 <= floor((x_k - lo_k)/h_k) <= m_k - 3 in every dimension
- *                 so that its four stencil nodes exist (else OUT_OF_GRID).
+ *   grid_lo/hi[d] grid extent, lo_k < hi_k.  With c = floor((x_k - lo_k)/h_k)
+ *                 the stencil nodes are c - 1 .. c + 2 (cubic) or
+ *                 c - 2 .. c + 3 (quintic), so every point needs
+ *                 1 <= c <= m_k - 3 (cubic) or 2 <= c <= m_k - 4 (quintic) in
+ *                 every dimension (else OUT_OF_GRID).
  *   lengthscale[d] SE length scales l_k > 0 (ARD form of App. A).
  *   outputscale   sigma_f > 0; K_UU = sigma_f^2 K_1 (x) ... (x) K_d with
  *                 K_k[a,b] = exp(-(u_a - u_b)^2 / (2 l_k^2)).
@@ -84,6 +111,8 @@ typedef enum { DSKI_FP64 = 0, DSKI_MIXED_3XTF32 = 1, DSKI_MIXED_TF32 = 2,
  *   noise_grad    sigma^2 added on gradient rows (> 0).  Sec. 2 uses one
  *                 noise; the terrain experiment of Sec. 4 fits two.
  *   prec          arithmetic of the MVM (dski_precision).
+ *   interp        interpolation scheme (dski_interp; 0 = CUBIC).
+ *   kuu           K_UU product (dski_kuu; 0 = DENSE).
  * The arrays are read during dski_create only. */
 typedef struct {
   int n, d;
@@ -94,6 +123,8 @@ typedef struct {
   double outputscale;
   double noise_value, noise_grad;
   dski_precision prec;
+  dski_interp interp;
+  dski_kuu kuu;
 } dski_params;
 
 /* Sec. 3.1: build the D-SKI operator for the points X_dev (device, n x d

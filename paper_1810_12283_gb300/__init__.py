@@ -15,9 +15,9 @@ import ctypes as C
 import torch
 
 from . import _lib
-from ._lib import DskiError, PREC
+from ._lib import DskiError, PREC, INTERP, KUU
 
-__all__ = ["DSKI", "Preconditioner", "DskiError", "PREC", "mll_function", "launch_count"]
+__all__ = ["DSKI", "Preconditioner", "DskiError", "PREC", "INTERP", "KUU", "mll_function", "launch_count"]
 
 
 def _stream_ptr(stream):
@@ -65,14 +65,20 @@ class Preconditioner:
 class DSKI:
     """D-SKI operator K~ = [W; dW] K_UU [W; dW]^T + diag(noise) on a regular grid.
 
-    X: (n, d) float64 CUDA tensor of points.  Vectors are length N = n(d+1)
+    X: (n, d) float64 CUDA tensor of points.  ``interp`` picks the stencil of
+    W and dW: "cubic" (Keys, 4^d nodes per row) or "quintic" (the paper's
+    six-point kernel, 6^d nodes per row).  ``kuu`` picks how the Kronecker
+    factors of K_UU are applied: "dense" or "fft" (Toeplitz factors through
+    circulant embedding and FP64 FFTs; FP64 and FP64_TC modes).  Vectors are
+    length N = n(d+1)
     in block order [values; d/dx_1; ...; d/dx_d] (columns of an (N, s)
     tensor stored column-major, i.e. pass ``V.T.contiguous().T`` or an
     (s, N) tensor's transpose -- the helpers below take (N,) or (s, N)).
     """
 
     def __init__(self, X, grid_m, grid_lo, grid_hi, lengthscale, outputscale=1.0,
-                 noise_value=1e-4, noise_grad=None, prec="fp64", stream=None):
+                 noise_value=1e-4, noise_grad=None, prec="fp64", stream=None,
+                 interp="cubic", kuu="dense"):
         lib = _lib.load()
         if not (isinstance(X, torch.Tensor) and X.is_cuda):
             raise TypeError("X must be a CUDA tensor")
@@ -80,6 +86,8 @@ class DSKI:
         n, d = X.shape
         self.n, self.d, self.N = n, d, n * (d + 1)
         self.prec = prec
+        self.interp = interp
+        self.kuu = kuu
         self.dtype = torch.float64 if prec in ("fp64", "fp64_tc") else torch.float32
         self.device = X.device
         self.stream = stream
@@ -91,7 +99,7 @@ class DSKI:
         ell = list(lengthscale) if hasattr(lengthscale, "__len__") else [lengthscale] * d
         self._ell = (C.c_double * d)(*[float(v) for v in ell])
         p = _lib.DskiParams(n, d, self._m, self._lo, self._hi, self._ell, float(outputscale),
-                            float(noise_value), float(ng), PREC[prec])
+                            float(noise_value), float(ng), PREC[prec], INTERP[interp], KUU[kuu])
         h = C.c_void_p()
         _lib.check(lib.dski_create(C.byref(h), C.byref(p), _dptr(X), _stream_ptr(stream)))
         self.h = h

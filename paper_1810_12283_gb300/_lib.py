@@ -14,6 +14,8 @@ DSKI_OK = 0
 STATUS = {0: "OK", -1: "ARG", -2: "OUT_OF_GRID", -3: "CUDA", -4: "NOT_CONVERGED",
           -5: "BREAKDOWN", -6: "TIMEOUT", -7: "ALLOC"}
 PREC = {"fp64": 0, "mixed_3xtf32": 1, "mixed_tf32": 2, "fp64_tc": 3}
+INTERP = {"cubic": 0, "quintic": 1}
+KUU = {"dense": 0, "fft": 1}
 
 # every extern "C" symbol include/dski.h declares
 EXPORTS = ["dski_create", "dski_set_hypers", "dski_mvm", "pivchol_build", "dski_pcg_solve",
@@ -32,7 +34,7 @@ class DskiParams(C.Structure):
                 ("lengthscale", C.POINTER(C.c_double)),
                 ("outputscale", C.c_double),
                 ("noise_value", C.c_double), ("noise_grad", C.c_double),
-                ("prec", C.c_int)]
+                ("prec", C.c_int), ("interp", C.c_int), ("kuu", C.c_int)]
 
 
 class DskiError(RuntimeError):

@@ -147,6 +147,8 @@ static void release_all(dski_handle h) {
     h->Khi[k].release();
     h->Klo[k].release();
     h->dK64[k].release();
+    h->fft_tw[k].release();
+    h->fft_lam[k].release();
     h->Kdig[k].release();
     h->Kexp[k].release();
   }
@@ -190,11 +192,18 @@ extern "C" int dski_create(dski_handle* out, const dski_params* p, const double*
     return set_error(DSKI_ERR_ARG, "dski_create: unknown precision %d", (int)p->prec);
   if (!finite_pos(p->outputscale) || !finite_pos(p->noise_value) || !finite_pos(p->noise_grad))
     return set_error(DSKI_ERR_ARG, "dski_create: outputscale and noises must be finite and > 0");
+  if (p->interp != DSKI_INTERP_CUBIC && p->interp != DSKI_INTERP_QUINTIC)
+    return set_error(DSKI_ERR_ARG, "dski_create: unknown interpolation scheme %d", (int)p->interp);
+  const int sw = p->interp == DSKI_INTERP_QUINTIC ? 6 : 4;   // stencil nodes per dimension
+  if (p->kuu != DSKI_KUU_DENSE && p->kuu != DSKI_KUU_FFT)
+    return set_error(DSKI_ERR_ARG, "dski_create: unknown K_UU product %d", (int)p->kuu);
+  if (p->kuu == DSKI_KUU_FFT && p->prec != DSKI_FP64 && p->prec != DSKI_FP64_TC)
+    return set_error(DSKI_ERR_ARG, "dski_create: the FFT K_UU product needs FP64 vectors (FP64 or FP64_TC)");
   long long M = 1, ncell = 1;
   for (int k = 0; k < p->d; ++k) {
-    if (p->grid_m[k] < 4 || p->grid_m[k] > 1027)
-      return set_error(DSKI_ERR_ARG, "dski_create: grid_m[%d] must be in 4..1027 (got %d)", k,
-                       p->grid_m[k]);
+    if (p->grid_m[k] < sw || p->grid_m[k] > 1027)
+      return set_error(DSKI_ERR_ARG, "dski_create: grid_m[%d] must be in %d..1027 (got %d)", k,
+                       sw, p->grid_m[k]);
     if (!(std::isfinite(p->grid_lo[k]) && std::isfinite(p->grid_hi[k]) &&
           p->grid_lo[k] < p->grid_hi[k]))
       return set_error(DSKI_ERR_ARG, "dski_create: need finite grid_lo[%d] < grid_hi[%d]", k, k);
@@ -203,7 +212,7 @@ extern "C" int dski_create(dski_handle* out, const dski_params* p, const double*
     if (p->prec == DSKI_FP64_TC && (p->grid_m[k] % 8 != 0 || p->grid_m[k] > 256))
       return set_error(DSKI_ERR_ARG, "dski_create: FP64_TC needs grid_m[%d] a multiple of 8 and <= 256", k);
     M *= p->grid_m[k];
-    ncell *= p->grid_m[k] - 3;
+    ncell *= p->grid_m[k] - sw + 1;
   }
   if (M > (1LL << 30))
     return set_error(DSKI_ERR_ARG, "dski_create: grid has %lld nodes (max 2^30)", M);
@@ -221,10 +230,13 @@ extern "C" int dski_create(dski_handle* out, const dski_params* p, const double*
   h->nv = p->noise_value;
   h->ng = p->noise_grad;
   h->prec = p->prec;
+  h->sw = sw;
+  h->kuu_fft = p->kuu == DSKI_KUU_FFT;
+  h->lead = sw / 2 - 1;
   h->stream = (cudaStream_t)cuda_stream;
   for (int k = 0; k < p->d; ++k) {
     h->m[k] = p->grid_m[k];
-    h->mc[k] = p->grid_m[k] - 3;
+    h->mc[k] = p->grid_m[k] - sw + 1;
     h->lo[k] = p->grid_lo[k];
     h->hi[k] = p->grid_hi[k];
     h->h[k] = (p->grid_hi[k] - p->grid_lo[k]) / (p->grid_m[k] - 1);

@@ -15,6 +15,8 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <type_traits>
+
 #include "../../include/dski.h"
 
 #define DSKI_MAXD 3
@@ -84,12 +86,16 @@ struct DevBuf {
 struct dski_handle_ {
   int n = 0, d = 0, N = 0;
   int m[DSKI_MAXD] = {1, 1, 1};     // grid nodes per dimension
-  int mc[DSKI_MAXD] = {1, 1, 1};    // cells per dimension (m_k - 3)
+  int mc[DSKI_MAXD] = {1, 1, 1};    // cells per dimension (m_k - sw + 1)
+  // interpolation stencil: sw nodes per dimension (4 cubic, 6 quintic); a
+  // point in cell floor(t) uses the nodes floor(t) - lead .. floor(t) - lead + sw - 1
+  int sw = 4, lead = 1;
   double lo[DSKI_MAXD] = {0, 0, 0}, hi[DSKI_MAXD] = {0, 0, 0}, h[DSKI_MAXD] = {1, 1, 1};
   double ell[DSKI_MAXD] = {1, 1, 1};
   double sf = 1.0, nv = 0.0, ng = 0.0;
   int prec = DSKI_FP64;
-  // FP64_TC: run the mode products on the FP64 units instead (true residuals)
+  // FP64_TC and FFT products: run the mode products as dense factors on the
+  // FP64 units instead (the PCG's true residuals)
   bool kron_exact = false;
   cudaStream_t stream = nullptr;
   // private non-blocking stream for the captured PCG chunks (the legacy
@@ -100,8 +106,8 @@ struct dski_handle_ {
   int ncell = 0;    // prod mc_k
   int sm_count = 0;
 
-  // geometry (sorted order); W64/W32: per point and dimension the four Keys
-  // weights then the four derivative weights (already divided by h_k)
+  // geometry (sorted order); W64/W32: per point and dimension the sw
+  // stencil weights then the sw derivative weights (already divided by h_k)
   dski::DevBuf perm, inv_perm, cell, cell_start, frac64, frac32, W64, W32;
   // Kronecker factors K_k (m_k x m_k, row-major, symmetric): FP64, FP32 and
   // the TF32 hi/lo split of the FP64 value (hi = rna_tf32(K), lo = rna_tf32(K - hi)).
@@ -110,6 +116,11 @@ struct dski_handle_ {
   dski::DevBuf dK64[DSKI_MAXD];
   // FP64_TC mode: eight BF16 digit planes of K_k (8 x m x m) and row exponents
   dski::DevBuf Kdig[DSKI_MAXD], Kexp[DSKI_MAXD];
+  // Toeplitz/FFT products of K_UU (kuu_fft): per factor the twiddles
+  // exp(-2 pi i j / L) (L/2 complex) and the circulant's spectrum / L (L
+  // values, bit-reversed order)
+  bool kuu_fft = false;
+  dski::DevBuf fft_tw[DSKI_MAXD], fft_lam[DSKI_MAXD];
   // FP64_TC: split-K partial sums of the mode products (workspace)
   dski::DevBuf ozP;
   // PCG: per-block partial sums of the dots fused into other kernels
@@ -185,6 +196,12 @@ void set_no_tune(bool on);
 int gather_internal(dski_handle h, const void* grid, const void* vin, void* vout, int s,
                     bool prec64);
 
+// Toeplitz mode products by FFT (kron_fft.cu): the per-factor multipliers
+// (after the factors), and Y = scale K_k X with the contracted mode first
+int fft_circulant_size(int m);
+int fft_prepare(dski_handle h);
+int mode_fft(dski_handle h, int k, const double* X, double* Y, long long R, int s, double scale);
+
 // tensor-core mode product (kron_tc.cu): TF32 (three = false) or 3xTF32
 int mode_tc_tf32(dski_handle h, const float* X, const float* Khi, const float* Klo, float* Y,
                  int m, long long R, int s, float scale, bool three);
@@ -223,6 +240,12 @@ int oz_slice(dski_handle h, const double* A, int rows, int cols, int lda, int mp
              int* fA, int stage);
 // vectors of this handle are double (FP64, FP64_TC) or float (MIXED modes)
 inline bool f64_vectors(dski_handle h) { return h->prec == DSKI_FP64 || h->prec == DSKI_FP64_TC; }
+// fn(std::integral_constant<int, S>{}) with S the handle's stencil width
+template <class F>
+auto with_stencil(dski_handle h, F&& fn) {
+  if (h->sw == 6) return fn(std::integral_constant<int, 6>{});
+  return fn(std::integral_constant<int, 4>{});
+}
 // read and clear the device error word: DSKI_OK, or DSKI_ERR_TIMEOUT if a
 // kernel's bounded wait ran out since the last check (synchronises)
 int check_device_error(dski_handle h);

@@ -2,25 +2,28 @@
 // K_UU (App. A): run once per dski_create / dski_set_hypers.
 //
 //  * each point's grid parameter t_k = (x_k - lo_k)/h_k, cell c_k = floor(t_k)
-//    and fraction f_k = t_k - c_k, in FP64; the four stencil nodes of
-//    dimension k are c_k - 1 .. c_k + 2, so a point needs 1 <= c_k <= m_k - 3;
+//    and fraction f_k = t_k - c_k, in FP64; the S stencil nodes of
+//    dimension k are c_k - lead .. c_k - lead + S - 1 (S = 4, lead = 1 for
+//    Keys' cubic; S = 6, lead = 2 for the quintic kernel), so a point needs
+//    lead <= c_k <= m_k - S + lead;
 //  * the flat cell id (first stencil node per dimension, C order over the
-//    (m_k - 3)-cell grid) is the sort key; a stable LSD radix sort (8-bit
+//    (m_k - S + 1)-cell grid) is the sort key; a stable LSD radix sort (8-bit
 //    digits, deterministic) orders the points by cell, and a CSR cell_start
 //    indexes each cell's points;
 //  * K_k[a, b] = exp(-((a - b) h_k)^2 / (2 l_k^2)) in FP64, with FP32 and TF32
-//    hi/lo copies for the mixed-precision mode products.
+//    hi/lo copies for the mixed-precision mode products, and (Toeplitz/FFT
+//    products) the circulant spectra of kron_fft.cu.
 #include <algorithm>
 #include <vector>
 
 #include "dski_internal.cuh"
-#include "keys.cuh"
+#include "interp.cuh"
 
 namespace dski {
 namespace {
 
 struct GeoParams {
-  int d;
+  int d, sw, lead;
   int m[DSKI_MAXD];
   int mc[DSKI_MAXD];
   double lo[DSKI_MAXD];
@@ -38,12 +41,12 @@ __global__ void k_points(const double* __restrict__ X, int n, GeoParams g,
     const double t = (X[(size_t)i * g.d + k] - g.lo[k]) / g.h[k];
     const double c = floor(t);
     // written so that NaN fails the test
-    if (!(c >= 1.0 && c <= (double)(g.m[k] - 3))) {
+    if (!(c >= (double)g.lead && c <= (double)(g.m[k] - g.sw + g.lead))) {
       ok = false;
       frac[(size_t)i * g.d + k] = 0.0;
       continue;
     }
-    flat = flat * (uint32_t)g.mc[k] + (uint32_t)((int)c - 1);
+    flat = flat * (uint32_t)g.mc[k] + (uint32_t)((int)c - g.lead);
     frac[(size_t)i * g.d + k] = t - c;
   }
   if (!ok) {
@@ -176,23 +179,24 @@ __global__ void k_apply_sort(const uint32_t* __restrict__ skey, const int* __res
 }
 
 // Interpolation weights of each sorted point, computed once in FP64: per
-// dimension k the four Keys weights w_k[o] and derivative weights
-// omega'(.)/h_k, stored as W[j][k][0..3] = w, W[j][k][4..7] = dw (8 d values
-// per point), with an FP32 copy rounded from the FP64 values.
+// dimension k the S stencil weights w_k[o] and derivative weights
+// phi'(.)/h_k, stored as W[j][k][0..S-1] = w, W[j][k][S..2S-1] = dw (2 S d
+// values per point), with an FP32 copy rounded from the FP64 values.
+template <int S>
 __global__ void k_weights(const double* __restrict__ f64, int n, int d, GeoParams g,
                           double* __restrict__ W64, float* __restrict__ W32) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   for (int k = 0; k < d; ++k) {
-    double w[4], dw[4];
-    keys4<double>(f64[(size_t)j * d + k], w, dw);
+    double w[S], dw[S];
+    stencil_weights<S, double>(f64[(size_t)j * d + k], w, dw);
     const double ih = 1.0 / g.h[k];
-    const size_t b = (size_t)j * 8 * d + 8 * k;
-    for (int o = 0; o < 4; ++o) {
+    const size_t b = (size_t)j * 2 * S * d + 2 * S * k;
+    for (int o = 0; o < S; ++o) {
       W64[b + o] = w[o];
-      W64[b + 4 + o] = dw[o] * ih;
+      W64[b + S + o] = dw[o] * ih;
       W32[b + o] = (float)w[o];
-      W32[b + 4 + o] = (float)(dw[o] * ih);
+      W32[b + S + o] = (float)(dw[o] * ih);
     }
   }
 }
@@ -239,6 +243,8 @@ int build_geometry(dski_handle h, const double* X_dev) {
   cudaStream_t st = h->stream;
   GeoParams g{};
   g.d = d;
+  g.sw = h->sw;
+  g.lead = h->lead;
   for (int k = 0; k < d; ++k) {
     g.m[k] = h->m[k];
     g.mc[k] = h->mc[k];
@@ -277,8 +283,8 @@ int build_geometry(dski_handle h, const double* X_dev) {
         cudaStreamSynchronize(st) != cudaSuccess) { rc = DSKI_ERR_CUDA; break; }
     if (nbad > 0) {
       rc = set_error(DSKI_ERR_OUT_OF_GRID,
-                     "%d point(s) lack a full 4^d stencil (need 1 <= floor((x-lo)/h) <= m-3)",
-                     nbad);
+                     "%d point(s) lack a full %d^d stencil (need %d <= floor((x-lo)/h) <= m-%d)",
+                     nbad, h->sw, h->lead, h->sw - h->lead);
       break;
     }
     // number of 8-bit passes needed for keys < ncell
@@ -299,7 +305,8 @@ int build_geometry(dski_handle h, const double* X_dev) {
     if (h->perm.ensure((size_t)n * 4) || h->inv_perm.ensure((size_t)n * 4) ||
         h->cell.ensure((size_t)n * 4) || h->cell_start.ensure((size_t)(h->ncell + 1) * 4) ||
         h->frac64.ensure((size_t)n * d * 8) || h->frac32.ensure((size_t)n * d * 4) ||
-        h->W64.ensure((size_t)n * d * 64) || h->W32.ensure((size_t)n * d * 32)) {
+        h->W64.ensure((size_t)n * d * 2 * h->sw * 8) ||
+        h->W32.ensure((size_t)n * d * 2 * h->sw * 4)) {
       rc = DSKI_ERR_ALLOC;
       break;
     }
@@ -307,8 +314,10 @@ int build_geometry(dski_handle h, const double* X_dev) {
                                                   h->inv_perm.as<int>(), h->cell.as<int>(),
                                                   h->frac64.as<double>(), h->frac32.as<float>());
     k_cell_start<<<(n + 255) / 256, 256, 0, st>>>(kin, n, h->ncell, h->cell_start.as<int>());
-    k_weights<<<(n + 255) / 256, 256, 0, st>>>(h->frac64.as<double>(), n, d, g, h->W64.as<double>(),
-                                               h->W32.as<float>());
+    with_stencil(h, [&](auto S) {
+      k_weights<decltype(S)::value><<<(n + 255) / 256, 256, 0, st>>>(h->frac64.as<double>(), n, d, g,
+                                                      h->W64.as<double>(), h->W32.as<float>());
+    });
     count_launches(3);
     if (cudaGetLastError() != cudaSuccess) { rc = DSKI_ERR_CUDA; break; }
     if (cudaStreamSynchronize(st) != cudaSuccess) { rc = DSKI_ERR_CUDA; break; }
@@ -339,6 +348,7 @@ int build_factors(dski_handle h) {
                                h->Kexp[k].as<int>()));
     }
   }
+  if (h->kuu_fft) DSKI_TRY(fft_prepare(h));
   return DSKI_OK;
 }
 

@@ -1,18 +1,25 @@
-// Keys cubic-convolution weights (a = -1/2), the interpolation scheme D-SKI
-// differentiates (Sec. 3.1).  For one coordinate with grid parameter
-// t = (x - lo)/h, cell c = floor(t) and fraction f = t - c in [0, 1), the
-// four stencil nodes c-1+o (o = 0..3) get weight omega(f + 1 - o) and
-// derivative weight omega'(f + 1 - o) / h, where
-//   omega(s) = 3/2|s|^3 - 5/2|s|^2 + 1           for |s| <= 1,
-//   omega(s) = -1/2|s|^3 + 5/2|s|^2 - 4|s| + 2   for 1 < |s| < 2,
-// (Keys' kernel with a = -1/2) and omega' its derivative in s.  Each branch
-// below is that polynomial at the node's known sign/branch, in Horner form.
+// Interpolation weights of one coordinate, the scheme D-SKI differentiates
+// (Sec. 3.1): for grid parameter t = (x - lo)/h, cell c = floor(t) and
+// fraction f = t - c in [0, 1), the S stencil nodes c - S/2 + 1 + o
+// (o = 0..S-1) get weight phi(t - node) and derivative weight
+// phi'(t - node) / h (the caller multiplies by 1/h).
+//
+// S = 4: Keys' cubic convolution kernel (a = -1/2),
+//   phi(s) = 3/2|s|^3 - 5/2|s|^2 + 1           for |s| <= 1,
+//   phi(s) = -1/2|s|^3 + 5/2|s|^2 - 4|s| + 2   for 1 < |s| < 2.
+// S = 6: the six-point quintic kernel the paper uses (Meijering et al.,
+//   1999): even, piecewise quintic on the knots 0..3, interpolating, C^3
+//   across the knots and at |s| = 3, reproducing quadratics (free parameter
+//   3/64).  With u the distance past the piece's left knot:
+//   |s| in [0, 1]: 1 - 17/8 s^2 + 63/32 s^4 - 27/32 s^5       (s = |s|)
+//   |s| in [1, 2]: u (-19/32 + 5/4 u - 9/16 u^2 - 19/64 u^3 + 13/64 u^4)
+//   |s| in [2, 3]: 3/64 u (1 - u)^4.
+// Each branch below is that polynomial at the node's known piece and sign,
+// in Horner form.
 #pragma once
 
 namespace dski {
 
-// All four weights and derivative weights (derivatives w.r.t. t; the caller
-// multiplies by 1/h).
 template <class T>
 __device__ __forceinline__ void keys4(T f, T w[4], T dw[4]) {
   const T s0 = f + T(1);   // node c-1: s in [1, 2)
@@ -29,31 +36,62 @@ __device__ __forceinline__ void keys4(T f, T w[4], T dw[4]) {
   dw[3] = -((T(-1.5) * s3 + T(5)) * s3 - T(4));
 }
 
-// Weight and derivative weight of the single node c-1+o.
+// quintic pieces and their derivatives (argument: |s| for the inner piece,
+// u in [0, 1] for the others)
 template <class T>
-__device__ __forceinline__ void keys1(T f, int o, T& w, T& dw) {
-  switch (o) {
-    case 0: {
-      const T s = f + T(1);
-      w = ((T(-0.5) * s + T(2.5)) * s - T(4)) * s + T(2);
-      dw = (T(-1.5) * s + T(5)) * s - T(4);
-    } break;
-    case 1: {
-      const T s = f;
-      w = (T(1.5) * s - T(2.5)) * s * s + T(1);
-      dw = (T(4.5) * s - T(5)) * s;
-    } break;
-    case 2: {
-      const T s = T(1) - f;
-      w = (T(1.5) * s - T(2.5)) * s * s + T(1);
-      dw = -((T(4.5) * s - T(5)) * s);
-    } break;
-    default: {
-      const T s = T(2) - f;
-      w = ((T(-0.5) * s + T(2.5)) * s - T(4)) * s + T(2);
-      dw = -((T(-1.5) * s + T(5)) * s - T(4));
-    } break;
-  }
+__device__ __forceinline__ T q5_in(T s) {
+  const T s2 = s * s;
+  return (((T(-27.0 / 32.0) * s + T(63.0 / 32.0)) * s2) + T(-17.0 / 8.0)) * s2 + T(1);
+}
+template <class T>
+__device__ __forceinline__ T q5_in_d(T s) {
+  const T s2 = s * s;
+  return ((T(-135.0 / 32.0) * s + T(63.0 / 8.0)) * s2 + T(-17.0 / 4.0)) * s;
+}
+template <class T>
+__device__ __forceinline__ T q5_mid(T u) {
+  return ((((T(13.0 / 64.0) * u + T(-19.0 / 64.0)) * u + T(-9.0 / 16.0)) * u + T(5.0 / 4.0)) * u +
+          T(-19.0 / 32.0)) * u;
+}
+template <class T>
+__device__ __forceinline__ T q5_mid_d(T u) {
+  return (((T(65.0 / 64.0) * u + T(-19.0 / 16.0)) * u + T(-27.0 / 16.0)) * u + T(5.0 / 2.0)) * u +
+         T(-19.0 / 32.0);
+}
+template <class T>
+__device__ __forceinline__ T q5_out(T u) {
+  const T v = T(1) - u, v2 = v * v;
+  return T(3.0 / 64.0) * u * (v2 * v2);
+}
+template <class T>
+__device__ __forceinline__ T q5_out_d(T u) {
+  const T v = T(1) - u;
+  return T(3.0 / 64.0) * (v * v * v) * (T(1) - T(5) * u);
+}
+
+template <class T>
+__device__ __forceinline__ void quintic6(T f, T w[6], T dw[6]) {
+  const T g = T(1) - f;
+  w[0] = q5_out(f);   // node c-2: s = 2 + f
+  dw[0] = q5_out_d(f);
+  w[1] = q5_mid(f);   // node c-1: s = 1 + f
+  dw[1] = q5_mid_d(f);
+  w[2] = q5_in(f);    // node c  : s = f
+  dw[2] = q5_in_d(f);
+  w[3] = q5_in(g);    // node c+1: s = -(1 - f)
+  dw[3] = -q5_in_d(g);
+  w[4] = q5_mid(g);   // node c+2: s = -(2 - f)
+  dw[4] = -q5_mid_d(g);
+  w[5] = q5_out(g);   // node c+3: s = -(3 - f)
+  dw[5] = -q5_out_d(g);
+}
+
+// All S weights and derivative weights (derivatives w.r.t. t).
+template <int S, class T>
+__device__ __forceinline__ void stencil_weights(T f, T* w, T* dw) {
+  static_assert(S == 4 || S == 6, "stencil of 4 (cubic) or 6 (quintic) nodes");
+  if constexpr (S == 4) keys4<T>(f, w, dw);
+  else quintic6<T>(f, w, dw);
 }
 
 }  // namespace dski

@@ -1,7 +1,7 @@
 // The D-SKI MVM of Sec. 3.1:
 //   K~ v = B (K_UU (B^T v)) + noise .* v,   B = [W; dW_1; ...; dW_d],
 // in three stages on the sorted, point-interleaved internal layout:
-//   scatter  g = B^T v   (grid-node-owned pull over the 4^d neighbouring
+//   scatter  g = B^T v   (grid-node-owned pull over the S^d neighbouring
 //                         cells: deterministic, no atomics)
 //   kron     h = s_f^2 (K_1 (x) ... (x) K_d) g  (d mode products)
 //   gather   out = B h + noise .* v   (point-owned, sum-factorised stencil)
@@ -12,7 +12,7 @@
 #include <mutex>
 
 #include "dski_internal.cuh"
-#include "keys.cuh"
+#include "interp.cuh"
 
 namespace dski {
 
@@ -46,17 +46,22 @@ namespace {
 // ------------------------------------------------------------- scatter ----
 // Grid node u receives sum_i [w_i(u) v_i^0 + sum_p dw_{i,p}(u) v_i^p] over the
 // points i whose stencil covers u, i.e. whose cell (first stencil node) f
-// satisfies u - 3 <= f <= u per dimension.  The cells of the last dimension
-// are contiguous in sorted order, so each (f_0, .., f_{d-2}) gives one range.
-// For d >= 2 four lanes share a node, lane `sub` taking f_0 = u_0 - 3 + sub;
-// their partial sums are combined in a fixed order (deterministic).
-template <class T, int D, int CB>
+// satisfies u - S + 1 <= f <= u per dimension.  The cells of the last
+// dimension are contiguous in sorted order, so each (f_0, .., f_{d-2}) gives
+// one range.  For d >= 2 SPLIT lanes share a node, lane `sub` taking the PER
+// first-dimension cells f_0 = u_0 - S + 1 + sub PER + i; their partial sums
+// are combined in a fixed order (deterministic).
+constexpr int scatter_split(int D, int S) { return D > 1 ? (S == 4 ? 4 : 2) : 1; }
+
+template <class T, int D, int CB, int S>
 __global__ void __launch_bounds__(256) k_scatter(MvmGeo g, const int* __restrict__ cell_start,
                                                  const int* __restrict__ cell,
                                                  const T* __restrict__ wt,
                                                  const T* __restrict__ v, T* __restrict__ grid,
                                                  int s, long long N, long long M) {
-  constexpr int SPLIT = D > 1 ? 4 : 1;
+  constexpr int SPLIT = scatter_split(D, S);
+  constexpr int PER = D > 1 ? S / SPLIT : 1;
+  constexpr int TW = 2 * S;   // table values per point and dimension
   const long long tix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long u = tix / SPLIT;
   const int sub = (int)(tix % SPLIT);
@@ -74,18 +79,20 @@ __global__ void __launch_bounds__(256) k_scatter(MvmGeo g, const int* __restrict
 #pragma unroll
   for (int q = 0; q < CB; ++q) acc[q] = T(0);
   const int L = D - 1;   // last (fastest) dimension
-  const int lo_l = max(0, uc[L] - 3), hi_l = min(uc[L], g.mc[L] - 1);
-  int f0 = 0, lo1 = 0, hi1 = 0;
-  bool active = valid && lo_l <= hi_l;
-  if (D > 1) {
-    f0 = uc[0] - 3 + sub;
-    active = active && f0 >= 0 && f0 <= g.mc[0] - 1;
-  }
+  const int lo_l = max(0, uc[L] - (S - 1)), hi_l = min(uc[L], g.mc[L] - 1);
+  int lo1 = 0, hi1 = 0;
   if (D > 2) {
-    lo1 = max(0, uc[1] - 3);
+    lo1 = max(0, uc[1] - (S - 1));
     hi1 = min(uc[1], g.mc[1] - 1);
   }
-  if (active) {
+  for (int i0 = 0; i0 < PER; ++i0) {
+    int f0 = 0;
+    bool active = valid && lo_l <= hi_l;
+    if (D > 1) {
+      f0 = uc[0] - (S - 1) + sub * PER + i0;
+      active = active && f0 >= 0 && f0 <= g.mc[0] - 1;
+    }
+    if (!active) continue;
     for (int f1 = lo1; f1 <= hi1; ++f1) {
       long long rowbase;
       if (D == 1) rowbase = 0;
@@ -97,21 +104,21 @@ __global__ void __launch_bounds__(256) k_scatter(MvmGeo g, const int* __restrict
         const int fl = (int)(cell[j] - rowbase);
         const int ol = uc[L] - fl;
         // weights of this point at this node from the per-point table
-        const T* wj = wt + (long long)j * (8 * D);
+        const T* wj = wt + (long long)j * (TW * D);
         T c[D + 1];
         if (D == 1) {
           c[0] = wj[ol];
-          c[1] = wj[4 + ol];
+          c[1] = wj[S + ol];
         } else if (D == 2) {
           const int o0 = uc[0] - f0;
-          const T w0 = wj[o0], dw0 = wj[4 + o0], w1 = wj[8 + ol], dw1 = wj[12 + ol];
+          const T w0 = wj[o0], dw0 = wj[S + o0], w1 = wj[TW + ol], dw1 = wj[TW + S + ol];
           c[0] = w0 * w1;
           c[1] = dw0 * w1;
           c[D > 1 ? 2 : 0] = w0 * dw1;
         } else {
           const int o0 = uc[0] - f0, o1 = uc[D > 2 ? 1 : 0] - f1;
-          const T w0 = wj[o0], dw0 = wj[4 + o0], w1 = wj[8 + o1], dw1 = wj[12 + o1];
-          const T w2 = wj[16 + ol], dw2 = wj[20 + ol];
+          const T w0 = wj[o0], dw0 = wj[S + o0], w1 = wj[TW + o1], dw1 = wj[TW + S + o1];
+          const T w2 = wj[2 * TW + ol], dw2 = wj[2 * TW + S + ol];
           const T w01 = w0 * w1;
           c[0] = w01 * w2;
           c[1] = dw0 * w1 * w2;
@@ -132,14 +139,11 @@ __global__ void __launch_bounds__(256) k_scatter(MvmGeo g, const int* __restrict
       }
     }
   }
-  if (SPLIT > 1) {
-    // fixed-order combination: (sub0 + sub1) + (sub2 + sub3)
+  // fixed-order combination over the node's lanes: (sub0 + sub1) + (sub2 + sub3)
 #pragma unroll
-    for (int q = 0; q < CB; ++q) {
-      acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 1);
-      acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 2);
-    }
-  }
+  for (int o = 1; o < SPLIT; o <<= 1)
+#pragma unroll
+    for (int q = 0; q < CB; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
   if (valid && sub == 0) {
 #pragma unroll
     for (int q = 0; q < CB; ++q)
@@ -149,7 +153,8 @@ __global__ void __launch_bounds__(256) k_scatter(MvmGeo g, const int* __restrict
 
 // ------------------------------------------ sum-factorised FP64 scatter ----
 // The weight of point j at node u is a product over dimensions, so the node
-// sum factors: with o_k = u_k - f_k the point's offset in dimension k,
+// sum factors: with o_k = u_k - f_k the point's offset in dimension k
+// (0 <= o_k < S),
 //   d = 2:  w1[o1] A[o0] + dw1[o1] B[o0],
 //           A[o0] = w0[o0] v^0 + dw0[o0] v^1,  B[o0] = w0[o0] v^2;
 //   d = 3:  w2[o2] P[o0][o1] + dw2[o2] Q[o0][o1],
@@ -160,19 +165,19 @@ __global__ void __launch_bounds__(256) k_scatter(MvmGeo g, const int* __restrict
 // GB300 where FP64 arithmetic bounds the scatter.
 // PCG fusion: with z != NULL the pass first replaces v by z + beta_q v (the
 // CG search-direction update) and writes it back, then forms the products.
-template <int D>
+template <int D, int S>
 __global__ void __launch_bounds__(256) k_scatter_prep(const double* __restrict__ wt,
                                                       double* __restrict__ v, int s,
                                                       int n, long long N, double sv, double sg,
                                                       const double* __restrict__ z,
                                                       const double* __restrict__ beta,
                                                       double* __restrict__ ab, CgUpdate up) {
-  constexpr int NC = D == 2 ? 8 : 32;   // coefficients per point and column
+  constexpr int NC = D == 2 ? 2 * S : 2 * S * S;   // coefficients per point and column
   const long long jt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = jt < n;
   double rsum[4] = {0.0, 0.0, 0.0, 0.0};   // ||r||^2 partials (fused CG update, s <= 4)
   const long long j = live ? jt : 0;
-  const double* wj = wt + j * (8 * D);
+  const double* wj = wt + j * (2 * S * D);
 #pragma unroll
   for (int q = 0; q < 4; ++q) {   // s <= 4 on this path
     if (q >= s || !live) break;
@@ -202,20 +207,20 @@ __global__ void __launch_bounds__(256) k_scatter_prep(const double* __restrict__
     double* o = ab + ((long long)q * n + j) * NC;
     if (D == 2) {
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        o[a] = wj[a] * vq[0] + wj[4 + a] * vq[1];
-        o[4 + a] = wj[a] * vq[2];
+      for (int a = 0; a < S; ++a) {
+        o[a] = wj[a] * vq[0] + wj[S + a] * vq[1];
+        o[S + a] = wj[a] * vq[2];
       }
     } else {
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const double t0 = wj[a] * vq[0] + wj[4 + a] * vq[1];
+      for (int a = 0; a < S; ++a) {
+        const double t0 = wj[a] * vq[0] + wj[S + a] * vq[1];
         const double t1 = wj[a] * vq[2];
         const double t2 = wj[a] * vq[D > 2 ? 3 : 0];
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          o[a * 4 + b] = wj[8 + b] * t0 + wj[12 + b] * t1;
-          o[16 + a * 4 + b] = wj[8 + b] * t2;
+        for (int b = 0; b < S; ++b) {
+          o[a * S + b] = wj[2 * S + b] * t0 + wj[3 * S + b] * t1;
+          o[S * S + a * S + b] = wj[2 * S + b] * t2;
         }
       }
     }
@@ -240,17 +245,18 @@ __global__ void __launch_bounds__(256) k_scatter_prep(const double* __restrict__
 }
 
 
-template <int D, int CB>
+template <int D, int CB, int S>
 __global__ void __launch_bounds__(256) k_scatter_ab(MvmGeo g, const int* __restrict__ cell_start,
                                                     const int* __restrict__ cell,
                                                     const double* __restrict__ wt,
                                                     const double* __restrict__ ab,
                                                     double* __restrict__ grid, int s, int n,
                                                     long long M) {
-  constexpr int NC = D == 2 ? 8 : 32;
+  constexpr int NC = D == 2 ? 2 * S : 2 * S * S;
+  constexpr int SPLIT = scatter_split(D, S), PER = S / SPLIT;
   const long long tix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long u = tix / 4;
-  const int sub = (int)(tix % 4);
+  const long long u = tix / SPLIT;
+  const int sub = (int)(tix % SPLIT);
   const bool valid = u < M;
   const int q0 = blockIdx.y * CB;
   int uc[3] = {0, 0, 0};
@@ -265,26 +271,26 @@ __global__ void __launch_bounds__(256) k_scatter_ab(MvmGeo g, const int* __restr
 #pragma unroll
   for (int q = 0; q < CB; ++q) acc[q] = 0.0;
   const int L = D - 1;
-  const int lo_l = max(0, uc[L] - 3), hi_l = min(uc[L], g.mc[L] - 1);
-  const int f0 = uc[0] - 3 + sub;
-  const int o0 = 3 - sub;
-  bool active = valid && lo_l <= hi_l && f0 >= 0 && f0 <= g.mc[0] - 1;
+  const int lo_l = max(0, uc[L] - (S - 1)), hi_l = min(uc[L], g.mc[L] - 1);
   int lo1 = 0, hi1 = 0;
   if (D > 2) {
-    lo1 = max(0, uc[1] - 3);
+    lo1 = max(0, uc[1] - (S - 1));
     hi1 = min(uc[1], g.mc[1] - 1);
   }
-  if (active) {
+  for (int i0 = 0; i0 < PER; ++i0) {
+    const int f0 = uc[0] - (S - 1) + sub * PER + i0;
+    const int o0 = uc[0] - f0;
+    if (!(valid && lo_l <= hi_l && f0 >= 0 && f0 <= g.mc[0] - 1)) continue;
     for (int f1 = lo1; f1 <= hi1; ++f1) {
       const long long rowbase = D == 2 ? (long long)f0 * g.mc[1]
                                        : ((long long)f0 * g.mc[1] + f1) * g.mc[D > 2 ? 2 : 1];
       const int js = cell_start[rowbase + lo_l];
       const int je = cell_start[rowbase + hi_l + 1];
-      const int ci = D == 2 ? o0 : o0 * 4 + (uc[D > 2 ? 1 : 0] - f1);   // coefficient index
+      const int ci = D == 2 ? o0 : o0 * S + (uc[D > 2 ? 1 : 0] - f1);   // coefficient index
       for (int j = js; j < je; ++j) {
         const int ol = uc[L] - (int)(cell[j] - rowbase);
-        const double wl = wt[(long long)j * (8 * D) + 8 * L + ol];
-        const double dl = wt[(long long)j * (8 * D) + 8 * L + 4 + ol];
+        const double wl = wt[(long long)j * (2 * S * D) + 2 * S * L + ol];
+        const double dl = wt[(long long)j * (2 * S * D) + 2 * S * L + S + ol];
 #pragma unroll
         for (int q = 0; q < CB; ++q) {
           if (q0 + q < s) {
@@ -296,10 +302,9 @@ __global__ void __launch_bounds__(256) k_scatter_ab(MvmGeo g, const int* __restr
     }
   }
 #pragma unroll
-  for (int q = 0; q < CB; ++q) {
-    acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 1);
-    acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 2);
-  }
+  for (int o = 1; o < SPLIT; o <<= 1)
+#pragma unroll
+    for (int q = 0; q < CB; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
   if (valid && sub == 0) {
 #pragma unroll
     for (int q = 0; q < CB; ++q)
@@ -319,7 +324,8 @@ __global__ void __launch_bounds__(256) k_scatter_ab(MvmGeo g, const int* __restr
 //      the (up to) 16 cells whose stencil holds the node; consecutive nodes
 //      read consecutive cells of one plane.
 // Each point is read once (the node-owned pull above reads it 16 times);
-// the per-cell planes hold 16 values per cell and column.
+// the per-cell planes hold 16 values per cell and column.  Cubic (4-node)
+// stencils only; the quintic stencil takes the node-owned pull.
 // Optional, as in k_scatter_prep: v0 scaled by sv, v1, v2 by sg; with z,
 // p = z + beta p is formed first and written back (fused PCG direction).
 template <class T, int CB, int G>
@@ -433,9 +439,9 @@ void launch_scatter_cells(dski_handle h, T* v, T* S, int s, T sv, T sg, const do
 // -------------------------------------------------------------- gather ----
 // out_j^0 = av sum_u w_j(u) h(u) + nv v_j^0,
 // out_j^p = ag sum_u dw_{j,p}(u) h(u) + ng v_j^p,
-// evaluated dimension by dimension over the 4^d stencil (av = ag = 1 and
+// evaluated dimension by dimension over the S^d stencil (av = ag = 1 and
 // nv, ng the noise for the MVM; other values for the preconditioner).
-template <class T, int D, int CB>
+template <class T, int D, int CB, int S>
 __global__ void __launch_bounds__(256) k_gather(MvmGeo g, const int* __restrict__ cell,
                                                 const T* __restrict__ wt,
                                                 const T* __restrict__ grid,
@@ -457,15 +463,15 @@ __global__ void __launch_bounds__(256) k_gather(MvmGeo g, const int* __restrict_
       t /= g.mc[k];
     }
   }
-  T w[D][4], dw[D][4];
+  T w[D][S], dw[D][S];
   {
-    const T* wj = wt + (long long)j * (8 * D);
+    const T* wj = wt + (long long)j * (2 * S * D);
 #pragma unroll
     for (int k = 0; k < D; ++k)
 #pragma unroll
-      for (int o = 0; o < 4; ++o) {
-        w[k][o] = wj[8 * k + o];
-        dw[k][o] = wj[8 * k + 4 + o];
+      for (int o = 0; o < S; ++o) {
+        w[k][o] = wj[2 * S * k + o];
+        dw[k][o] = wj[2 * S * k + S + o];
       }
   }
   long long base = 0;
@@ -481,7 +487,7 @@ __global__ void __launch_bounds__(256) k_gather(MvmGeo g, const int* __restrict_
     for (int cc = 0; cc <= D; ++cc) r[cc] = T(0);
     if (D == 1) {
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
+      for (int a = 0; a < S; ++a) {
         const T x = hq[a];
         r[0] += w[0][a] * x;
         r[1] += dw[0][a] * x;
@@ -489,10 +495,10 @@ __global__ void __launch_bounds__(256) k_gather(MvmGeo g, const int* __restrict_
     } else if (D == 2) {
       const int s1 = g.m[D > 1 ? 1 : 0];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
+      for (int a = 0; a < S; ++a) {
         T rw = T(0), rd = T(0);
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
+        for (int b = 0; b < S; ++b) {
           const T x = hq[(long long)a * s1 + b];
           rw += w[D > 1 ? 1 : 0][b] * x;
           rd += dw[D > 1 ? 1 : 0][b] * x;
@@ -505,13 +511,13 @@ __global__ void __launch_bounds__(256) k_gather(MvmGeo g, const int* __restrict_
       const long long s1 = (long long)g.m[1] * g.m[2];
       const int s2 = g.m[2];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
+      for (int a = 0; a < S; ++a) {
         T aw = T(0), ad1 = T(0), ad2 = T(0);
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
+        for (int b = 0; b < S; ++b) {
           T lw = T(0), ld = T(0);
 #pragma unroll
-          for (int c2 = 0; c2 < 4; ++c2) {
+          for (int c2 = 0; c2 < S; ++c2) {
             const T x = hq[a * s1 + (long long)b * s2 + c2];
             lw += w[D > 2 ? 2 : 0][c2] * x;
             ld += dw[D > 2 ? 2 : 0][c2] * x;
@@ -644,14 +650,14 @@ __global__ void k_perm_out(const int* __restrict__ perm, const T* __restrict__ v
       vu[q * N + (long long)c * n + i] = vi[q * N + (long long)j * (d + 1) + c];
 }
 
-template <class T, int D, int CB>
+template <class T, int D, int CB, int S>
 void launch_scatter(dski_handle h, const MvmGeo& g, const T* wt, const T* v, T* grid, int s,
                     cudaStream_t st) {
-  const long long threads = (long long)h->M * (D > 1 ? 4 : 1);
+  const long long threads = (long long)h->M * scatter_split(D, S);
   dim3 grd((unsigned)((threads + 255) / 256), (unsigned)((s + CB - 1) / CB));
   StageScope sc(h, ST_SCATTER, st);
-  k_scatter<T, D, CB><<<grd, 256, 0, st>>>(g, h->cell_start.as<int>(), h->cell.as<int>(), wt,
-                                           v, grid, s, (long long)h->N, (long long)h->M);
+  k_scatter<T, D, CB, S><<<grd, 256, 0, st>>>(g, h->cell_start.as<int>(), h->cell.as<int>(), wt,
+                                              v, grid, s, (long long)h->N, (long long)h->M);
 }
 
 struct GatherScale {
@@ -661,12 +667,12 @@ struct GatherScale {
   double* dpart = nullptr;     // per-block partial sums of v^T out (FP64 only)
 };
 
-template <class T, int D, int CB>
+template <class T, int D, int CB, int S>
 void launch_gather(dski_handle h, const MvmGeo& g, const T* wt, const T* grid, const T* v,
                    T* out, int s, cudaStream_t st, const GatherScale& gs) {
   dim3 grd((unsigned)((h->n + 255) / 256), (unsigned)((s + CB - 1) / CB));
   StageScope sc(h, gs.stage, st);
-  k_gather<T, D, CB><<<grd, 256, 0, st>>>(g, h->cell.as<int>(), wt, grid, v, out, s, h->n,
+  k_gather<T, D, CB, S><<<grd, 256, 0, st>>>(g, h->cell.as<int>(), wt, grid, v, out, s, h->n,
                                           (long long)h->N, (long long)h->M, (T)gs.nv, (T)gs.ng,
                                           (T)gs.av, (T)gs.ag, gs.dpart);
 }
@@ -674,9 +680,12 @@ void launch_gather(dski_handle h, const MvmGeo& g, const T* wt, const T* grid, c
 template <class T, int D>
 void scatter_dispatch(dski_handle h, const MvmGeo& g, const T* wt, const T* v, T* grid, int s,
                       cudaStream_t st) {
-  if (s == 1) launch_scatter<T, D, 1>(h, g, wt, v, grid, s, st);
-  else if (s <= 4) launch_scatter<T, D, 4>(h, g, wt, v, grid, s, st);
-  else launch_scatter<T, D, 8>(h, g, wt, v, grid, s, st);
+  with_stencil(h, [&](auto Sc) {
+    constexpr int S = decltype(Sc)::value;
+    if (s == 1) launch_scatter<T, D, 1, S>(h, g, wt, v, grid, s, st);
+    else if (s <= 4) launch_scatter<T, D, 4, S>(h, g, wt, v, grid, s, st);
+    else launch_scatter<T, D, 8, S>(h, g, wt, v, grid, s, st);
+  });
 }
 
 template <class T, int D>
@@ -689,9 +698,12 @@ void gather_dispatch(dski_handle h, const MvmGeo& g, const T* wt, const T* grid,
     gs.nv = h->nv;
     gs.ng = h->ng;
   }
-  if (s == 1) launch_gather<T, D, 1>(h, g, wt, grid, v, out, s, st, gs);
-  else if (s <= 4) launch_gather<T, D, 4>(h, g, wt, grid, v, out, s, st, gs);
-  else launch_gather<T, D, 8>(h, g, wt, grid, v, out, s, st, gs);
+  with_stencil(h, [&](auto Sc) {
+    constexpr int S = decltype(Sc)::value;
+    if (s == 1) launch_gather<T, D, 1, S>(h, g, wt, grid, v, out, s, st, gs);
+    else if (s <= 4) launch_gather<T, D, 4, S>(h, g, wt, grid, v, out, s, st, gs);
+    else launch_gather<T, D, 8, S>(h, g, wt, grid, v, out, s, st, gs);
+  });
 }
 
 template <class T>
@@ -784,10 +796,14 @@ void mode_simt(dski_handle h, const T* X, const T* K, T* Y, int m, long long R, 
 
 void set_no_tune(bool on) { g_no_tune = on; }
 
+// the FP32 d = 2 scatter takes the per-cell passes for cubic stencils
+static bool cells_path(dski_handle h, bool prec64) { return h->d == 2 && !prec64 && h->sw == 4; }
+
 size_t scatter_ws_bytes(dski_handle h, int s, bool prec64) {
-  if (h->d == 2 && !prec64) return (size_t)s * 16 * h->mc[0] * h->mc[1] * 4;
+  if (cells_path(h, prec64)) return (size_t)s * 16 * h->mc[0] * h->mc[1] * 4;
   if (!(prec64 && h->d >= 2 && s <= 4)) return 0;
-  return (size_t)s * h->n * (h->d == 2 ? 8 : 32) * 8;
+  const size_t S = (size_t)h->sw;
+  return (size_t)s * h->n * (h->d == 2 ? 2 * S : 2 * S * S) * 8;
 }
 
 namespace {
@@ -833,7 +849,7 @@ int scatter_fused(dski_handle h, const void* vin, void* g, int s, bool prec64, v
   // warp instructions per point against ~1.4 there.
   if (up && !(prec64 && h->d >= 2 && s <= 4))
     return set_error(DSKI_ERR_ARG, "fused CG update needs FP64, d >= 2 and s <= 4");
-  if (h->d == 2 && !prec64) {
+  if (cells_path(h, prec64)) {
     if (z || sv != 1.0 || sg != 1.0)
       return set_error(DSKI_ERR_ARG, "scaled / fused scatter needs FP64 vectors");
     void* S = ws;
@@ -861,25 +877,34 @@ int scatter_fused(dski_handle h, const void* vin, void* g, int s, bool prec64, v
     }
     const double* wt = h->W64.as<double>();
     const dim3 gp((unsigned)((h->n + 255) / 256));
-    const dim3 gs((unsigned)((h->M * 4 + 255) / 256), 1);
     StageScope sc(h, ST_SCATTER, st, 2);
-    if (h->d == 2) {
-      k_scatter_prep<2><<<gp, 256, 0, st>>>(wt, (double*)vin, s, h->n, h->N, sv, sg, z, beta, ab, upd);
-      if (s == 1)
-        k_scatter_ab<2, 1><<<gs, 256, 0, st>>>(geo, h->cell_start.as<int>(), h->cell.as<int>(),
-                                               wt, ab, (double*)g, s, h->n, h->M);
-      else
-        k_scatter_ab<2, 4><<<gs, 256, 0, st>>>(geo, h->cell_start.as<int>(), h->cell.as<int>(),
-                                               wt, ab, (double*)g, s, h->n, h->M);
-    } else {
-      k_scatter_prep<3><<<gp, 256, 0, st>>>(wt, (double*)vin, s, h->n, h->N, sv, sg, z, beta, ab, upd);
-      if (s == 1)
-        k_scatter_ab<3, 1><<<gs, 256, 0, st>>>(geo, h->cell_start.as<int>(), h->cell.as<int>(),
-                                               wt, ab, (double*)g, s, h->n, h->M);
-      else
-        k_scatter_ab<3, 4><<<gs, 256, 0, st>>>(geo, h->cell_start.as<int>(), h->cell.as<int>(),
-                                               wt, ab, (double*)g, s, h->n, h->M);
-    }
+    with_stencil(h, [&](auto Sc) {
+      constexpr int S = decltype(Sc)::value;
+      const dim3 gs((unsigned)((h->M * scatter_split(2, S) + 255) / 256), 1);
+      if (h->d == 2) {
+        k_scatter_prep<2, S><<<gp, 256, 0, st>>>(wt, (double*)vin, s, h->n, h->N, sv, sg, z,
+                                                 beta, ab, upd);
+        if (s == 1)
+          k_scatter_ab<2, 1, S><<<gs, 256, 0, st>>>(geo, h->cell_start.as<int>(),
+                                                    h->cell.as<int>(), wt, ab, (double*)g, s,
+                                                    h->n, h->M);
+        else
+          k_scatter_ab<2, 4, S><<<gs, 256, 0, st>>>(geo, h->cell_start.as<int>(),
+                                                    h->cell.as<int>(), wt, ab, (double*)g, s,
+                                                    h->n, h->M);
+      } else {
+        k_scatter_prep<3, S><<<gp, 256, 0, st>>>(wt, (double*)vin, s, h->n, h->N, sv, sg, z,
+                                                 beta, ab, upd);
+        if (s == 1)
+          k_scatter_ab<3, 1, S><<<gs, 256, 0, st>>>(geo, h->cell_start.as<int>(),
+                                                    h->cell.as<int>(), wt, ab, (double*)g, s,
+                                                    h->n, h->M);
+        else
+          k_scatter_ab<3, 4, S><<<gs, 256, 0, st>>>(geo, h->cell_start.as<int>(),
+                                                    h->cell.as<int>(), wt, ab, (double*)g, s,
+                                                    h->n, h->M);
+      }
+    });
     DSKI_LAUNCHED();
     return DSKI_OK;
   }
@@ -890,14 +915,13 @@ int scatter_fused(dski_handle h, const void* vin, void* g, int s, bool prec64, v
     switch (h->d) {
       case 1: scatter_dispatch<double, 1>(h, geo, fr, (const double*)vin, (double*)g, s, st); break;
       case 2: scatter_dispatch<double, 2>(h, geo, fr, (const double*)vin, (double*)g, s, st); break;
-
       default: scatter_dispatch<double, 3>(h, geo, fr, (const double*)vin, (double*)g, s, st); break;
     }
   } else {
     const float* fr = h->W32.as<float>();
     switch (h->d) {
       case 1: scatter_dispatch<float, 1>(h, geo, fr, (const float*)vin, (float*)g, s, st); break;
-
+      case 2: scatter_dispatch<float, 2>(h, geo, fr, (const float*)vin, (float*)g, s, st); break;
       default: scatter_dispatch<float, 3>(h, geo, fr, (const float*)vin, (float*)g, s, st); break;
     }
   }
@@ -919,8 +943,13 @@ int kron_internal(dski_handle h, void* g, void* tmp, int s, bool prec64, int dfa
     const double scale = last ? h->sf * h->sf : 1.0;
     // FP64_TC: the tensor-core product from m_k = 64 on; below, its fixed
     // per-CTA latency (~10 us) exceeds the FP64 product (~8 us at m_k = 24)
-    if (prec64 && h->prec == DSKI_FP64_TC && dfactor < 0 && !h->kron_exact &&
-        h->m[k] >= kOzMinM) {
+    if (prec64 && h->kuu_fft && dfactor < 0 && !h->kron_exact) {
+      // Toeplitz factor by circulant embedding and FFT (all FP64); the PCG's
+      // true residuals take the dense factors (kron_exact), so its restarts
+      // refine x against the dense operator
+      DSKI_TRY(mode_fft(h, k, (const double*)cur, (double*)nxt, R, s, scale));
+    } else if (prec64 && h->prec == DSKI_FP64_TC && dfactor < 0 && !h->kron_exact &&
+               h->m[k] >= kOzMinM) {
       DSKI_TRY(mode_tc_oz(h, (const double*)cur, h->Kdig[k].as<uint16_t>(), h->Kexp[k].as<int>(),
                           (double*)nxt, h->m[k], R, s, scale));
     } else if (prec64) {

@@ -494,8 +494,8 @@ int cg_run(dski_handle h, CgRun& run) {
     return DSKI_OK;
   };
   auto true_residual = [&](int first) -> int {
-    // FP64_TC: the true residual takes the FP64-unit mode products, so the
-    // restarts refine x against the FP64 operator
+    // FP64_TC and FFT products: the true residual takes the dense FP64-unit
+    // mode products, so the restarts refine x against that operator
     h->kron_exact = true;
     const int mrc = mvm_internal(h, run.X, Q, s, true);
     h->kron_exact = false;
@@ -610,7 +610,7 @@ int cg_run(dski_handle h, CgRun& run) {
       }
     }
     ++chunks_run;
-    if (gexec) {
+    if (gexec && chunk == 16) {   // the graph holds exactly one full chunk
       if (cudaGraphLaunch(gexec, st) != cudaSuccess)
         return set_error(DSKI_ERR_CUDA, "dski_pcg_solve: graph launch: %s",
                          cudaGetErrorString(cudaGetLastError()));

@@ -3,14 +3,15 @@
 //
 // The D-SKI matrix is K = B K_UU B^T with K_UU = s_f^2 K_1 (x) ... (x) K_d.
 // Because K_UU is a Kronecker product and every row of B is a tensor product
-// of per-dimension 4-point stencils, entries of K factor over dimensions:
+// of per-dimension S-point stencils (S = 4 cubic, 6 quintic), entries of K
+// factor over dimensions:
 //   K[(i,c), (j,c')] = s_f^2 prod_k  a_ik^(c)T  K_k[S_ik, S_jk]  a_jk^(c'),
-// where S_ik are the four stencil nodes of point i in dimension k and
-// a_ik^(c) its Keys weights (derivative weights / h_k in dimension c-1 when
+// where S_ik are the S stencil nodes of point i in dimension k and a_ik^(c)
+// its interpolation weights (derivative weights / h_k in dimension c-1 when
 // c >= 1).  On a regular grid K_k is Toeplitz, K_k[u, v] = kappa_k(|u - v|),
-// so the diagonal needs only the 4 x 4 block kappa_k(|o - o'|) and a pivot
+// so the diagonal needs only the S x S block kappa_k(|o - o'|) and a pivot
 // row needs only kappa_k at the offsets between two stencils: the method of
-// Sec. 3.3 ("only the diagonal and the rows of the pivots") at O(d 16) per
+// Sec. 3.3 (only the diagonal and the pivot rows are formed) at O(d S^2) per
 // entry, without forming the grid.
 //
 // Greedy pivoting: the pivot is the largest residual diagonal entry; ties go
@@ -24,7 +25,7 @@
 #include <cmath>
 #include <new>
 
-#include "keys.cuh"
+#include "interp.cuh"
 #include "solve_internal.cuh"
 
 namespace dski {
@@ -110,18 +111,18 @@ __device__ void finish_pivot(int nblocks, const ArgMax* part_a, const double* pa
   if (!(b.v > 0.0) || !(tr > 1e-14 * st->trace0)) st->stop = 1;
 }
 
-template <int D>
+template <int D, int S>
 __device__ __forceinline__ void point_weights(const PcGeo& g, const double* frac, long long j,
-                                              double w[D][4], double dw[D][4]) {
+                                              double w[D][S], double dw[D][S]) {
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    keys4<double>(frac[j * D + k], w[k], dw[k]);
+    stencil_weights<S, double>(frac[j * D + k], w[k], dw[k]);
 #pragma unroll
-    for (int o = 0; o < 4; ++o) dw[k][o] *= g.invh[k];
+    for (int o = 0; o < S; ++o) dw[k][o] *= g.invh[k];
   }
 }
 
-template <int D>
+template <int D, int S>
 __global__ void __launch_bounds__(256) k_pc_diag(PcGeo g, const int* __restrict__ cell,
                                                  const double* __restrict__ frac,
                                                  const int* __restrict__ perm,
@@ -134,16 +135,16 @@ __global__ void __launch_bounds__(256) k_pc_diag(PcGeo g, const int* __restrict_
   ArgMax best{-1.0, 0x7fffffffffffffffLL, 0};
   double tr = 0.0;
   if (j < g.n) {
-    double w[D][4], dw[D][4];
-    point_weights<D>(g, frac, j, w, dw);
+    double w[D][S], dw[D][S];
+    point_weights<D, S>(g, frac, j, w, dw);
     double qw[D], qd[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       double a = 0.0, b = 0.0;
 #pragma unroll
-      for (int o = 0; o < 4; ++o)
+      for (int o = 0; o < S; ++o)
 #pragma unroll
-        for (int o2 = 0; o2 < 4; ++o2) {
+        for (int o2 = 0; o2 < S; ++o2) {
           const double kv = g.kap[k][o > o2 ? o - o2 : o2 - o];
           a += w[k][o] * kv * w[k][o2];
           b += dw[k][o] * kv * dw[k][o2];
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(256) k_pc_diag(PcGeo g, const int* __restrict_
   if (last_block(ticket, gridDim.x)) finish_pivot(gridDim.x, part_a, part_s, st, 0, nullptr, 1, 0);
 }
 
-template <int D>
+template <int D, int S>
 __global__ void __launch_bounds__(256) k_pc_step(PcGeo g, const int* __restrict__ cell,
                                                  const double* __restrict__ frac,
                                                  const int* __restrict__ perm,
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(256) k_pc_step(PcGeo g, const int* __restrict_
   __shared__ ArgMax sh[256];
   __shared__ double shs[256];
   __shared__ double Lp[128];
-  __shared__ double ap[D][4];
+  __shared__ double ap[D][S];
   __shared__ int fp[D];
   if (st->stop) return;   // uniform across the grid: written by an earlier launch
   const long long ep = st->pivot;
@@ -190,13 +191,13 @@ __global__ void __launch_bounds__(256) k_pc_step(PcGeo g, const int* __restrict_
   if (threadIdx.x == 0) {
     int f[DSKI_MAXD];
     cell_coords(g, cell[jp], f);
-    double w[D][4], dw[D][4];
-    point_weights<D>(g, frac, jp, w, dw);
+    double w[D][S], dw[D][S];
+    point_weights<D, S>(g, frac, jp, w, dw);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       fp[k] = f[k];
 #pragma unroll
-      for (int o = 0; o < 4; ++o) ap[k][o] = (cp == k + 1) ? dw[k][o] : w[k][o];
+      for (int o = 0; o < S; ++o) ap[k][o] = (cp == k + 1) ? dw[k][o] : w[k][o];
     }
   }
   __syncthreads();
@@ -207,17 +208,17 @@ __global__ void __launch_bounds__(256) k_pc_step(PcGeo g, const int* __restrict_
   if (j < g.n) {
     int f[DSKI_MAXD];
     cell_coords(g, cell[j], f);
-    double w[D][4], dw[D][4];
-    point_weights<D>(g, frac, j, w, dw);
+    double w[D][S], dw[D][S];
+    point_weights<D, S>(g, frac, j, w, dw);
     double Wk[D], Dk[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       double a = 0.0, b = 0.0;
 #pragma unroll
-      for (int o = 0; o < 4; ++o) {
+      for (int o = 0; o < S; ++o) {
         double hk = 0.0;
 #pragma unroll
-        for (int o2 = 0; o2 < 4; ++o2) {
+        for (int o2 = 0; o2 < S; ++o2) {
           const int delta = abs(f[k] + o - fp[k] - o2);
           hk += g.kap[k][delta] * ap[k][o2];
         }
@@ -324,6 +325,20 @@ __global__ void k_inv_sqrt_noise(int n, int d, double nv, double ng, double* __r
   const double v = (e % (d + 1)) == 0 ? nv : ng;
   dis[e] = 1.0 / sqrt(v);
   ds[e] = sqrt(v);
+}
+
+// the diagonal, then `rank` pivot steps (each stops itself once the
+// factorisation has stopped)
+template <int D, int S>
+void launch_pc(dski_handle h, const PcGeo& g, unsigned nb, int rank, double* Dg, double* L,
+               ArgMax* part_a, double* part_s, unsigned* tk, PcState* stt, int* piv_list,
+               cudaStream_t st) {
+  k_pc_diag<D, S><<<nb, 256, 0, st>>>(g, h->cell.as<int>(), h->frac64.as<double>(),
+                                      h->perm.as<int>(), Dg, part_a, part_s, tk, stt);
+  for (int k = 0; k < rank; ++k)
+    k_pc_step<D, S><<<nb, 256, 0, st>>>(g, h->cell.as<int>(), h->frac64.as<double>(),
+                                        h->perm.as<int>(), Dg, L, k, part_a, part_s, tk, stt,
+                                        piv_list);
 }
 
 PcGeo make_pcgeo(dski_handle h) {
@@ -484,38 +499,14 @@ extern "C" int pivchol_build(dski_handle h, int rank, pivchol_handle* out, int* 
     const PcGeo g = make_pcgeo(h);
     {
       StageScope sc(h, ST_PIVCHOL, st, 1 + rank);
-      switch (h->d) {
-        case 1:
-          k_pc_diag<1><<<nb, 256, 0, st>>>(g, h->cell.as<int>(), h->frac64.as<double>(),
-                                           h->perm.as<int>(), Dg.as<double>(), part_a, part_s,
-                                           tk, stt);
-          for (int k = 0; k < rank; ++k)
-            k_pc_step<1><<<nb, 256, 0, st>>>(g, h->cell.as<int>(), h->frac64.as<double>(),
-                                             h->perm.as<int>(), Dg.as<double>(),
-                                             pc->L.as<double>(), k, part_a, part_s, tk, stt,
-                                             piv_list);
-          break;
-        case 2:
-          k_pc_diag<2><<<nb, 256, 0, st>>>(g, h->cell.as<int>(), h->frac64.as<double>(),
-                                           h->perm.as<int>(), Dg.as<double>(), part_a, part_s,
-                                           tk, stt);
-          for (int k = 0; k < rank; ++k)
-            k_pc_step<2><<<nb, 256, 0, st>>>(g, h->cell.as<int>(), h->frac64.as<double>(),
-                                             h->perm.as<int>(), Dg.as<double>(),
-                                             pc->L.as<double>(), k, part_a, part_s, tk, stt,
-                                             piv_list);
-          break;
-        default:
-          k_pc_diag<3><<<nb, 256, 0, st>>>(g, h->cell.as<int>(), h->frac64.as<double>(),
-                                           h->perm.as<int>(), Dg.as<double>(), part_a, part_s,
-                                           tk, stt);
-          for (int k = 0; k < rank; ++k)
-            k_pc_step<3><<<nb, 256, 0, st>>>(g, h->cell.as<int>(), h->frac64.as<double>(),
-                                             h->perm.as<int>(), Dg.as<double>(),
-                                             pc->L.as<double>(), k, part_a, part_s, tk, stt,
-                                             piv_list);
-          break;
-      }
+      with_stencil(h, [&](auto Sc) {
+        constexpr int S = decltype(Sc)::value;
+        switch (h->d) {
+          case 1: launch_pc<1, S>(h, g, nb, rank, Dg.as<double>(), pc->L.as<double>(), part_a, part_s, tk, stt, piv_list, st); break;
+          case 2: launch_pc<2, S>(h, g, nb, rank, Dg.as<double>(), pc->L.as<double>(), part_a, part_s, tk, stt, piv_list, st); break;
+          default: launch_pc<3, S>(h, g, nb, rank, Dg.as<double>(), pc->L.as<double>(), part_a, part_s, tk, stt, piv_list, st); break;
+        }
+      });
     }
     if (cudaGetLastError() != cudaSuccess) { rc = set_error(DSKI_ERR_CUDA, "pivchol_build: launch failed"); break; }
     {

@@ -29,7 +29,7 @@ __global__ void k_pivot_factors(const int* __restrict__ piv, const int* __restri
                                 const double* __restrict__ wt, int d, int mc0, int mc1, int mc2,
                                 const double* __restrict__ K0, const double* __restrict__ K1,
                                 const double* __restrict__ K2, int m0, int m1, int m2,
-                                double sf2, int r, double* __restrict__ Hf) {
+                                double sf2, int r, int S, double* __restrict__ Hf) {
   const int k = blockIdx.x, dim = blockIdx.y;
   const int e = piv[k];
   const int j = e / (d + 1), c = e % (d + 1);
@@ -44,7 +44,9 @@ __global__ void k_pivot_factors(const int* __restrict__ piv, const int* __restri
   }
   const int m = dim == 0 ? m0 : (dim == 1 ? m1 : m2);
   const double* K = dim == 0 ? K0 : (dim == 1 ? K1 : K2);
-  const double* a = wt + (long long)j * 8 * d + 8 * dim + (c == dim + 1 ? 4 : 0);
+  // the point's S weights in this dimension (derivative weights for its
+  // gradient row), from the per-point table of 2 S values per dimension
+  const double* a = wt + (long long)j * 2 * S * d + 2 * S * dim + (c == dim + 1 ? S : 0);
   // offset of this dimension's block inside Hf: sum of r * m over earlier dims
   long long off = 0;
   if (dim >= 1) off += (long long)r * m0;
@@ -52,8 +54,7 @@ __global__ void k_pivot_factors(const int* __restrict__ piv, const int* __restri
   const double sc = dim == 0 ? sf2 : 1.0;
   for (int u = threadIdx.x; u < m; u += blockDim.x) {
     double v = 0.0;
-#pragma unroll
-    for (int o = 0; o < 4; ++o) v += K[(long long)u * m + f[dim] + o] * a[o];
+    for (int o = 0; o < S; ++o) v += K[(long long)u * m + f[dim] + o] * a[o];
     Hf[off + (long long)k * m + u] = sc * v;
   }
 }
@@ -222,7 +223,7 @@ int grid_precond_build(dski_handle h, pivchol_handle pc, const int* piv_dev, con
     k_pivot_factors<<<dim3(r, 2), 256, 0, st>>>(
         piv_dev, h->cell.as<int>(), h->W64.as<double>(), 2, h->mc[0], h->mc[1], 1,
         h->K64[0].as<double>(), h->K64[1].as<double>(), nullptr, m0, m1, 1, h->sf * h->sf, r,
-        pc->Hf.as<double>());
+        h->sw, pc->Hf.as<double>());
     k_transpose<<<(r * m1 + 255) / 256, 256, 0, st>>>(pc->Hf.as<double>() + (size_t)r * m0, r, m1,
                                                       pc->H1T.as<double>());
     k_gather_lp<<<(r * r + 255) / 256, 256, 0, st>>>(pc->L.as<double>(), h->N, piv_dev, r,

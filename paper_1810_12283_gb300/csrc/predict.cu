@@ -13,7 +13,7 @@
 #include <algorithm>
 
 #include "solve_internal.cuh"
-#include "keys.cuh"
+#include "interp.cuh"
 
 namespace dski {
 namespace {
@@ -25,28 +25,29 @@ struct PredGeo {
   double lo[DSKI_MAXD], h[DSKI_MAXD];
 };
 
-// Stencil of a test point: first node (c - 1) per dimension, weights and
-// derivative weights (already divided by h), as for the training points.
-template <int D>
+// Stencil of a test point: first node (c - S/2 + 1) per dimension, weights
+// and derivative weights (already divided by h), as for the training points.
+template <int D, int S>
 __device__ __forceinline__ bool pred_stencil(const double* x, const PredGeo& g, int first[D],
-                                             double w[D][4], double dw[D][4]) {
+                                             double w[D][S], double dw[D][S]) {
+  constexpr int lead = S / 2 - 1;
   bool ok = true;
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     const double t = (x[k] - g.lo[k]) / g.h[k];
     const double c = floor(t);
-    if (!(c >= 1.0 && c <= (double)(g.m[k] - 3))) {   // NaN fails too
+    if (!(c >= (double)lead && c <= (double)(g.m[k] - S + lead))) {   // NaN fails too
       ok = false;
       first[k] = 0;
-      for (int o = 0; o < 4; ++o) w[k][o] = dw[k][o] = 0.0;
+      for (int o = 0; o < S; ++o) w[k][o] = dw[k][o] = 0.0;
       continue;
     }
-    first[k] = (int)c - 1;
-    double ww[4], dd[4];
-    keys4<double>(t - c, ww, dd);
+    first[k] = (int)c - lead;
+    double ww[S], dd[S];
+    stencil_weights<S, double>(t - c, ww, dd);
     const double ih = 1.0 / g.h[k];
 #pragma unroll
-    for (int o = 0; o < 4; ++o) {
+    for (int o = 0; o < S; ++o) {
       w[k][o] = ww[o];
       dw[k][o] = dd[o] * ih;
     }
@@ -55,26 +56,26 @@ __device__ __forceinline__ bool pred_stencil(const double* x, const PredGeo& g, 
 }
 
 // out (block order) = [W*; dW*] h at n* test points: one thread per point.
-template <int D>
+template <int D, int S>
 __global__ void k_pred_gather(const double* __restrict__ Xs, int ns, PredGeo g,
                               const double* __restrict__ hgrid, int with_grad,
                               double* __restrict__ out, int* __restrict__ bad) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ns) return;
   int first[D];
-  double w[D][4], dw[D][4];
-  if (!pred_stencil<D>(Xs + (long long)i * D, g, first, w, dw)) atomicAdd(bad, 1);
+  double w[D][S], dw[D][S];
+  if (!pred_stencil<D, S>(Xs + (long long)i * D, g, first, w, dw)) atomicAdd(bad, 1);
   double val = 0.0, grad[D];
 #pragma unroll
   for (int p = 0; p < D; ++p) grad[p] = 0.0;
-  constexpr int NS = D == 1 ? 4 : (D == 2 ? 16 : 64);
+  constexpr int NS = D == 1 ? S : (D == 2 ? S * S : S * S * S);
   for (int t = 0; t < NS; ++t) {
     int o[D];
     int r = t;
 #pragma unroll
     for (int k = D - 1; k >= 0; --k) {
-      o[k] = r & 3;
-      r >>= 2;
+      o[k] = r % S;
+      r /= S;
     }
     long long idx = 0;
     double wp = 1.0;
@@ -102,22 +103,22 @@ __global__ void k_pred_gather(const double* __restrict__ Xs, int ns, PredGeo g,
 }
 
 // Column c of G (M x s, zeroed) = value weights of test point i0 + c.
-template <int D>
+template <int D, int S>
 __global__ void k_pred_scatter(const double* __restrict__ Xs, int i0, int s, PredGeo g,
                                long long M, double* __restrict__ G, int* __restrict__ bad) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= s) return;
   int first[D];
-  double w[D][4], dw[D][4];
-  if (!pred_stencil<D>(Xs + (long long)(i0 + c) * D, g, first, w, dw)) atomicAdd(bad, 1);
-  constexpr int NS = D == 1 ? 4 : (D == 2 ? 16 : 64);
+  double w[D][S], dw[D][S];
+  if (!pred_stencil<D, S>(Xs + (long long)(i0 + c) * D, g, first, w, dw)) atomicAdd(bad, 1);
+  constexpr int NS = D == 1 ? S : (D == 2 ? S * S : S * S * S);
   for (int t = 0; t < NS; ++t) {
     int o[D];
     int r = t;
 #pragma unroll
     for (int k = D - 1; k >= 0; --k) {
-      o[k] = r & 3;
-      r >>= 2;
+      o[k] = r % S;
+      r /= S;
     }
     long long idx = 0;
     double wp = 1.0;
@@ -153,7 +154,7 @@ __device__ __forceinline__ double test_probe(unsigned long long seed, long long 
 
 // G[j][:] (M x P, zeroed) = sum_i z_ij w*_i: thread (test point, probe),
 // FP64 atomics where test points share grid nodes.
-template <int D>
+template <int D, int S>
 __global__ void k_pred_scatter_z(const double* __restrict__ Xs, int ns, int P,
                                  unsigned long long seed, PredGeo g, long long M,
                                  double* __restrict__ G, int* __restrict__ bad) {
@@ -161,20 +162,20 @@ __global__ void k_pred_scatter_z(const double* __restrict__ Xs, int ns, int P,
   if (t >= (long long)ns * P) return;
   const int i = (int)(t % ns), j = (int)(t / ns);
   int first[D];
-  double w[D][4], dw[D][4];
-  if (!pred_stencil<D>(Xs + (long long)i * D, g, first, w, dw)) {
+  double w[D][S], dw[D][S];
+  if (!pred_stencil<D, S>(Xs + (long long)i * D, g, first, w, dw)) {
     if (j == 0) atomicAdd(bad, 1);
     return;
   }
   const double z = test_probe(seed, ns, j, i);
-  constexpr int NS = D == 1 ? 4 : (D == 2 ? 16 : 64);
+  constexpr int NS = D == 1 ? S : (D == 2 ? S * S : S * S * S);
   for (int s4 = 0; s4 < NS; ++s4) {
     int o[D];
     int r = s4;
 #pragma unroll
     for (int k = D - 1; k >= 0; --k) {
-      o[k] = r & 3;
-      r >>= 2;
+      o[k] = r % S;
+      r /= S;
     }
     long long idx = 0;
     double wp = z;
@@ -188,16 +189,16 @@ __global__ void k_pred_scatter_z(const double* __restrict__ Xs, int ns, int P,
 }
 
 // var[i] -= (1/P) sum_j z_ij (w*_i . H[j]): one thread per test point.
-template <int D>
+template <int D, int S>
 __global__ void k_pred_cv(const double* __restrict__ Xs, int ns, int P, unsigned long long seed,
                           PredGeo g, long long M, const double* __restrict__ H,
                           double* __restrict__ var) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ns) return;
   int first[D];
-  double w[D][4], dw[D][4];
-  if (!pred_stencil<D>(Xs + (long long)i * D, g, first, w, dw)) return;
-  constexpr int NS = D == 1 ? 4 : (D == 2 ? 16 : 64);
+  double w[D][S], dw[D][S];
+  if (!pred_stencil<D, S>(Xs + (long long)i * D, g, first, w, dw)) return;
+  constexpr int NS = D == 1 ? S : (D == 2 ? S * S : S * S * S);
   double acc = 0.0;
   for (int j = 0; j < P; ++j) {
     const double* hj = H + (long long)j * M;
@@ -207,8 +208,8 @@ __global__ void k_pred_cv(const double* __restrict__ Xs, int ns, int P, unsigned
       int r = s4;
 #pragma unroll
       for (int k = D - 1; k >= 0; --k) {
-        o[k] = r & 3;
-        r >>= 2;
+        o[k] = r % S;
+        r /= S;
       }
       long long idx = 0;
       double wp = 1.0;
@@ -277,11 +278,14 @@ extern "C" int dski_predict(dski_handle h, pivchol_handle pc, const double* alph
     {
       StageScope sc(h, ST_GATHER, st);
       const unsigned nb = (unsigned)((n_star + 127) / 128);
-      switch (d) {
-        case 1: k_pred_gather<1><<<nb, 128, 0, st>>>(Xs_dev, n_star, g, (const double*)res, with_grad, mean_dev, badp); break;
-        case 2: k_pred_gather<2><<<nb, 128, 0, st>>>(Xs_dev, n_star, g, (const double*)res, with_grad, mean_dev, badp); break;
-        default: k_pred_gather<3><<<nb, 128, 0, st>>>(Xs_dev, n_star, g, (const double*)res, with_grad, mean_dev, badp); break;
-      }
+      with_stencil(h, [&](auto Sc) {
+        constexpr int S = decltype(Sc)::value;
+        switch (d) {
+          case 1: k_pred_gather<1, S><<<nb, 128, 0, st>>>(Xs_dev, n_star, g, (const double*)res, with_grad, mean_dev, badp); break;
+          case 2: k_pred_gather<2, S><<<nb, 128, 0, st>>>(Xs_dev, n_star, g, (const double*)res, with_grad, mean_dev, badp); break;
+          default: k_pred_gather<3, S><<<nb, 128, 0, st>>>(Xs_dev, n_star, g, (const double*)res, with_grad, mean_dev, badp); break;
+        }
+      });
     }
     DSKI_LAUNCHED();
     if (cudaStreamSynchronize(st) != cudaSuccess)
@@ -300,11 +304,14 @@ extern "C" int dski_predict(dski_handle h, pivchol_handle pc, const double* alph
         return set_error(DSKI_ERR_CUDA, "dski_predict: memset failed");
       {
         StageScope sc(h, ST_SCATTER, st);
-        switch (d) {
-          case 1: k_pred_scatter<1><<<1, 64, 0, st>>>(Xs_dev, i0, s, g, M, G1.as<double>(), badp); break;
-          case 2: k_pred_scatter<2><<<1, 64, 0, st>>>(Xs_dev, i0, s, g, M, G1.as<double>(), badp); break;
-          default: k_pred_scatter<3><<<1, 64, 0, st>>>(Xs_dev, i0, s, g, M, G1.as<double>(), badp); break;
-        }
+        with_stencil(h, [&](auto Sc) {
+          constexpr int S = decltype(Sc)::value;
+          switch (d) {
+            case 1: k_pred_scatter<1, S><<<1, 64, 0, st>>>(Xs_dev, i0, s, g, M, G1.as<double>(), badp); break;
+            case 2: k_pred_scatter<2, S><<<1, 64, 0, st>>>(Xs_dev, i0, s, g, M, G1.as<double>(), badp); break;
+            default: k_pred_scatter<3, S><<<1, 64, 0, st>>>(Xs_dev, i0, s, g, M, G1.as<double>(), badp); break;
+          }
+        });
       }
       DSKI_LAUNCHED();
       void* res = nullptr;
@@ -360,11 +367,14 @@ extern "C" int dski_predict_var_cv(dski_handle h, pivchol_handle pc, const doubl
     StageScope sc(h, ST_SCATTER, st);
     const long long th = (long long)n_star * P;
     const unsigned nb = (unsigned)((th + 255) / 256);
-    switch (d) {
-      case 1: k_pred_scatter_z<1><<<nb, 256, 0, st>>>(Xs_dev, n_star, P, seed, g, M, G1.as<double>(), badp); break;
-      case 2: k_pred_scatter_z<2><<<nb, 256, 0, st>>>(Xs_dev, n_star, P, seed, g, M, G1.as<double>(), badp); break;
-      default: k_pred_scatter_z<3><<<nb, 256, 0, st>>>(Xs_dev, n_star, P, seed, g, M, G1.as<double>(), badp); break;
-    }
+    with_stencil(h, [&](auto Sc) {
+      constexpr int S = decltype(Sc)::value;
+      switch (d) {
+        case 1: k_pred_scatter_z<1, S><<<nb, 256, 0, st>>>(Xs_dev, n_star, P, seed, g, M, G1.as<double>(), badp); break;
+        case 2: k_pred_scatter_z<2, S><<<nb, 256, 0, st>>>(Xs_dev, n_star, P, seed, g, M, G1.as<double>(), badp); break;
+        default: k_pred_scatter_z<3, S><<<nb, 256, 0, st>>>(Xs_dev, n_star, P, seed, g, M, G1.as<double>(), badp); break;
+      }
+    });
   }
   DSKI_LAUNCHED();
   void* res = nullptr;
@@ -397,11 +407,14 @@ extern "C" int dski_predict_var_cv(dski_handle h, pivchol_handle pc, const doubl
   {
     StageScope sc(h, ST_GATHER, st);
     const unsigned nb = (unsigned)((n_star + 127) / 128);
-    switch (d) {
-      case 1: k_pred_cv<1><<<nb, 128, 0, st>>>(Xs_dev, n_star, P, seed, g, M, (const double*)res, var_dev); break;
-      case 2: k_pred_cv<2><<<nb, 128, 0, st>>>(Xs_dev, n_star, P, seed, g, M, (const double*)res, var_dev); break;
-      default: k_pred_cv<3><<<nb, 128, 0, st>>>(Xs_dev, n_star, P, seed, g, M, (const double*)res, var_dev); break;
-    }
+    with_stencil(h, [&](auto Sc) {
+      constexpr int S = decltype(Sc)::value;
+      switch (d) {
+        case 1: k_pred_cv<1, S><<<nb, 128, 0, st>>>(Xs_dev, n_star, P, seed, g, M, (const double*)res, var_dev); break;
+        case 2: k_pred_cv<2, S><<<nb, 128, 0, st>>>(Xs_dev, n_star, P, seed, g, M, (const double*)res, var_dev); break;
+        default: k_pred_cv<3, S><<<nb, 128, 0, st>>>(Xs_dev, n_star, P, seed, g, M, (const double*)res, var_dev); break;
+      }
+    });
   }
   DSKI_LAUNCHED();
   int hb = 0;

@@ -15,13 +15,14 @@ def gpu_op(p, prec="fp64"):
     from paper_1810_12283_gb300 import DSKI
     X = torch.tensor(p["X"], dtype=torch.float64, device="cuda")
     return DSKI(X, p["m"], p["lo"], p["hi"], p["ell"], p["sf"], p["noise_value"],
-                p["noise_grad"], prec=prec)
+                p["noise_grad"], prec=prec, interp=p.get("interp", "cubic"),
+                kuu=p.get("kuu", "dense"))
 
 
 def oracle_op(p):
     from oracle.dski import DSKI as ODSKI, Grid
-    return ODSKI(p["X"], Grid(p["m"], p["lo"], p["hi"]), p["ell"], p["sf"], p["noise_value"],
-                 p["noise_grad"])
+    return ODSKI(p["X"], Grid(p["m"], p["lo"], p["hi"], p.get("interp", "cubic")), p["ell"],
+                 p["sf"], p["noise_value"], p["noise_grad"])
 
 
 def rel(a, b):
@@ -48,8 +49,8 @@ def mvm_tolerance(orc, v, prec):
     FP64 mode: 1e-10 relative.  Other modes: u * ||abs|| / ||K~ v|| (the
     condition number of evaluating the product term by term times the unit
     roundoff of the mode), never below 1e-6 (FP32 modes) or 1e-10 (FP64_TC,
-    whose digit-split mode products carry ~2^-42 relative error; u = 2^-40
-    leaves a margin of four).  D-SKI gradient rows cancel
+    whose digit-split mode products carry ~2^-61 error relative to the
+    operands' row maxima; u = 2^-40 leaves a wide margin).  D-SKI gradient rows cancel
     terms of size ~1/h against results of size ~1/l, so this condition
     number reaches ~1e5 on fine grids; the bound is the textbook
     normwise one (Higham, Sec. 3.5) with gamma_k replaced by u."""
