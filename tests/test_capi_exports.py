@@ -65,11 +65,11 @@ def test_invalid_arguments_are_rejected_before_any_device_work():
 
     def create(**kw):
         f = dict(n=10, d=2, grid_m=m, grid_lo=lo, grid_hi=hi, lengthscale=ell, outputscale=1.0,
-                 noise_value=1e-3, noise_grad=1e-3, prec=0)
+                 noise_value=1e-3, noise_grad=1e-3, prec=0, interp=0, kuu=0)
         f.update(kw)
         p = _lib.DskiParams(f["n"], f["d"], f["grid_m"], f["grid_lo"], f["grid_hi"],
                             f["lengthscale"], f["outputscale"], f["noise_value"],
-                            f["noise_grad"], f["prec"])
+                            f["noise_grad"], f["prec"], f["interp"], f["kuu"])
         h = C.c_void_p()
         rc = lib.dski_create(C.byref(h), C.byref(p), dummy, None)
         return rc, lib.dski_last_error().decode()
@@ -83,6 +83,13 @@ def test_invalid_arguments_are_rejected_before_any_device_work():
     assert create(grid_hi=(C.c_double * 2)(0.0, 1.0))[0] == -1
     assert create(lengthscale=(C.c_double * 2)(0.2, float("nan")))[0] == -1
     assert create(prec=3, grid_m=(C.c_int * 2)(20, 16))[0] == -1   # FP64_TC needs m % 8 == 0
+    # interpolation scheme and K_UU product (Sec. 3.1)
+    assert create(interp=2)[0] == -1
+    assert create(interp=1, grid_m=(C.c_int * 2)(5, 16)) == \
+        (-1, "dski_create: grid_m[0] must be in 6..1027 (got 5)")   # quintic: 6 nodes
+    assert create(kuu=2)[0] == -1
+    assert create(kuu=1, prec=1) == \
+        (-1, "dski_create: the FFT K_UU product needs FP64 vectors (FP64 or FP64_TC)")
     assert lib.dski_mvm(None, dummy, dummy, 1) == -1
     assert lib.dski_pcg_solve(None, None, dummy, dummy, 1, 1e-8, 10, None, None) == -1
     assert lib.dski_mvm_noalloc(None, dummy, dummy, 1) == -1
