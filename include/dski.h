@@ -88,8 +88,9 @@ typedef enum { DSKI_INTERP_CUBIC = 0, DSKI_INTERP_QUINTIC = 1 } dski_interp;
  * with FP64 FFTs, O(m_k log m_k) per grid line instead of O(m_k^2); FP64 and
  * FP64_TC modes only.  The FFT's rounding is normwise (~log2(L) u |Fc| |x|
  * per product), so dski_pcg_solve ends each pass at a 1e-4 reduction of the
- * residual, forms its true residuals with the dense factors, and its
- * restarts refine x against the dense operator.  The
+ * residual (not while SLQ records Lanczos coefficients), forms its true
+ * residuals with the dense factors, and its restarts refine x against the
+ * dense operator.  The
  * gradient of Eq. 1 applies dK_k / dlog l_k densely in either case.  A
  * zero-initialised dski_params selects DENSE. */
 typedef enum { DSKI_KUU_DENSE = 0, DSKI_KUU_FFT = 1 } dski_kuu;

@@ -454,8 +454,10 @@ int cg_run(dski_handle h, CgRun& run) {
   // inner reduction target (1e-4)^2 where the iterations run a perturbed
   // operator (mixed modes; FFT products, whose normwise rounding stalls the
   // recurrence on ill-conditioned systems): each pass then ends at a 1e-4
-  // reduction and the restart from the dense true residual refines x
-  const double eta2 = (mixed || h->kuu_fft) ? 1e-8 : 0.0;
+  // reduction and the restart from the dense true residual refines x.  Not
+  // while Lanczos coefficients are recorded: the record covers the first
+  // pass, which must then run the full depth.
+  const double eta2 = (depth == 0 && (mixed || h->kuu_fft)) ? 1e-8 : 0.0;
   const double* dis = run.pc ? run.pc->dis.as<double>() : nullptr;
   const dim3 grd(nbx, s);
   const dim3 grv(std::min(nbv, nbx), s);

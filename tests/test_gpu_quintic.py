@@ -153,3 +153,33 @@ def test_quintic_grid_bounds():
     with pytest.raises(DskiError) as e:
         gpu_op(q, "fp64")
     assert e.value.status == "ARG"
+
+
+def test_quintic_slq_and_mll_gradient_same_probes():
+    """SLQ log determinant (Sec. 2) and the gradient of Eq. 1 with the
+    quintic stencil equal the oracle's with identical probes (the GPU's
+    pivots rebuilt in the oracle), as on the cubic path."""
+    need_gpu()
+    from oracle.mll import mll_grad_hutchinson_z
+    from oracle.probes import preconditioned_probes
+    from oracle.slq import slq_logdet_z
+    from oracle.solve import QRPreconditioner, pivoted_cholesky
+    p = Q(W.small2d(60, m=16, seed=11, nv=1e-2, ng=1e-2))
+    op = gpu_op(p, "fp64")
+    orc = oracle_op(p)
+    pc = op.pivchol(20)
+    _, piv = pc.export()
+    Lo, _, _ = pivoted_cholesky(orc.kgrad_diag(), orc.kgrad_row, 20, pivots=piv)
+    Pc = QRPreconditioner(Lo, orc.noise)
+    P, seed = 12, 2024
+    Z = preconditioned_probes(seed, Pc, P)
+    ld, se = op.logdet(pc, probes=P, depth=12, seed=seed)
+    est, se_o, _, _ = slq_logdet_z(orc.mvm, Pc, Z, depth=12, rtol=1e-15, maxit=12)
+    assert abs(ld - est) <= 1e-10 * abs(est), (ld, est)
+    P, seed = 16, 31
+    mll, g = op.mll_grad(torch.tensor(p["y"], device="cuda"), pc, probes=P, seed=seed)
+    Z = preconditioned_probes(seed, Pc, P)
+    _, tr, go = mll_grad_hutchinson_z(orc, p["y"], Pc, Z, rtol=1e-12)
+    assert np.allclose(g, go, rtol=1e-6, atol=1e-6 * np.abs(go).max()), (g, go)
+    pc.close()
+    op.close()
