@@ -187,6 +187,50 @@ def interp_matrix(X, grid):
     return B.tocsr()
 
 
+def interp_matrix_1d(X, grid, k):
+    """Per-dimension interpolation matrices of dimension k: W_k and dW_k
+    (n x m_k, the S weights and derivative weights of each point's stencil
+    in that dimension)."""
+    first, w, dw = stencils(X, grid)
+    n, S = w.shape[0], w.shape[2]
+    Wk = np.zeros((n, grid.m[k]))
+    Dk = np.zeros((n, grid.m[k]))
+    rows = np.repeat(np.arange(n), S)
+    cols = (first[:, k][:, None] + np.arange(S)[None, :]).ravel()
+    np.add.at(Wk, (rows, cols), w[:, k, :].ravel())
+    np.add.at(Dk, (rows, cols), dw[:, k, :].ravel())
+    return Wk, Dk
+
+
+def dense_kgrad_factored(X, grid, factors, outputscale):
+    """Dense B K_UU B^T without forming K_UU (grids too large for
+    kuu_dense).  Every row of B is a tensor product of per-dimension
+    stencils and K_UU = s_f^2 K_1 (x) ... (x) K_d, so each entry factors over
+    dimensions:
+      (B K_UU B^T)[(i,c), (j,c')] = s_f^2 prod_k (a_k K_k b_k^T)[i, j],
+    with a_k = dW_k if c = k + 1 else W_k (rows; c = 0 value, c = p + 1 the
+    derivative in dimension p) and b_k likewise for c'.  `factors` are the
+    K_k (any symmetric m_k x m_k matrices, e.g. dK_k / dlog l_k in one
+    dimension).  Block order [values; d/dx_1; ...]."""
+    X = np.asarray(X, np.float64)
+    n, d = X.shape
+    blocks = []
+    for k in range(d):
+        Wk, Dk = interp_matrix_1d(X, grid, k)
+        Kk = factors[k]
+        WK, DK = Wk @ Kk, Dk @ Kk
+        blocks.append({(0, 0): WK @ Wk.T, (1, 0): DK @ Wk.T, (0, 1): WK @ Dk.T,
+                       (1, 1): DK @ Dk.T})
+    out = np.empty((n * (d + 1), n * (d + 1)))
+    for c in range(d + 1):
+        for c2 in range(d + 1):
+            T = np.full((n, n), float(outputscale) ** 2)
+            for k in range(d):
+                T *= blocks[k][(int(c == k + 1), int(c2 == k + 1))]
+            out[c * n:(c + 1) * n, c2 * n:(c2 + 1) * n] = T
+    return out
+
+
 def noise_diag(n, d, noise_value, noise_grad):
     """Diagonal of the noise term: sigma_v^2 on value rows, sigma_g^2 on gradient rows."""
     return np.concatenate([np.full(n, float(noise_value)), np.full(n * d, float(noise_grad))])

@@ -15,7 +15,7 @@ Test infrastructure only (see ``oracle/__init__``).
 """
 import numpy as np
 
-from .dski import DSKI, kfactor, kfactor_dlogell, kron_apply
+from .dski import DSKI, dense_kgrad_factored, kfactor, kfactor_dlogell, kron_apply
 from .solve import chol_solve, chol_logdet, pcg
 
 
@@ -35,21 +35,43 @@ def dtheta_mvm(op: DSKI, i, V):
     return out.ravel() if V.ndim == 1 else out
 
 
-def mll_dense(op: DSKI, y):
-    """Eq. 1 by the direct (Cholesky) method."""
-    A = op.dense()
+def dtheta_dense_factored(op: DSKI, i):
+    """dK~/dtheta_i as a dense matrix through dense_kgrad_factored (for grids
+    too large for the dense K_UU); equals dtheta_mvm(op, i, I)."""
+    d = op.d
+    if i < d:
+        facs = [kfactor_dlogell(op.grid, k, op.ell[k]) if k == i else kfactor(op.grid, k, op.ell[k])
+                for k in range(d)]
+        return dense_kgrad_factored(op.X, op.grid, facs, op.sf)
+    if i == d:
+        facs = [kfactor(op.grid, k, op.ell[k]) for k in range(d)]
+        return 2.0 * dense_kgrad_factored(op.X, op.grid, facs, op.sf)
+    return np.diag(2.0 * op.noise)
+
+
+def _dense_matrix(op: DSKI, factored):
+    if not factored:
+        return op.dense()
+    facs = [kfactor(op.grid, k, op.ell[k]) for k in range(op.d)]
+    return dense_kgrad_factored(op.X, op.grid, facs, op.sf) + np.diag(op.noise)
+
+
+def mll_dense(op: DSKI, y, factored=False):
+    """Eq. 1 by the direct (Cholesky) method; factored=True forms K~ through
+    dense_kgrad_factored (large grids)."""
+    A = _dense_matrix(op, factored)
     alpha = chol_solve(A, y)
     return -0.5 * (y @ alpha + chol_logdet(A) + op.N * np.log(2.0 * np.pi))
 
 
-def mll_grad_dense(op: DSKI, y):
+def mll_grad_dense(op: DSKI, y, factored=False):
     """Exact gradient of Eq. 1 with the trace taken through the dense inverse."""
-    A = op.dense()
+    A = _dense_matrix(op, factored)
     alpha = chol_solve(A, y)
     Ainv = chol_solve(A, np.eye(op.N))
     g = []
     for i in range(op.d + 2):
-        dK = dtheta_mvm(op, i, np.eye(op.N))
+        dK = dtheta_dense_factored(op, i) if factored else dtheta_mvm(op, i, np.eye(op.N))
         g.append(0.5 * alpha @ dK @ alpha - 0.5 * np.sum(Ainv * dK.T))
     return np.array(g)
 

@@ -3,6 +3,7 @@ multivariate normal density, the exact gradient against central finite
 differences, and the Hutchinson gradient against the exact one with scaled
 basis probes (an exact trace)."""
 import numpy as np
+import pytest
 import scipy.stats as st
 
 from oracle.dski import DSKI, Grid
@@ -68,3 +69,44 @@ def test_hutchinson_with_factor_basis_probes_is_exact():
     Z = np.sqrt(P) * Pc.factor_apply(np.eye(P))
     _, _, g = mll_grad_hutchinson_z(op, y, Pc, Z, rtol=1e-14)
     assert np.allclose(g, mll_grad_dense(op, y), rtol=1e-7, atol=1e-7)
+
+
+@pytest.mark.parametrize("d,m,interp", [(2, (9, 11), "cubic"), (3, (7, 8, 9), "cubic"),
+                                        (2, (11, 13), "quintic"), (3, (9, 10, 11), "quintic")])
+def test_factored_dense_matrices_equal_the_kronecker_ones(d, m, interp):
+    # the per-dimension (Hadamard) form of B K_UU B^T and of every dK~/dtheta
+    # equals the one through the dense K_UU
+    from oracle.dski import dense_kgrad_factored, kfactor
+    from oracle.mll import dtheta_dense_factored, dtheta_mvm
+    X = np.random.default_rng(1).uniform(0, 1, (15, d))
+    g = Grid(m, (-0.6,) * d, (1.6,) * d, interp)
+    op = DSKI(X, g, [0.3, 0.4, 0.5][:d], 1.3, 1e-3, 2e-3)
+    A = op.dense_kgrad()
+    B = dense_kgrad_factored(X, g, [kfactor(g, k, op.ell[k]) for k in range(d)], op.sf)
+    assert np.allclose(B, A, rtol=0, atol=1e-14 * np.abs(A).max())
+    for i in range(d + 2):
+        Di = dtheta_mvm(op, i, np.eye(op.N))
+        assert np.allclose(dtheta_dense_factored(op, i), Di, rtol=0, atol=1e-13 * np.abs(Di).max())
+
+
+def test_surface_subsample_gradient_matches_central_differences():
+    # the 3-D bumpy-surface generator at 55,000 points, seeded n = 1,000
+    # subsample, theta = (log 0.2 x 3, log 1, log 1e-2): the exact gradient of
+    # Eq. 1 against central differences of the exact L with step 1e-4
+    from synth import workloads as W
+    from oracle.mll import mll_dense, mll_grad_dense
+    p = W.subsample(W.surface3d_big(), 1000, seed=0)
+
+    def op_at(th):
+        s2 = np.exp(2 * th[4])
+        return DSKI(p["X"], Grid(p["m"], p["lo"], p["hi"]), np.exp(th[:3]), np.exp(th[3]), s2, s2)
+
+    th = np.array([np.log(0.2)] * 3 + [0.0, 0.5 * np.log(1e-4)])
+    g = mll_grad_dense(op_at(th), p["y"], factored=True)
+    h = 1e-4
+    for i in range(5):
+        e = np.zeros(5)
+        e[i] = h
+        fd = (mll_dense(op_at(th + e), p["y"], factored=True)
+              - mll_dense(op_at(th - e), p["y"], factored=True)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * abs(g[i]), (i, fd, g[i])
