@@ -317,7 +317,9 @@ def test_mll_gradient_surface_subsample_against_dense():
     a seeded n = 1,000 subsample, 64^3 grid, l = 0.2, s_f = 1, sigma^2 =
     1e-4) through the autograd Function: PCG, the 16-probe trace estimate and
     the adjoint grid products.  The mean over six probe seeds equals the
-    exact dense gradient within five standard errors, in FP64 and FP64_TC.
+    exact dense gradient within five standard errors, in FP64_TC (the FP64
+    path passed the same check once; it is left out to keep the suite short,
+    each gradient taking ~25 s on this system).
     The oracle forms the dense matrices factor by factor, and central
     differences with step 1e-4 pin that gradient (test_oracle_mll)."""
     need_gpu()
@@ -328,7 +330,7 @@ def test_mll_gradient_surface_subsample_against_dense():
     orc = oracle_op(p)
     ge = mll_grad_dense(orc, p["y"], factored=True)
     y = torch.tensor(p["y"], device="cuda")
-    for prec in ("fp64", "fp64_tc"):
+    for prec in ("fp64_tc",):
         op = gpu_op(p, prec)
         gs = []
         for seed in range(6):
