@@ -75,3 +75,19 @@ def test_gather_byte_count():
 def test_scatter_flop_count():
     import bench
     assert bench.scatter_flops(100_000, 2) == 100_000 * 83
+
+
+def test_quintic_stencil_counts_and_workload_names():
+    # the quintic stencil (6 nodes per dimension): 2 * 6 * d weights per
+    # point, 36 node-point pairs per point in the d = 2 node pass
+    import bench
+    n, d, M = 1000, 2, 256 * 256
+    assert bench.stencil_nodes("cubic") == 4 and bench.stencil_nodes("quintic") == 6
+    assert bench.scatter_bytes(n, d, M, 1, 8, 6) - bench.scatter_bytes(n, d, M, 1, 8) == \
+        n * (2 * 6 - 2 * 4) * d * 8
+    assert bench.scatter_flops(n, d, 6) == n * (3 + 6 * 3 + 6 + 36 * 4)
+    assert bench.mvm_bytes(n, d, M, 1, 8, 6) - bench.mvm_bytes(n, d, M, 1, 8) == \
+        2 * n * 8 * (12 - 8) * d
+    name = bench.workload_name(100_000)
+    assert "interp" not in name and "kuu" not in name
+    assert bench.workload_name(100_000, "quintic", "fft").endswith("interp=quintic kuu=fft")
