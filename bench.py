@@ -35,7 +35,10 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-METRIC = "PCG solve time to rel. residual 1e-8, terrain n=100k d=2 (GB300, tensor-core FP64_TC vs FP64)"
+# the headline metric (PCG solve seconds and D-SKI MVM HBM GB/s, mixed
+# vs FP64, on the terrain workload at relative residual 1e-8); `value` is the
+# solve time of the headline mode, the other modes sit under "compare"
+METRIC = "PCG solve s & D-SKI MVM HBM GB/s: mixed vs FP64, same GB300, rel res 1e-8"
 UNIT = "s"
 RANK = 100
 PROF_ITERS = 3000   # PCG iterations of the profiled (untimed) step
@@ -52,28 +55,44 @@ def stencil_nodes(interp):
     return 6 if interp == "quintic" else 4
 
 
-def mvm_bytes(n, d, M, s, elem, S=4):
-    """Algorithmic HBM bytes of one MVM: v read by scatter and by the noise
-    term, out written, the grid written by scatter and read by gather, and
-    the per-point geometry (cell id + 2 S d weights) read by scatter and gather."""
-    N = n * (d + 1)
-    geo = n * (4 + elem * 2 * S * d)
-    return s * (3 * N * elem + 2 * M * elem) + 2 * geo
+def geometry_bytes(d, elem):
+    """Per-point geometry the scatter and gather need: the int32 cell id and
+    d cell fractions in the vector precision (g = 4 + 4 d bytes with FP32
+    vectors, 4 + 8 d with FP64)."""
+    return 4 + elem * d
 
 
-def scatter_bytes(n, d, M, s, elem, S=4):
-    """HBM model of one scatter: v (N s elements) read, the per-point weight
-    table (2 S d elements) and cell id (4 B) read, the grid (M s elements)
-    written."""
+def weight_table_bytes(d, elem, S=4):
+    """Per-point bytes of the precomputed stencil weight tables the kernels
+    read instead of recomputing the weights from the fractions (S weights
+    and S derivative weights per dimension): traffic beyond the algorithmic
+    model, reported separately."""
+    return elem * 2 * S * d
+
+
+def mvm_bytes(n, d, s, elem):
+    """Algorithmic HBM bytes of one MVM: v read by the scatter and by the
+    noise term, out written (3 N s elements), the per-point geometry read by
+    scatter and gather (2 n g).  The grid stays in L2."""
     N = n * (d + 1)
-    return N * s * elem + n * (4 + 2 * S * d * elem) + M * s * elem
+    return 3 * N * s * elem + 2 * n * geometry_bytes(d, elem)
+
+
+def scatter_bytes(n, d, M, s, elem):
+    """Algorithmic bytes of one scatter: v read (N s elements), the geometry
+    read (n g), the grid written (M s elements)."""
+    N = n * (d + 1)
+    return N * s * elem + n * geometry_bytes(d, elem) + M * s * elem
+
+
+def gather_bytes(n, d, M, s, elem):
+    """Algorithmic bytes of one gather with the noise term: the grid (M s)
+    and v (N s) read, the geometry read (n g), out (N s) written."""
+    N = n * (d + 1)
+    return M * s * elem + 2 * N * s * elem + n * geometry_bytes(d, elem)
 
 
 OZ_PAIRS = 36   # digit pairs (a, b), a + b < 8, of the FP64_TC mode product
-# DRAM bytes (read + write) of one k_oz_mode mode product on the 256 x 256
-# terrain grid, from one ncu capture of the current kernel
-# (profiles/k_oz_mode_terrain2d_ncu.md): 1,626,880 read, 0 written
-OZ_MODE_TRAFFIC = 1_626_880
 
 
 def scatter_flops(n, d, S=4):
@@ -84,11 +103,32 @@ def scatter_flops(n, d, S=4):
     return n * (3 + S * 3 + S + S * S * 4)
 
 
-def precond_bytes(N, r, s):
-    """Algorithmic bytes of one preconditioner apply: Q1 (8 bytes per entry,
-    FP64 or an FP32 hi/lo pair) read twice (Q1^T y, then y - Q1 c), r read
-    twice, z written."""
-    return 2 * N * r * 8 + s * 3 * N * 8
+def measure_peaks(dev):
+    """Dense-GEMM rates of this GPU measured in the run (CUDA events, best of
+    3 after a warm-up): FP64 (cuBLAS DGEMM, 8192^3) and TF32 (cuBLAS FP32
+    GEMM on the TF32 tensor cores, 8192^3), in TFLOP/s."""
+    import torch
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    for name, dt, tf32, nn in (("fp64_tflops", torch.float64, False, 8192),
+                               ("tf32_tflops", torch.float32, True, 8192)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(nn, nn, device=dev, dtype=dt)
+        b = torch.randn(nn, nn, device=dev, dtype=dt)
+        c = a @ b
+        best = 1e30
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        out[name] = 2.0 * nn ** 3 / best / 1e12
+        del a, b, c
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    torch.cuda.empty_cache()
+    return out
 
 
 class ClockSampler:
@@ -169,18 +209,33 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def cpu_baseline(p, iters_gpu, budget_s=12.0):
-    """The FP64 oracle on the host cores: operator build, rank-100 pivoted
-    Cholesky and QR preconditioner (timed whole), then PCG iterations timed
-    on a bounded sample and scaled to the GPU's iteration count."""
+# the FP64 PCG iteration count of the terrain solve to 1e-8 measured on
+# GB300 (the FP64 mode's "compare" entry of the bench line); the reference
+# arm, which runs no GPU code, scales its per-iteration oracle time to it
+FP64_TERRAIN_ITERS = 120158
+
+
+def oracle_operator(p):
+    """The oracle's D-SKI operator and rank-100 preconditioner for problem p,
+    and the seconds the set-up took."""
     from oracle.dski import DSKI as ODSKI, Grid
-    from oracle.solve import QRPreconditioner, pcg, pivoted_cholesky
+    from oracle.solve import QRPreconditioner, pivoted_cholesky
     t0 = time.perf_counter()
     op = ODSKI(p["X"], Grid(p["m"], p["lo"], p["hi"], p.get("interp", "cubic")), p["ell"],
                p["sf"], p["noise_value"], p["noise_grad"])
     L, _, _ = pivoted_cholesky(op.kgrad_diag(), op.kgrad_row, RANK)
     Pc = QRPreconditioner(L, op.noise)
-    t_setup = time.perf_counter() - t0
+    return op, Pc, time.perf_counter() - t0
+
+
+def cpu_baseline(p, iters_scaled_to, iters_source, budget_s=12.0, built=None):
+    """The FP64 oracle on the host cores: operator build, rank-100 pivoted
+    Cholesky and QR preconditioner (timed whole), then PCG iterations timed
+    on a bounded sample and scaled to `iters_scaled_to` iterations -- an
+    extrapolation, labelled as such.  `built`: (op, Pc, setup seconds) from
+    oracle_operator, reused."""
+    from oracle.solve import pcg
+    op, Pc, t_setup = built if built is not None else oracle_operator(p)
     k = 5
     while True:
         t0 = time.perf_counter()
@@ -190,18 +245,115 @@ def cpu_baseline(p, iters_gpu, budget_s=12.0):
             break
         k = int(k * max(2.0, min(8.0, budget_s / 4 / max(dt, 1e-3))))
     per_it = dt / k
-    est = t_setup + per_it * iters_gpu
+    est = t_setup + per_it * iters_scaled_to
     return {"value": est, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+            "extrapolated": True, "iters_timed": k, "iters_scaled_to": int(iters_scaled_to),
+            "iters_source": iters_source, "setup_s": t_setup, "s_per_iter": per_it,
             "sample": (f"oracle setup (operator, rank-{RANK} pivoted Cholesky, QR) timed whole "
                        f"({t_setup:.1f} s); {k} oracle PCG iterations timed ({dt:.1f} s, "
-                       f"{per_it * 1e3:.1f} ms each), scaled to the GPU's {iters_gpu} iterations")}
+                       f"{per_it * 1e3:.1f} ms each), extrapolated to {int(iters_scaled_to)} "
+                       f"iterations ({iters_source})")}
 
 
-def gather_bytes(n, d, M, s, elem):
-    """HBM model of one gather with the noise term: the grid (M s) and v
-    (N s) read, the per-point weights and cell id read, out (N s) written."""
-    N = n * (d + 1)
-    return M * s * elem + 2 * N * s * elem + n * (4 + 8 * d * elem)
+SUB_N, SUB_SEED, SUB_PROBES, SUB_DEPTH = 1000, 9, 8, 12
+SUB_RTOL = 1e-10
+
+
+def gpu_subsample_run(DSKI, p, prec, dev):
+    """The GPU's solve, SLQ log determinant and Eq. 1 gradient on a seeded
+    1000-point subsample of the workload (same grid and hyperparameters),
+    for the oracle check.  Returns host values and the GPU's pivots."""
+    import torch
+    from synth import workloads as W
+    q = W.subsample(p, SUB_N, seed=SUB_SEED)
+    op = DSKI(torch.tensor(q["X"], device=dev), q["m"], q["lo"], q["hi"], q["ell"], q["sf"],
+              q["noise_value"], q["noise_grad"], prec=prec, interp=p["interp"], kuu=p["kuu"])
+    pc = op.pivchol(RANK)
+    _, piv = pc.export()
+    y = torch.tensor(q["y"], device=dev)
+    out = {"prec": prec, "q": q, "piv": piv, "rank": pc.rank}
+    try:
+        x, it, rr = op.solve(y, pc, rtol=SUB_RTOL, maxit=200000, allow_not_converged=True)
+        out.update(x=x.cpu().numpy(), iters=it[0], relres=rr[0])
+    except Exception as e:   # noqa: BLE001 -- reported
+        out["solve_error"] = str(e)
+    try:
+        out["logdet"], out["logdet_se"] = op.logdet(pc, probes=SUB_PROBES, depth=SUB_DEPTH,
+                                                    seed=777)
+    except Exception as e:   # noqa: BLE001
+        out["logdet_error"] = str(e)
+    try:
+        out["mll"], out["grad"] = op.mll_grad(y, pc, probes=SUB_PROBES, seed=31, rtol=SUB_RTOL,
+                                              maxit=200000)
+    except Exception as e:   # noqa: BLE001
+        out["grad_error"] = str(e)
+    pc.close()
+    op.close()
+    return out
+
+
+def oracle_check(p, built, xs, subs):
+    """Errors of the GPU's results against the FP64 oracle (untimed).
+    xs: {mode: x} full-size solutions (host, block order):
+      relres_oracle = ||y - K~_oracle x|| / ||y||.
+    subs: gpu_subsample_run results: the subsample's solve against the dense
+    direct solve, the SLQ log determinant against the oracle's with the same
+    probes (and the exact dense log determinant, in GPU standard errors),
+    the gradient of Eq. 1 against the oracle's same-probe estimator (solves
+    from the dense Cholesky factor) and the exact dense gradient."""
+    import numpy as np
+    from oracle.dski import DSKI as ODSKI, Grid
+    from oracle.mll import mll_grad_dense, mll_grad_hutchinson_direct
+    from oracle.probes import preconditioned_probes
+    from oracle.slq import slq_logdet_z
+    from oracle.solve import QRPreconditioner, chol_logdet, chol_solve, pivoted_cholesky
+    from oracle.mll import _dense_matrix
+    op = built[0]
+    y = p["y"]
+    out = {"full": {}}
+    ny = float(np.linalg.norm(y))
+    for mode, x in xs.items():
+        out["full"][mode] = {"relres_oracle": float(np.linalg.norm(y - op.mvm(x)) / ny)}
+    for sub in subs:
+        q = sub["q"]
+        o = ODSKI(q["X"], Grid(q["m"], q["lo"], q["hi"], q.get("interp", "cubic")), q["ell"],
+                  q["sf"], q["noise_value"], q["noise_grad"])
+        A = _dense_matrix(o, True)
+        r = {"n": int(q["X"].shape[0]), "rtol": SUB_RTOL, "probes": SUB_PROBES,
+             "depth": SUB_DEPTH}
+        if "x" in sub:
+            xd = chol_solve(A, q["y"])
+            nq = float(np.linalg.norm(q["y"]))
+            r["solve"] = {"iters": sub["iters"], "relres_gpu": sub["relres"],
+                          "relres_oracle": float(np.linalg.norm(q["y"] - A @ sub["x"]) / nq),
+                          "backward_diff_vs_direct": float(np.linalg.norm(A @ (sub["x"] - xd)) / nq)}
+        else:
+            r["solve"] = {"error": sub.get("solve_error")}
+        Lo, _, _ = pivoted_cholesky(o.kgrad_diag(), o.kgrad_row, sub["rank"], pivots=sub["piv"])
+        Pc = QRPreconditioner(Lo, o.noise)
+        if "logdet" in sub:
+            Z = preconditioned_probes(777, Pc, SUB_PROBES)
+            est, se_o, _, _ = slq_logdet_z(o.mvm, Pc, Z, depth=SUB_DEPTH, rtol=1e-15,
+                                           maxit=SUB_DEPTH)
+            exact = chol_logdet(A)
+            r["logdet"] = {"gpu": sub["logdet"], "oracle_same_probes": float(est),
+                           "rel_err_same_probes": float(abs(sub["logdet"] - est) / abs(est)),
+                           "exact_dense": float(exact),
+                           "gpu_minus_exact_in_se": float((sub["logdet"] - exact) / sub["logdet_se"])}
+        else:
+            r["logdet"] = {"error": sub.get("logdet_error")}
+        if "grad" in sub:
+            Z = preconditioned_probes(31, Pc, SUB_PROBES)
+            _, _, go = mll_grad_hutchinson_direct(o, q["y"], Pc, Z, factored=True)
+            ge = mll_grad_dense(o, q["y"], factored=True)
+            g = np.array(sub["grad"])
+            r["grad"] = {"gpu": g.tolist(), "oracle_same_probes": go.tolist(),
+                         "max_rel_err_same_probes": float(np.max(np.abs(g - go)) / np.max(np.abs(go))),
+                         "exact_dense": ge.tolist()}
+        else:
+            r["grad"] = {"error": sub.get("grad_error")}
+        out["subsample_" + sub["prec"]] = r
+    return out
 
 
 SWEEP = ((100_000, 256), (1_000_000, 256), (10_000_000, 1024), (30_000_000, 1024))
@@ -325,12 +477,16 @@ def run_reference(args, p):
     rank, ws, dist = dist_init()
     if rank != 0:
         return 0
-    # the oracle PCG is scaled to the iteration count the FP64 GPU path needs
-    # for this system (measured on GB300; passed in with --ref-iters)
+    # the oracle PCG is extrapolated to the iteration count FP64 PCG needs
+    # for this system (measured on GB300; --ref-iters): a full oracle solve
+    # would take ~35 minutes of CPU time
     iters = args.ref_iters
+    src = ("FP64 PCG iterations of this system to 1e-8 measured on GB300"
+           if iters == FP64_TERRAIN_ITERS else "--ref-iters")
     steps = []
     for _ in range(max(args.steps, 1)):
-        steps.append(cpu_baseline(p, iters, budget_s=max(4.0, 60.0 / (args.steps + args.warmup))))
+        steps.append(cpu_baseline(p, iters, src,
+                                  budget_s=max(4.0, 60.0 / (args.steps + args.warmup))))
     v = statistics.median(s["value"] for s in steps)
     cb = dict(steps[0])
     cb["value"] = v
@@ -359,8 +515,9 @@ def main():
                          "min(1.5x the headline iterations, 30000)")
     ap.add_argument("--maxit", type=int, default=400000)
     ap.add_argument("--n", type=int, default=100_000)
-    ap.add_argument("--ref-iters", type=int, default=120126,
-                    help="reference arm: PCG iterations to scale the oracle's per-iteration time to")
+    ap.add_argument("--ref-iters", type=int, default=FP64_TERRAIN_ITERS,
+                    help="reference arm: PCG iterations to extrapolate the oracle's "
+                         "per-iteration time to")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--interp", default="cubic", choices=["cubic", "quintic"],
                     help="interpolation stencil (Keys cubic, 4^d; the paper's quintic, 6^d)")
@@ -428,7 +585,7 @@ def main():
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
-        ms, its, rrs, stages, launches = [], [], [], None, 0
+        ms, its, rrs, stages, launches, xlast = [], [], [], None, 0, None
         for i in range(steps):
             flush.fill_(i & 255)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -443,11 +600,12 @@ def main():
             rrs.append(rr)
             if st is not None:
                 stages = st
+            xlast = x
             pc.close()
             op.close()
         if dist is not None:
             dist.barrier()
-        return ms, its, rrs, stages, launches
+        return ms, its, rrs, stages, launches, xlast
 
     def mvm_rate(prec, reps=50):
         op = DSKI(X, p["m"], p["lo"], p["hi"], p["ell"], p["sf"], p["noise_value"],
@@ -471,27 +629,34 @@ def main():
         op.close()
         per = tot / reps
         elem = 8 if prec in ("fp64", "fp64_tc") else 4
-        return {"ms_per_mvm": per, "gbs": mvm_bytes(n, d, M, 1, elem, SN) / (per / 1e3) / 1e9,
+        algo = mvm_bytes(n, d, 1, elem)
+        extra = 2 * n * weight_table_bytes(d, elem, SN)
+        return {"ms_per_mvm": per, "gbs": algo / (per / 1e3) / 1e9, "algo_bytes": algo,
+                "extra_traffic": extra,
+                "extra_traffic_note": "per-point stencil weight tables read by scatter and "
+                                      "gather, beyond the algorithmic model (not counted in gbs)",
                 "stages_us": {k: round(1e3 * v[0] / max(v[2], 1) * v[1] / reps, 2)
                               for k, v in st.items() if v[1]}}
 
     # timed steps with the stage timers off: the PCG chunks then replay as
     # CUDA graphs (the timers' events would disable them)
     with ClockSampler(local) as clk:
-        ms, its, rrs, _, launches = timed_steps(args.prec, args.warmup, args.steps, False)
+        ms, its, rrs, _, launches, x_head = timed_steps(args.prec, args.warmup, args.steps, False)
     clocks = clk.summary()
+    xs = {args.prec: x_head.cpu().numpy()}
     # stage data from one more, untimed step with the timers on, its PCG
     # capped at PROF_ITERS iterations
     prof_iters = min(PROF_ITERS, max(its[-1], 1))
-    _, _, _, stages, _ = timed_steps(args.prec, 0, 1, True, maxit=prof_iters)
+    _, _, _, stages, _, _ = timed_steps(args.prec, 0, 1, True, maxit=prof_iters)
     compare = {}
     for mode in [m for m in args.compare.split(",") if m and m != args.prec]:
         try:
             cap = args.maxit if mode in ("fp64", "fp64_tc") else min(int(1.5 * its[-1]) + 100, 30000)
-            msc, itc, rrc, _, _ = timed_steps(mode, 0, 1, False, maxit=cap)
+            msc, itc, rrc, _, _, xc = timed_steps(mode, 0, 1, False, maxit=cap)
             compare[mode] = {"s_per_step": msc[-1] / 1e3, "iters": itc[-1], "relres": rrc[-1],
-                             "reached_rtol": rrc[-1] <= RTOL,
+                             "reached_rtol": rrc[-1] <= RTOL, "iter_cap": cap,
                              "s_per_iter": msc[-1] / 1e3 / max(itc[-1], 1)}
+            xs[mode] = xc.cpu().numpy()
         except Exception as e:   # noqa: BLE001 -- reported, not fatal
             compare[mode] = {"error": str(e)}
     mvm = {prec: mvm_rate(prec) for prec in ("fp64", "fp64_tc", "mixed_3xtf32")
@@ -524,6 +689,12 @@ def main():
         pass
     hbm = peaks.get("hbm_gbs") or 6800.0
     hbm_src = "measured" if peaks.get("hbm_gbs") else "fallback"
+    bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
+    bf16_src = ("measured" if peaks.get("bf16_tflops_sustained") else "fallback") + \
+        " sustained dense BF16 (cuBLAS; the kernel runs inside a long step)"
+    gemm = measure_peaks(dev)   # FP64 and TF32 dense-GEMM rates of this GPU, in this run
+    fp64_pk = gemm["fp64_tflops"]
+    fp64_src = "measured in this run: cuBLAS DGEMM 8192^3, best of 3"
     it_last = its[-1]
     # per stage (profiled step: set-up + prof_iters PCG iterations): mean
     # device time per launch, and per PCG iteration for the iteration stages
@@ -531,44 +702,60 @@ def main():
     per_launch_ms = {k: v[0] / max(v[2], 1) for k, v in st.items()}
     stage_total_ms = {k: per_launch_ms[k] * v[1] for k, v in st.items()}
     iter_stages = ("scatter", "kron", "gather", "precond", "pcg_vec")
-    # roofline of the dominant kernel (the ncu launch list of this command
-    # ranks it first).  FP64: the Kronecker mode product k_mode_simt, one
-    # launch per mode product, 2 M m_k FP64 flops on the FP64 units.  FP64_TC:
+    # Roofline of the kernel the ncu launch list of this command ranks first.
+    # FP64: the Kronecker mode product k_mode_simt (one launch per mode
+    # product, 2 M m_k FP64 flops) against the measured DGEMM rate.  FP64_TC:
     # the digit-product kernel k_oz_mode, one launch per mode product (the
-    # kron stage), OZ_PAIRS digit-pair BF16 products of 2 M m_k flops each
-    # against the measured sustained BF16 peak (timed inside a long step).
-    # The FP64 scatter is reported beside it against its FP64 flops.
-    # Mixed modes: the FP32 scatter against its HBM model.
-    fp64_peak_src = "nominal GB300 FP64 1.25 TFLOP/s (MEASURED_PEAKS has no FP64 entry; a DGEMM probe measured 1.05)"
+    # kron stage), the method's 2 M m_k flops against the BF16 tensor pipe it
+    # runs on; the rate of the 36 digit-pair BF16 products it issues for them,
+    # and the FP64-equivalent rate against the measured DGEMM rate, beside it.
+    # Mixed modes: the FP32 scatter against the HBM model.  The FP64 scatter
+    # is reported beside (FP64 flops against the measured DGEMM rate).
     roof_scatter = None
-    traffic = None
+    extra = {}
+    elem = 8 if args.prec in ("fp64", "fp64_tc") else 4
     if args.prec in ("fp64", "fp64_tc"):
         per_sc = 2 * per_launch_ms["scatter"] / 1e3
         fl = scatter_flops(n, d, SN)
+        bsc = scatter_bytes(n, d, M, 1, 8)
         roof_scatter = {"kernel": "k_scatter_prep + k_scatter_ab (scatter)", "bound": "alu",
-                        "achieved": fl / per_sc / 1e12, "peak": 1.25, "unit": "TFLOP/s",
-                        "frac": fl / per_sc / 1e12 / 1.25, "peak_source": fp64_peak_src,
-                        "algo_per_launch": fl}
+                        "achieved": fl / per_sc / 1e12, "peak": fp64_pk, "unit": "TFLOP/s",
+                        "frac": fl / per_sc / 1e12 / fp64_pk, "peak_source": fp64_src,
+                        "algo_per_launch": fl,
+                        "hbm_view": {"algo_bytes": bsc, "achieved_gbs": bsc / per_sc / 1e9,
+                                     "frac_of_hbm": bsc / per_sc / 1e9 / hbm}}
     if args.prec == "fp64":
         per_s = per_launch_ms["kron"] / 1e3
         algo = 2 * M * p["m"][0]
         achieved = algo / per_s / 1e12
-        kern, bound, unit, peak, peak_src = "k_mode_simt (kron)", "alu", "TFLOP/s", 1.25, fp64_peak_src
+        kern, bound, unit, peak, peak_src = ("k_mode_simt (kron, one mode product)", "alu",
+                                             "TFLOP/s", fp64_pk, fp64_src)
     elif args.prec == "fp64_tc":
         per_s = per_launch_ms["kron"] / 1e3
-        algo = OZ_PAIRS * 2 * M * p["m"][0]
+        algo = 2 * M * p["m"][0]
         achieved = algo / per_s / 1e12
-        bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
-        kern, bound, unit, peak = "k_oz_mode (kron, one mode product)", "tensor", "TFLOP/s", bf16
-        traffic = OZ_MODE_TRAFFIC if M == 65_536 else None
-        peak_src = ("measured" if peaks.get("bf16_tflops_sustained") else "fallback") + \
-            " sustained dense BF16 (cuBLAS)"
+        kern, bound, unit, peak, peak_src = ("k_oz_mode (kron, one mode product)", "tensor",
+                                             "TFLOP/s", bf16, bf16_src)
+        extra = {"digit_products": {"algo_per_launch": OZ_PAIRS * algo,
+                                    "achieved": OZ_PAIRS * achieved,
+                                    "frac": OZ_PAIRS * achieved / bf16,
+                                    "note": "the 36 BF16 digit-pair products issued per FP64 "
+                                            "product (the tensor pipe's own work)"},
+                 "fp64_equivalent": {"achieved": achieved, "peak": fp64_pk,
+                                     "frac": achieved / fp64_pk, "peak_source": fp64_src}}
     else:
         per_s = 2 * per_launch_ms["scatter"] / 1e3
-        algo = scatter_bytes(n, d, M, 1, 4, SN)
+        algo = scatter_bytes(n, d, M, 1, 4)
         achieved = algo / per_s / 1e9
         kern, bound, unit, peak, peak_src = ("k_scatter_cells + k_scatter_nodes (scatter)", "hbm",
                                              "GB/s", hbm, hbm_src + " HBM copy bandwidth")
+    roofline = {"kernel": kern, "bound": bound, "achieved": achieved, "peak": peak,
+                "peak_source": peak_src, "unit": unit, "frac": achieved / peak,
+                "traffic": None,
+                "traffic_note": "DRAM bytes per launch come from the ncu capture of this kernel "
+                                "on the same workload, not from this run",
+                "algo_per_launch": algo, "launch_us": per_s * 1e6}
+    roofline.update(extra)
     line = {
         "metric": METRIC, "value": t_step, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
@@ -586,17 +773,29 @@ def main():
                           "stage_us_per_iter": {k: round(1e3 * stage_total_ms[k] / prof_iters, 1)
                                                 for k in iter_stages if k in stage_total_ms}},
         "mvm": mvm,
+        "peaks": {"hbm_gbs": hbm, "hbm_source": hbm_src, "bf16_tflops_sustained": bf16,
+                  "fp64_tflops": fp64_pk, "tf32_tflops": gemm["tf32_tflops"],
+                  "gemm_source": fp64_src.replace("DGEMM", "GEMM (DGEMM; TF32 FP32 GEMM)")},
         "roofline_scatter": roof_scatter,
-        "roofline": {"kernel": kern, "bound": bound, "achieved": achieved,
-                     "peak": peak, "peak_source": peak_src, "unit": unit,
-                     "frac": achieved / peak, "traffic": traffic, "algo_per_launch": algo},
+        "roofline": roofline,
         "e2e": {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": (n * d + N) * 8,
                 "d2h_bytes_per_step": N * 8, "iters": it_e, "relres": rr_e},
         "gpu_launches": launches // args.steps,
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(p, it_last)
+        # the oracle leg: the GPU's results on a seeded subsample first (GPU
+        # work, untimed), then the oracle on the host cores
+        subs = []
+        for mode in dict.fromkeys([args.prec, "fp64"]):
+            subs.append(gpu_subsample_run(DSKI, p, mode, dev))
+        built = oracle_operator(p)
+        if "fp64" in compare and "iters" in compare["fp64"]:
+            ref_it, ref_src = compare["fp64"]["iters"], "this run's FP64 PCG iteration count"
+        else:
+            ref_it, ref_src = it_last, f"this run's {args.prec} PCG iteration count"
+        line["cpu_baseline"] = cpu_baseline(p, ref_it, ref_src, built=built)
+        line["oracle_check"] = oracle_check(p, built, xs, subs)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -227,6 +227,15 @@ int dski_logdet_slq(dski_handle h, pivchol_handle pc, int probes, int depth, uin
 int dski_mll_grad(dski_handle h, pivchol_handle pc, const double* y_dev, int probes,
                   uint64_t seed, double* mll_host, double* grad_host);
 
+/* Eq. 1, as dski_mll_grad with the batched PCG's stopping rule given:
+ * every column (the solve K~ a = y and the P probe solves) stops when its
+ * FP64 true relative residual is <= rtol (0 < rtol < 1), or after maxit
+ * iterations (then NOT_CONVERGED).  dski_mll_grad is this call with
+ * rtol = 1e-8, maxit = 100000.  Errors: as dski_mll_grad. */
+int dski_mll_grad_tol(dski_handle h, pivchol_handle pc, const double* y_dev, int probes,
+                      uint64_t seed, double rtol, int maxit, double* mll_host,
+                      double* grad_host);
+
 /* Prediction at n_star test points (Sec. 5: the mean, and the fast
  * predictive-variance estimate, that Bayesian optimisation evaluates at many
  * points).  The D-SKI cross-covariance of the test values / gradients with
@@ -288,20 +297,40 @@ int dski_profile(dski_handle h, int mode, double* ms_host, long long* launches_h
  * handles).  A host-side counter, incremented at every launch site. */
 long long dski_launch_count(void);
 
+/* Test aid for failure handling (the paper has no counterpart).  Every
+ * CTA of the tensor-core mode products (FP64_TC, and the MIXED modes' split
+ * contraction) waits on an mbarrier for its TMA loads with a bounded number
+ * of polls; when the budget runs out the CTA records a device error word,
+ * waits (with the full budget) for its loads to land, frees its tensor
+ * memory and returns, so the context stays usable.  The next dski_pcg_solve
+ * host check (at most 16 iterations later), dski_logdet_slq or
+ * dski_mll_grad then returns DSKI_ERR_TIMEOUT and clears the word.
+ *   polls >= 0  caps that first wait of every later product launched on
+ *               this handle at `polls` polls (0: it gives up at once);
+ *   polls < 0   restores the default budget (2^22 polls).
+ * The products of a launch whose wait gave up are not valid.
+ * Errors: ARG (NULL handle). */
+int dski_set_wait_budget(dski_handle h, int polls);
+
 /* The paper has no counterpart: this is dski_mvm for callers that cannot
  * allocate device memory -- applications whose device memory belongs to a
  * pool allocator that must see every allocation, real-time loops where
  * cudaMalloc's implicit device synchronisation is not allowed, plug-ins
  * whose host forbids device allocation after start-up.  Same arguments,
  * layouts and result as dski_mvm, but it calls no cudaMalloc, cudaFree or
- * allocating library routine: its temporaries (the permuted input and output,
- * N x s each, two grids, M x s each, in the mode's element size, and the
- * scatter's intermediate: in the MIXED modes with d = 2 its per-cell stencil
- * sums, 16 floats per cell of the grid and column; in FP64 mode with d >= 2
- * and s <= 4 its per-point coefficients, 8 (d = 2) or 32 (d = 3) doubles per
- * point and column) live in one fixed device array
+ * allocating library routine: its temporaries live in one fixed device array
  * of DSKI_NOALLOC_SCRATCH_BYTES (32 MiB) that the library reserves on every
- * GPU that loads it, until the process exits.
+ * GPU that loads it, until the process exits.  They are:
+ *   - the permuted input and output, N x s each, and two grids, M x s each,
+ *     in the mode's element size;
+ *   - the scatter's intermediate: with the cubic stencil, d = 2 and a MIXED
+ *     mode, its per-cell stencil sums, 16 floats per cell of the grid and
+ *     column; in FP64 mode with d >= 2 and s <= 4, its per-point
+ *     coefficients, 2 S (d = 2) or 2 S^2 (d = 3) doubles per point and
+ *     column, S the stencil width (4 cubic, 6 quintic);
+ *   - in the MIXED modes, the tensor-core mode products' split-contraction
+ *     partials (for m_k % 4 == 0, m_k <= 256): ceil(m_k/32) FP32 128 x 32
+ *     tiles per 128 x 32 output tile and column, for the largest mode.
  *   - Sizes that do not fit (each part padded to 256 bytes) are rejected with
  *     DSKI_ERR_ARG and a message; nothing runs.
  *   - The first call on a device looks up the array's device address (with

@@ -113,3 +113,29 @@ def mll_grad_hutchinson_z(op: DSKI, y, precond, Z, rtol=1e-12, maxit=20000):
             tr[i] += u @ dtheta_mvm(op, i, v)
     tr /= P
     return fit, tr, fit - 0.5 * tr
+
+
+def mll_grad_hutchinson_direct(op: DSKI, y, precond, Z, factored=False):
+    """The estimator of mll_grad_hutchinson_z with every solve taken from the
+    Cholesky factor of the dense K~ instead of PCG (exact solves, for systems
+    small enough to factor but slow to iterate on):
+      fit_i = 1/2 a^T dK~_i a,  a = K~^{-1} y,
+      tr_i  = mean_j (K~^{-1} z_j)^T dK~_i (M^{-1} z_j),
+      grad_i = fit_i - 1/2 tr_i.
+    factored=True forms K~ and dK~_i through dense_kgrad_factored."""
+    A = _dense_matrix(op, factored)
+    alpha = chol_solve(A, y)
+    Z = np.asarray(Z, np.float64)
+    U = chol_solve(A, Z)
+    V = np.column_stack([precond.solve(Z[:, j]) for j in range(Z.shape[1])])
+    fit = np.empty(op.d + 2)
+    tr = np.empty(op.d + 2)
+    for i in range(op.d + 2):
+        if factored:
+            dK = dtheta_dense_factored(op, i)
+            fit[i] = 0.5 * alpha @ (dK @ alpha)
+            tr[i] = np.mean(np.sum(U * (dK @ V), axis=0))
+        else:
+            fit[i] = 0.5 * alpha @ dtheta_mvm(op, i, alpha)
+            tr[i] = np.mean(np.sum(U * dtheta_mvm(op, i, V), axis=0))
+    return fit, tr, fit - 0.5 * tr

@@ -189,13 +189,26 @@ class DSKI:
                                                C.c_uint64(seed), C.byref(ld), C.byref(se)))
         return ld.value, se.value
 
-    def mll_grad(self, y, pc, probes=16, seed=777):
+    def mll_grad(self, y, pc, probes=16, seed=777, rtol=None, maxit=100000):
+        """Log marginal likelihood of Eq. 1 and its gradient (log l_1..d,
+        log s_f, log s_n).  rtol: the batched PCG's stopping rule (default
+        1e-8, dski_mll_grad); given, dski_mll_grad_tol runs with it."""
         Y = self._cols(y, torch.float64)
         mll = C.c_double()
         g = (C.c_double * (self.d + 2))()
-        _lib.check(_lib.load().dski_mll_grad(self.h, pc.ptr, _dptr(Y), int(probes),
-                                             C.c_uint64(seed), C.byref(mll), g))
+        if rtol is None:
+            _lib.check(_lib.load().dski_mll_grad(self.h, pc.ptr, _dptr(Y), int(probes),
+                                                 C.c_uint64(seed), C.byref(mll), g))
+        else:
+            _lib.check(_lib.load().dski_mll_grad_tol(self.h, pc.ptr, _dptr(Y), int(probes),
+                                                     C.c_uint64(seed), float(rtol), int(maxit),
+                                                     C.byref(mll), g))
         return mll.value, list(g)
+
+    def set_wait_budget(self, polls):
+        """Test aid: cap the first mbarrier wait of the tensor-core mode
+        products at `polls` polls (0: gives up at once; < 0: default)."""
+        _lib.check(_lib.load().dski_set_wait_budget(self.h, int(polls)))
 
     def predict(self, alpha, Xs, pc=None, with_grad=True, variance=True):
         """Mean (and gradient, block order) at the test points Xs (n* x d

@@ -345,7 +345,24 @@ extern "C" int dski_profile(dski_handle h, int mode, double* ms_host, long long*
 
 extern "C" long long dski_launch_count(void) { return g_launches.load(); }
 
+extern "C" int dski_set_wait_budget(dski_handle h, int polls) {
+  dski::clear_error();
+  if (!h) return dski::set_error(DSKI_ERR_ARG, "dski_set_wait_budget: NULL handle");
+  h->wait_budget = polls < 0 ? -1 : polls;
+  return DSKI_OK;
+}
+
 namespace dski {
+bool first_on_device(std::atomic<unsigned long long>* mask) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return true;   // unknown device: redo the (idempotent) set-up
+  }
+  const unsigned long long bit = 1ull << dev;
+  return (mask->fetch_or(bit) & bit) == 0;
+}
+
 int check_device_error(dski_handle h) {
   int e = 0;
   if (cudaMemcpyAsync(&e, h->dev_err.ptr, sizeof(int), cudaMemcpyDeviceToHost, h->stream) !=

@@ -15,6 +15,7 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <atomic>
 #include <type_traits>
 
 #include "../../include/dski.h"
@@ -134,6 +135,9 @@ struct dski_handle_ {
   dski::DevBuf s_part, s_tnpart, s_ticket, s_state, s_vec[12];
   // device error word (int): set by kernels whose bounded waits ran out
   dski::DevBuf dev_err;
+  // polls of the first mbarrier wait of the tensor-core mode products
+  // (dski_set_wait_budget; -1: the default budget)
+  int wait_budget = -1;
   // stage timers (NULL unless profiling is on)
   dski::Profiler* prof = nullptr;
 };
@@ -185,8 +189,10 @@ int mvm_pcg_fused(dski_handle h, double* P, const double* Z, const double* beta,
 // (dpart[q nblocks + block], nblocks = ceil(n / 256))
 int gather_scaled(dski_handle h, const double* grid, const double* vin, double* vout, int s,
                   double av, double ag, double nv, double ng, int stage, double* dpart = nullptr);
+// tc_ws: caller memory for the MIXED modes' tensor-core partials (the
+// largest mode_tc_tf32_ws_bytes over the modes); NULL = the handle's workspace
 int kron_internal(dski_handle h, void* g, void* tmp, int s, bool prec64, int dfactor,
-                  const void* dK, void** result);
+                  const void* dK, void** result, void* tc_ws = nullptr);
 
 // while on, the mode-product tile autotuner uses its heuristic (no timing, no
 // events) on this thread -- for callers that must not create resources
@@ -202,9 +208,13 @@ int fft_circulant_size(int m);
 int fft_prepare(dski_handle h);
 int mode_fft(dski_handle h, int k, const double* X, double* Y, long long R, int s, double scale);
 
-// tensor-core mode product (kron_tc.cu): TF32 (three = false) or 3xTF32
+// tensor-core mode product (kron_tc.cu): TF32 (three = false) or 3xTF32.
+// ws: caller memory for the split contraction's FP32 partials
+// (mode_tc_tf32_ws_bytes bytes); NULL = the handle's workspace, grown on demand
 int mode_tc_tf32(dski_handle h, const float* X, const float* Khi, const float* Klo, float* Y,
-                 int m, long long R, int s, float scale, bool three);
+                 int m, long long R, int s, float scale, bool three, float* ws = nullptr);
+// bytes of split-contraction partials one mode_tc_tf32 call needs (0: none)
+size_t mode_tc_tf32_ws_bytes(int m, long long R, int s);
 // FP64_TC mode products (kron_tc.cu): digits and row exponents of a factor,
 // and one mode product;
 // a factor's digit planes take kOzDigits x m x m BF16 values
@@ -246,6 +256,10 @@ auto with_stencil(dski_handle h, F&& fn) {
   if (h->sw == 6) return fn(std::integral_constant<int, 6>{});
   return fn(std::integral_constant<int, 4>{});
 }
+// true the first time it is called for the current device with this mask
+// (one bit per device ordinal < 64): per-device, once-only set-up such as
+// cudaFuncSetAttribute, which acts on the current device only
+bool first_on_device(std::atomic<unsigned long long>* mask);
 // read and clear the device error word: DSKI_OK, or DSKI_ERR_TIMEOUT if a
 // kernel's bounded wait ran out since the last check (synchronises)
 int check_device_error(dski_handle h);

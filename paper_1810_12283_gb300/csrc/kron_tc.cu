@@ -202,7 +202,7 @@ template <int NMMA>
 __global__ void __launch_bounds__(128) k_mode_tc_tf32_split(
     const __grid_constant__ CUtensorMap tHi, const __grid_constant__ CUtensorMap tLo,
     const float* __restrict__ X, float* __restrict__ Y, float* __restrict__ P, int m, long long R,
-    int KS, float scale, int* __restrict__ err) {
+    int KS, float scale, int* __restrict__ err, uint32_t wait1) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sAh = smem;
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(128) k_mode_tc_tf32_split(
   constexpr uint32_t idesc = tc::instr_desc(tc::kFmtTF32, TC_M, TC_N);
   int ok = 1;
   if (tid == 0) {
-    if (tc::mbar_wait(full, 0, WAIT_LIMIT)) {
+    if (tc::mbar_wait(full, 0, wait1)) {
       tc::fence_after();
       const uint32_t aH = tc::smem_u32(sAh), aL = tc::smem_u32(sAl);
       const uint32_t bH = tc::smem_u32(sBh), bL = tc::smem_u32(sBl);
@@ -324,10 +324,25 @@ __global__ void __launch_bounds__(128) k_mode_tc_tf32_split(
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 
 // One mode product on the tensor cores (mixed modes).  Returns DSKI_OK or CUDA.
+static bool tf32_split_path(int m) { return m % 4 == 0 && m <= 256; }
+
+// budget of the first mbarrier wait of a tensor-core product (see
+// dski_set_wait_budget)
+static uint32_t first_wait_polls(dski_handle h) {
+  return h->wait_budget < 0 ? WAIT_LIMIT : (uint32_t)h->wait_budget;
+}
+
+size_t mode_tc_tf32_ws_bytes(int m, long long R, int s) {
+  if (!tf32_split_path(m)) return 0;
+  const int KS = (m + TC_KC - 1) / TC_KC;
+  const long long tiles = (long long)s * ((m + TC_M - 1) / TC_M) * ((R + TC_N - 1) / TC_N);
+  return (size_t)tiles * KS * TC_M * TC_N * 4;
+}
+
 int mode_tc_tf32(dski_handle h, const float* X, const float* Khi, const float* Klo, float* Y,
-                 int m, long long R, int s, float scale, bool three) {
+                 int m, long long R, int s, float scale, bool three, float* ws) {
   auto enc = tensor_map_encoder();
-  if (enc && m % 4 == 0 && m <= 256) {
+  if (enc && tf32_split_path(m)) {
     // split contraction over a cluster, K by TMA
     CUtensorMap tHi, tLo;
     const cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)m};
@@ -342,16 +357,18 @@ int mode_tc_tf32(dski_handle h, const float* X, const float* Khi, const float* K
       if (r != CUDA_SUCCESS)
         return set_error(DSKI_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     }
-    static bool attr_split = false;
-    if (!attr_split) {
+    static std::atomic<unsigned long long> attr_split{0};
+    if (first_on_device(&attr_split)) {
       cudaFuncSetAttribute(k_mode_tc_tf32_split<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TS_SMEM);
       cudaFuncSetAttribute(k_mode_tc_tf32_split<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, TS_SMEM);
-      attr_split = true;
     }
     const int KS = (m + TC_KC - 1) / TC_KC;
-    const long long tiles = (long long)s * ((m + TC_M - 1) / TC_M) * ((R + TC_N - 1) / TC_N);
-    if (h->ozP.ensure((size_t)tiles * KS * TC_M * TC_N * 4))
-      return set_error(DSKI_ERR_ALLOC, "tensor-core workspace allocation failed");
+    float* part = ws;
+    if (!part) {
+      if (h->ozP.ensure(mode_tc_tf32_ws_bytes(m, R, s)))
+        return set_error(DSKI_ERR_ALLOC, "tensor-core workspace allocation failed");
+      part = h->ozP.as<float>();
+    }
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)((m + TC_M - 1) / TC_M), (unsigned)((R + TC_N - 1) / TC_N),
                        (unsigned)(s * KS));
@@ -369,19 +386,18 @@ int mode_tc_tf32(dski_handle h, const float* X, const float* Khi, const float* K
     cfg.numAttrs = 2;
     StageScope sc(h, ST_KRON, h->stream);
     const cudaError_t e =
-        three ? cudaLaunchKernelEx(&cfg, k_mode_tc_tf32_split<3>, tHi, tLo, X, Y, h->ozP.as<float>(),
-                                   m, R, KS, scale, h->dev_err.as<int>())
-              : cudaLaunchKernelEx(&cfg, k_mode_tc_tf32_split<1>, tHi, tLo, X, Y, h->ozP.as<float>(),
-                                   m, R, KS, scale, h->dev_err.as<int>());
+        three ? cudaLaunchKernelEx(&cfg, k_mode_tc_tf32_split<3>, tHi, tLo, X, Y, part, m, R, KS,
+                                   scale, h->dev_err.as<int>(), first_wait_polls(h))
+              : cudaLaunchKernelEx(&cfg, k_mode_tc_tf32_split<1>, tHi, tLo, X, Y, part, m, R, KS,
+                                   scale, h->dev_err.as<int>(), first_wait_polls(h));
     if (e != cudaSuccess)
       return set_error(DSKI_ERR_CUDA, "TF32 mode product launch: %s", cudaGetErrorString(e));
     return DSKI_OK;
   }
-  static bool attr_set = false;
-  if (!attr_set) {
+  static std::atomic<unsigned long long> attr_set{0};
+  if (first_on_device(&attr_set)) {
     cudaFuncSetAttribute(k_mode_tc_tf32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     cudaFuncSetAttribute(k_mode_tc_tf32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-    attr_set = true;
   }
   dim3 grd((unsigned)((m + TC_M - 1) / TC_M), (unsigned)((R + TC_N - 1) / TC_N), (unsigned)s);
   StageScope sc(h, ST_KRON, h->stream);
@@ -575,6 +591,7 @@ struct OzKArgs {
   int Mrows, mp, KS;
   double scale;
   int* err;
+  uint32_t wait1;   // polls of the first wait (the TMA of A's digit planes)
 };
 
 // Y_q[j][r] = scale sum_i A[j][i] xs_q[i] X_q[r][i] (or its transpose): A's
@@ -692,7 +709,7 @@ __global__ void __launch_bounds__(128) k_oz_mode(const __grid_constant__ CUtenso
   constexpr uint32_t idesc = tc::instr_desc(tc::kFmtBF16, Z_M, Z_N);
   int ok = 1;
   if (tid == 0) {
-    if (tc::mbar_wait(full, 0, WAIT_LIMIT)) {
+    if (tc::mbar_wait(full, 0, a.wait1)) {
       tc::fence_after();
       const uint32_t aB = sbase;
       const uint32_t bB = aB + OZ_S * Z_A;
@@ -854,11 +871,9 @@ int oz_gemm(dski_handle h, const OzGemm& g, int stage) {
     if (r != CUDA_SUCCESS)
       return set_error(DSKI_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   }
-  static bool attr_set = false;
-  if (!attr_set) {
+  static std::atomic<unsigned long long> attr_set{0};
+  if (first_on_device(&attr_set))
     cudaFuncSetAttribute(k_oz_mode, cudaFuncAttributeMaxDynamicSharedMemorySize, Z_SMEM);
-    attr_set = true;
-  }
   OzKArgs a{};
   a.X = g.X;
   a.ldx = g.ldx;
@@ -875,6 +890,7 @@ int oz_gemm(dski_handle h, const OzGemm& g, int stage) {
   a.KS = (g.mp + Z_KC - 1) / Z_KC;   // <= 8
   a.scale = g.scale;
   a.err = h->dev_err.as<int>();
+  a.wait1 = first_wait_polls(h);
   const long long tiles = (long long)g.s * ((g.Mrows + Z_M - 1) / Z_M) * ((g.R + Z_N - 1) / Z_N);
   DevBuf& ws = g.workspace ? *g.workspace : h->ozP;
   if (ws.ensure((size_t)tiles * a.KS * Z_TILE * sizeof(longlong2)))

@@ -932,7 +932,7 @@ int scatter_fused(dski_handle h, const void* vin, void* g, int s, bool prec64, v
 // d mode products g -> result (ping-pong between g and tmp).  Factor k is
 // K_k, except k == dfactor which uses dK (same precision as the path).
 int kron_internal(dski_handle h, void* g, void* tmp, int s, bool prec64, int dfactor,
-                  const void* dK, void** result) {
+                  const void* dK, void** result, void* tc_ws) {
   cudaStream_t st = h->stream;
   void* cur = g;
   void* nxt = tmp;
@@ -960,7 +960,7 @@ int kron_internal(dski_handle h, void* g, void* tmp, int s, bool prec64, int dfa
       // mixed modes: tensor cores, TF32 or 3xTF32
       DSKI_TRY(mode_tc_tf32(h, (const float*)cur, h->Khi[k].as<float>(), h->Klo[k].as<float>(),
                             (float*)nxt, h->m[k], R, s, (float)scale,
-                            h->prec == DSKI_MIXED_3XTF32));
+                            h->prec == DSKI_MIXED_3XTF32, static_cast<float*>(tc_ws)));
     } else {
       const float* K = k == dfactor ? (const float*)dK : h->K32[k].as<float>();
       mode_simt<float>(h, (const float*)cur, K, (float*)nxt, h->m[k], R, s, (float)scale,

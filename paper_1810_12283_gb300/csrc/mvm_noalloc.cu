@@ -9,14 +9,15 @@
 // point allocates nothing; the array below is reserved when the library is
 // loaded, on every GPU that loads it, and stays reserved until the process
 // exits.
+#include <algorithm>
 #include <mutex>
 
 #include "dski_internal.cuh"
 
 namespace {
 
-// Layout of one call: [vin | vout | gridA | gridB | scatter intermediate],
-// each part padded to 256 bytes.
+// Layout of one call: [vin | vout | gridA | gridB | scatter intermediate |
+// tensor-core partials], each part padded to 256 bytes.
 constexpr size_t kScratchBytes = size_t(32) << 20;   // DSKI_NOALLOC_SCRATCH_BYTES
 static_assert(kScratchBytes == (size_t)DSKI_NOALLOC_SCRATCH_BYTES, "keep dski.h in sync");
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -65,12 +66,17 @@ extern "C" int dski_mvm_noalloc(dski_handle h, const void* v_dev, void* out_dev,
   const size_t vbytes = (size_t)h->N * s * es;
   const size_t gbytes = (size_t)h->M * s * es;
   const size_t abytes = scatter_ws_bytes(h, s, f64);
-  const size_t need = 2 * pad256(vbytes) + 2 * pad256(gbytes) + pad256(abytes);
+  // MIXED modes: the split-contraction partials of the largest mode product
+  size_t tbytes = 0;
+  if (!f64)
+    for (int k = 0; k < h->d; ++k)
+      tbytes = std::max(tbytes, mode_tc_tf32_ws_bytes(h->m[k], h->M / h->m[k], s));
+  const size_t need = 2 * pad256(vbytes) + 2 * pad256(gbytes) + pad256(abytes) + pad256(tbytes);
   if (need > kScratchBytes)
     return set_error(DSKI_ERR_ARG,
                      "dski_mvm_noalloc: needs %zu scratch bytes for s = %d, the fixed limit is %zu "
-                     "(2 N s + 2 M s elements and the scatter intermediate); use dski_mvm or "
-                     "fewer columns",
+                     "(2 N s + 2 M s elements, the scatter intermediate and the tensor-core "
+                     "partials); use dski_mvm or fewer columns",
                      need, s, kScratchBytes);
   const char* a = (const char*)v_dev;
   const char* b = (const char*)out_dev;
@@ -92,6 +98,7 @@ extern "C" int dski_mvm_noalloc(dski_handle h, const void* v_dev, void* out_dev,
   void* gA = p + 2 * pad256(vbytes);
   void* gB = p + 2 * pad256(vbytes) + pad256(gbytes);
   void* ab = p + 2 * pad256(vbytes) + 2 * pad256(gbytes);
+  void* tp = p + 2 * pad256(vbytes) + 2 * pad256(gbytes) + pad256(abytes);
   // Every stage writes its whole output before the next reads it, so nothing
   // in the array has to start at zero.  The tile autotuner stays off here.
   struct NoTune {
@@ -101,7 +108,7 @@ extern "C" int dski_mvm_noalloc(dski_handle h, const void* v_dev, void* out_dev,
   DSKI_TRY(permute_in(h, v_dev, vin, s, f64, h->stream));
   DSKI_TRY(scatter_internal_ws(h, vin, gA, s, f64, abytes ? ab : nullptr));
   void* res = nullptr;
-  DSKI_TRY(kron_internal(h, gA, gB, s, f64, -1, nullptr, &res));
+  DSKI_TRY(kron_internal(h, gA, gB, s, f64, -1, nullptr, &res, tbytes ? tp : nullptr));
   DSKI_TRY(gather_internal(h, res, vin, vout, s, f64));
   DSKI_TRY(permute_out(h, vout, out_dev, s, f64, h->stream));
   return DSKI_OK;

@@ -44,6 +44,11 @@ struct ColState {
   double *ahist, *bhist;
   int depth;
   int s;
+  // the inner passes run a perturbed operator (mixed modes, FFT products):
+  // a non-positive p^T q there ends the pass instead of breaking down, and
+  // the restart from the FP64 true residual refines x against the exact
+  // operator
+  int soft;
 };
 
 constexpr int CG_THREADS = 256;
@@ -145,7 +150,7 @@ __device__ void alpha_finish(const double* tot, ColState& cs) {
     if (cs.active[cc]) {
       const double t = tot[cc];
       if (!(t > 0.0) || !isfinite(t) || !isfinite(cs.rz[cc])) {
-        cs.bd[cc] = 1;
+        if (!cs.soft || !isfinite(cs.rz[cc])) cs.bd[cc] = 1;
         cs.active[cc] = 0;
       } else {
         al = cs.rz[cc] / t;
@@ -458,6 +463,7 @@ int cg_run(dski_handle h, CgRun& run) {
   // while Lanczos coefficients are recorded: the record covers the first
   // pass, which must then run the full depth.
   const double eta2 = (depth == 0 && (mixed || h->kuu_fft)) ? 1e-8 : 0.0;
+  cs.soft = eta2 > 0.0 ? 1 : 0;
   const double* dis = run.pc ? run.pc->dis.as<double>() : nullptr;
   const dim3 grd(nbx, s);
   const dim3 grv(std::min(nbv, nbx), s);

@@ -259,10 +259,18 @@ extern "C" int dski_logdet_slq(dski_handle h, pivchol_handle pc, int probes, int
 
 extern "C" int dski_mll_grad(dski_handle h, pivchol_handle pc, const double* y_dev, int probes,
                              uint64_t seed, double* mll_host, double* grad_host) {
+  return dski_mll_grad_tol(h, pc, y_dev, probes, seed, 1e-8, 100000, mll_host, grad_host);
+}
+
+extern "C" int dski_mll_grad_tol(dski_handle h, pivchol_handle pc, const double* y_dev,
+                                 int probes, uint64_t seed, double rtol, int maxit,
+                                 double* mll_host, double* grad_host) {
   clear_error();
   if (!h || !pc || !y_dev) return set_error(DSKI_ERR_ARG, "dski_mll_grad: NULL argument");
   if (pc->h != h) return set_error(DSKI_ERR_ARG, "dski_mll_grad: preconditioner of another handle");
   if (probes < 2 || probes > 256) return set_error(DSKI_ERR_ARG, "dski_mll_grad: probes in 2..256");
+  if (!(rtol > 0.0) || !(rtol < 1.0) || maxit < 1)
+    return set_error(DSKI_ERR_ARG, "dski_mll_grad: rtol in (0, 1) and maxit >= 1");
   const long long N = h->N;
   const long long M = h->M;
   const int d = h->d;
@@ -280,7 +288,7 @@ extern "C" int dski_mll_grad(dski_handle h, pivchol_handle pc, const double* y_d
   DSKI_TRY(permute_in(h, y_dev, Bi, 1, true, st));
   CgRun run;
   SlqOut out;
-  int rc = probe_solve(h, pc, probes, depth, seed, 1e-8, 100000, run, Bi, Xi, 1, out);
+  int rc = probe_solve(h, pc, probes, depth, seed, rtol, maxit, run, Bi, Xi, 1, out);
   if (rc != DSKI_OK) return rc;
   // V = [alpha, M^-1 z_1 .. M^-1 z_P]
   double* V = Vb.as<double>();

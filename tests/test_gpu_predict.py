@@ -3,10 +3,12 @@ against the FP64 oracle (oracle/predict.py).
 
 * mean and gradient at test points, mu* = [W*; dW*] K_UU [W; dW]^T alpha, for
   the same alpha, within the normwise bound of the product evaluated term by
-  term: 64 u || |B*| K_UU |B|^T |alpha| || / ||mu*|| (Higham, Sec. 3.5; u = 2^-53
-  on the FP64 path, 2^-48 for FP64_TC's digit products).  alpha = K~^-1 y of
-  an ill-conditioned system carries entries far above mu*, so this condition
-  number, not 1, sets the scale;
+  term: 64 u || |B*| K_UU |B|^T |alpha| || / ||mu*|| (Higham, Sec. 3.5;
+  u = 2^-53 on every path: prediction runs in FP64 arithmetic in every mode,
+  and FP64_TC's digit products are held to the FP64 bar).  alpha = K~^-1 y
+  of an ill-conditioned system carries entries far above mu*, so this
+  condition number, not 1, sets the scale.  Every element is also held to
+  the componentwise bound gamma_K (|B*| K_UU |B|^T |alpha|)_i;
 * the preconditioner variance estimate s_f^2 - k_x^T M^-1 k_x with the
   GPU's own pivots rebuilt in the oracle: 1e-9 relative;
 * d = 2 and d = 3, grid-form (d = 2, M < N) and Q1-form preconditioners, and
@@ -16,7 +18,8 @@ import numpy as np
 import pytest
 
 from synth import workloads as W
-from tests._gpu_helpers import gpu_op, oracle_op, need_gpu, rel, torch
+from tests._gpu_helpers import (gpu_op, oracle_op, need_gpu, rel, torch, elem_err,
+                                elem_tolerance)
 
 pytestmark = pytest.mark.gpu
 
@@ -28,11 +31,16 @@ def _test_points(p, k, seed):
     return rng.uniform(lo, hi, (k, len(p["m"])))
 
 
-def _mean_tolerance(orc, alpha, Xs, u):
+def _abs_mean(orc, alpha, Xs):
+    """|B*| K_UU |B|^T |alpha|: the mean's terms in absolute value."""
     from oracle.dski import interp_matrix, kuu_apply
     Bs = abs(interp_matrix(Xs, orc.grid))
-    a = Bs @ kuu_apply(orc.grid, orc.ell, orc.sf, (abs(orc.B).T @ np.abs(alpha))[:, None])[:, 0]
+    return Bs @ kuu_apply(orc.grid, orc.ell, orc.sf, (abs(orc.B).T @ np.abs(alpha))[:, None])[:, 0]
+
+
+def _mean_tolerance(orc, alpha, Xs, u):
     from oracle.predict import dski_mean
+    a = _abs_mean(orc, alpha, Xs)
     ref = dski_mean(orc, alpha, Xs)
     return max(1e-13, 64 * u * np.linalg.norm(a) / np.linalg.norm(ref))
 
@@ -51,17 +59,21 @@ def test_predictive_mean_and_gradient(make, prec):
     alpha = np.linalg.solve(orc.dense(), p["y"])
     Xs = _test_points(p, 37, 11)
     want = dski_mean(orc, alpha, Xs)
-    tol = _mean_tolerance(orc, alpha, Xs, 2.0**-48 if prec == "fp64_tc" else 2.0**-53)
+    tol = _mean_tolerance(orc, alpha, Xs, 2.0**-53)
+    etol = elem_tolerance(orc, "fp64")
     op = gpu_op(p, prec)
     mean, var = op.predict(torch.tensor(alpha, device="cuda"), torch.tensor(Xs, device="cuda"))
     assert var is None
     assert rel(mean.cpu().numpy(), want) <= tol, (rel(mean.cpu().numpy(), want), tol)
+    ee = elem_err(mean.cpu().numpy(), want, _abs_mean(orc, alpha, Xs))
+    assert ee <= etol, (ee, etol)
     # a well-conditioned alpha (random): the same bound is tight here
     a2 = np.random.default_rng(5).normal(size=orc.N)
-    tol2 = _mean_tolerance(orc, a2, Xs, 2.0**-48 if prec == "fp64_tc" else 2.0**-53)
+    tol2 = _mean_tolerance(orc, a2, Xs, 2.0**-53)
     m2, _ = op.predict(torch.tensor(a2, device="cuda"), torch.tensor(Xs, device="cuda"))
     got2 = rel(m2.cpu().numpy(), dski_mean(orc, a2, Xs))
     assert got2 <= tol2 and tol2 < 1e-9, (got2, tol2)
+    assert elem_err(m2.cpu().numpy(), dski_mean(orc, a2, Xs), _abs_mean(orc, a2, Xs)) <= etol
     # values only
     m0, _ = op.predict(torch.tensor(alpha, device="cuda"), torch.tensor(Xs, device="cuda"),
                        with_grad=False)

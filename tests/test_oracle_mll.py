@@ -110,3 +110,21 @@ def test_surface_subsample_gradient_matches_central_differences():
         fd = (mll_dense(op_at(th + e), p["y"], factored=True)
               - mll_dense(op_at(th - e), p["y"], factored=True)) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * abs(g[i]), (i, fd, g[i])
+
+
+def test_direct_hutchinson_equals_pcg_hutchinson_with_same_probes():
+    """The dense-Cholesky form of the same-probe estimator equals the PCG
+    form (solves to 1e-13) on the same probes, with K~ formed either way."""
+    from oracle.mll import mll_grad_hutchinson_direct
+    from oracle.probes import preconditioned_probes
+    X, grid, theta, y = _setup(n=12, seed=6)
+    op = _make(theta, X, grid, 2.0)
+    L, _, _ = pivoted_cholesky(op.kgrad_diag(), op.kgrad_row, 6)
+    Pc = QRPreconditioner(L, op.noise)
+    Z = preconditioned_probes(17, Pc, 5)
+    fit, tr, g = mll_grad_hutchinson_z(op, y, Pc, Z, rtol=1e-13)
+    for factored in (False, True):
+        fit2, tr2, g2 = mll_grad_hutchinson_direct(op, y, Pc, Z, factored=factored)
+        assert np.allclose(fit2, fit, rtol=1e-9, atol=0)
+        assert np.allclose(tr2, tr, rtol=1e-9, atol=1e-12)
+        assert np.allclose(g2, g, rtol=1e-9, atol=1e-12)

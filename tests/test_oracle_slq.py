@@ -100,3 +100,21 @@ def test_preconditioned_rademacher_within_standard_errors():
     Pc = QRPreconditioner(L, op.noise)
     est, se, _, _ = slq_logdet_z(op.mvm, Pc, preconditioned_probes(5, Pc, 24), depth=30)
     assert abs(est - chol_logdet(A)) < 4 * se + 1e-6 * abs(chol_logdet(A))
+
+
+def test_splitmix64_matches_published_reference_outputs():
+    """Pin the generator itself (not only its two forms against each other):
+    the first outputs of the stream for two seeds are the values published
+    with the reference implementation (tests/golden/splitmix64.txt).  A wrong
+    constant in the increment or the finaliser changes every one of them."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "splitmix64.txt")
+    rows = [list(map(int, ln.split())) for ln in open(path)
+            if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 2
+    for seed, *expected in rows:
+        assert splitmix64_stream(seed, len(expected)) == expected
+        assert [splitmix64_at(seed, k + 1) for k in range(len(expected))] == expected
+        # the vectorised form used to build probe matrices: sign of the top bit
+        Z = rademacher(seed, len(expected), 1)[:, 0]
+        assert list(Z) == [1.0 if v >> 63 == 0 else -1.0 for v in expected]
