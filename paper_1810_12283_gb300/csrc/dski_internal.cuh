@@ -132,7 +132,7 @@ struct dski_handle_ {
   dski::DevBuf gridA, gridB, vin, vout, scratch;
   // solver workspace: reduction partials, last-block tickets (zeroed at
   // allocation), per-column scalar state and solver vectors
-  dski::DevBuf s_part, s_tnpart, s_ticket, s_state, s_vec[12];
+  dski::DevBuf s_part, s_tnpart, s_ticket, s_state, s_vec[13];
   // device error word (int): set by kernels whose bounded waits ran out
   dski::DevBuf dev_err;
   // polls of the first mbarrier wait of the tensor-core mode products

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <type_traits>
 
 #include "dski_internal.cuh"
 #include "interp.cuh"
@@ -42,6 +43,17 @@ static MvmGeo make_geo(dski_handle h) {
 }
 
 namespace {
+
+template <class T>
+struct T2v {
+  T x, y;
+};
+// two consecutive values (8-byte aligned for float: one 64-bit load)
+__device__ __forceinline__ T2v<float> ld2(const float* p) {
+  const float2 f = __ldg(reinterpret_cast<const float2*>(p));
+  return {f.x, f.y};
+}
+__device__ __forceinline__ T2v<double> ld2(const double* p) { return {__ldg(p), __ldg(p + 1)}; }
 
 // ------------------------------------------------------------- scatter ----
 // Grid node u receives sum_i [w_i(u) v_i^0 + sum_p dw_{i,p}(u) v_i^p] over the
@@ -330,7 +342,8 @@ __global__ void __launch_bounds__(256) k_scatter_ab(MvmGeo g, const int* __restr
 // p = z + beta p is formed first and written back (fused PCG direction).
 template <class T, int CB, int G>
 __global__ void __launch_bounds__(256) k_scatter_cells(const int* __restrict__ cell_start,
-                                                       const T* __restrict__ wt, T* __restrict__ v,
+                                                       const T* __restrict__ frac, T ih0, T ih1,
+                                                       T* __restrict__ v,
                                                        T* __restrict__ S, int s, long long N,
                                                        int ncell, T sv, T sg,
                                                        const double* __restrict__ z,
@@ -347,10 +360,18 @@ __global__ void __launch_bounds__(256) k_scatter_cells(const int* __restrict__ c
   if (live) {
     const int js = cell_start[c], je = cell_start[c + 1];
     for (int j = js + g; j < je; j += G) {
+      // the point's weights from its two cell fractions (the 12 bytes of
+      // geometry a point carries, instead of a 64-byte weight table):
+      // w[0..3] = phi, w[4..7] = phi' / h in dimension 0, w[8..15] likewise in 1
       T w[16];
-      const T* wj = wt + (long long)j * 16;
+      const T2v<T> fr = ld2(frac + 2 * (long long)j);
+      keys4<T>(fr.x, w, w + 4);
+      keys4<T>(fr.y, w + 8, w + 12);
 #pragma unroll
-      for (int k = 0; k < 16; ++k) w[k] = wj[k];
+      for (int k = 0; k < 4; ++k) {
+        w[4 + k] *= ih0;
+        w[12 + k] *= ih1;
+      }
 #pragma unroll
       for (int q = 0; q < CB; ++q) {
         if (q0 + q >= s) break;
@@ -429,11 +450,13 @@ __global__ void __launch_bounds__(256) k_scatter_nodes(MvmGeo geo, const T* __re
 template <class T, int CB, int G>
 void launch_scatter_cells(dski_handle h, T* v, T* S, int s, T sv, T sg, const double* z,
                           const double* beta, cudaStream_t st) {
+  static_assert(std::is_same<T, float>::value, "the per-cell scatter reads the FP32 fractions");
   const int ncell = h->mc[0] * h->mc[1];
   const long long threads = (long long)ncell * G;
   const dim3 grd((unsigned)((threads + 255) / 256), (unsigned)((s + CB - 1) / CB));
-  k_scatter_cells<T, CB, G><<<grd, 256, 0, st>>>(h->cell_start.as<int>(), wt_table<T>(h), v, S, s,
-                                                  h->N, ncell, sv, sg, z, beta);
+  k_scatter_cells<T, CB, G><<<grd, 256, 0, st>>>(h->cell_start.as<int>(), h->frac32.as<float>(),
+                                                  (T)(1.0 / h->h[0]), (T)(1.0 / h->h[1]), v, S,
+                                                  s, h->N, ncell, sv, sg, z, beta);
 }
 
 // -------------------------------------------------------------- gather ----
@@ -464,7 +487,18 @@ __global__ void __launch_bounds__(256) k_gather(MvmGeo g, const int* __restrict_
     }
   }
   T w[D][S], dw[D][S];
-  {
+  if constexpr (std::is_same<T, float>::value) {
+    // FP32: the weights from the point's D cell fractions (wt is the FP32
+    // fraction array, n x D) -- the geometry the byte model counts, instead
+    // of a 2 S D-value weight table per point
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      stencil_weights<S, T>(__ldg(wt + (long long)j * D + k), w[k], dw[k]);
+      const T ih = (T)g.invh[k];
+#pragma unroll
+      for (int o = 0; o < S; ++o) dw[k][o] *= ih;
+    }
+  } else {
     const T* wj = wt + (long long)j * (2 * S * D);
 #pragma unroll
     for (int k = 0; k < D; ++k)
@@ -670,6 +704,8 @@ struct GatherScale {
 template <class T, int D, int CB, int S>
 void launch_gather(dski_handle h, const MvmGeo& g, const T* wt, const T* grid, const T* v,
                    T* out, int s, cudaStream_t st, const GatherScale& gs) {
+  // FP32 gathers evaluate the weights from the FP32 fractions
+  if constexpr (std::is_same<T, float>::value) wt = h->frac32.as<float>();
   dim3 grd((unsigned)((h->n + 255) / 256), (unsigned)((s + CB - 1) / CB));
   StageScope sc(h, gs.stage, st);
   k_gather<T, D, CB, S><<<grd, 256, 0, st>>>(g, h->cell.as<int>(), wt, grid, v, out, s, h->n,
@@ -812,12 +848,14 @@ namespace {
 template <class T, int CB>
 void scatter_cells_d2(dski_handle h, T* v, T* S, T* grid, int s, T sv, T sg, const double* z,
                       const double* beta, cudaStream_t st) {
+  // group size: about four points per lane, so that the butterfly over the
+  // group (16 CB values per level) stays short against the points' loads
   const int ncell = h->mc[0] * h->mc[1];
   const double per = (double)h->n / std::max(1, ncell);
-  if (per <= 2.0) launch_scatter_cells<T, CB, 2>(h, v, S, s, sv, sg, z, beta, st);
-  else if (per <= 4.0) launch_scatter_cells<T, CB, 4>(h, v, S, s, sv, sg, z, beta, st);
-  else if (per <= 8.0) launch_scatter_cells<T, CB, 8>(h, v, S, s, sv, sg, z, beta, st);
-  else if (per <= 16.0) launch_scatter_cells<T, CB, 16>(h, v, S, s, sv, sg, z, beta, st);
+  if (per <= 8.0) launch_scatter_cells<T, CB, 2>(h, v, S, s, sv, sg, z, beta, st);
+  else if (per <= 16.0) launch_scatter_cells<T, CB, 4>(h, v, S, s, sv, sg, z, beta, st);
+  else if (per <= 32.0) launch_scatter_cells<T, CB, 8>(h, v, S, s, sv, sg, z, beta, st);
+  else if (per <= 64.0) launch_scatter_cells<T, CB, 16>(h, v, S, s, sv, sg, z, beta, st);
   else launch_scatter_cells<T, CB, 32>(h, v, S, s, sv, sg, z, beta, st);
   const dim3 gn((unsigned)((h->M + 255) / 256), (unsigned)((s + CB - 1) / CB));
   k_scatter_nodes<T, CB><<<gn, 256, 0, st>>>(make_geo(h), S, grid, s, h->M, ncell);

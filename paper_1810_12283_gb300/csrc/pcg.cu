@@ -635,8 +635,49 @@ int cg_run(dski_handle h, CgRun& run) {
 
   int its = 0, restarts = 0, nact = 0;
   const int max_restarts = mixed ? 200 : 64;
+  // Passes on a perturbed operator (cs.soft): refinement from the FP64 true
+  // residual converges only while the operator's error stays below the
+  // system's smallest eigenvalue.  The x of the smallest true residual is
+  // kept, and the solve stops once three passes in a row have not improved
+  // on it; x is then restored to that iterate.
+  double* Xbest = cs.soft ? wbuf(h->s_vec[12], Ns) : nullptr;
+  if (cs.soft && !Xbest) return set_error(DSKI_ERR_ALLOC, "dski_pcg_solve: workspace allocation failed");
+  std::vector<double> best_rn2(s, HUGE_VAL), cur_rn2(s), bn2(s);
+  std::vector<int> stale(s, 0);
+  bool diverged = false;
+  auto track_best = [&](bool first) -> int {   // after a true residual (stream synchronised)
+    if (!cs.soft) return DSKI_OK;
+    if ((first && cudaMemcpy(bn2.data(), cs.bn2, s * 8, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+        cudaMemcpy(cur_rn2.data(), cs.rn2, s * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return set_error(DSKI_ERR_CUDA, "dski_pcg_solve: %s", cudaGetErrorString(cudaGetLastError()));
+    bool stop = true;
+    for (int c = 0; c < s; ++c) {
+      if (cur_rn2[c] < best_rn2[c]) {
+        best_rn2[c] = cur_rn2[c];
+        stale[c] = 0;
+        if (cudaMemcpyAsync(Xbest + (size_t)c * N, run.X + (size_t)c * N, (size_t)N * 8,
+                            cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+          return set_error(DSKI_ERR_CUDA, "dski_pcg_solve: copy failed");
+      } else {
+        ++stale[c];
+      }
+      const bool done = cur_rn2[c] <= tol2 * bn2[c];
+      if (!done && stale[c] < 3) stop = false;
+    }
+    if (stop && !first) {
+      // restore the best iterate of every column that has moved away from it
+      for (int c = 0; c < s; ++c)
+        if (cur_rn2[c] > best_rn2[c] &&
+            cudaMemcpyAsync(run.X + (size_t)c * N, Xbest + (size_t)c * N, (size_t)N * 8,
+                            cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+          return set_error(DSKI_ERR_CUDA, "dski_pcg_solve: copy failed");
+      diverged = true;
+    }
+    return DSKI_OK;
+  };
   DSKI_TRY(true_residual(1));
   DSKI_TRY(read_nactive(&nact));
+  DSKI_TRY(track_best(true));
   while (nact > 0) {
     DSKI_TRY(precond_z(1));   // p = M^-1 r
     while (its < run.maxit) {
@@ -648,6 +689,13 @@ int cg_run(dski_handle h, CgRun& run) {
     }
     DSKI_TRY(true_residual(0));
     DSKI_TRY(read_nactive(&nact));
+    DSKI_TRY(track_best(false));
+    if (diverged) {
+      // the restored iterates' true residuals, for the results below
+      DSKI_TRY(true_residual(0));
+      DSKI_TRY(read_nactive(&nact));
+      break;
+    }
     if (nact == 0 || its >= run.maxit || restarts >= max_restarts) break;
     ++restarts;
     cs.depth = 0;   // the Lanczos record covers the first pass only

@@ -20,6 +20,9 @@ shape, size and structure of the experiment it stands in for:
                   [200, 5000], 128-feature random Fourier targets, l ~ U[0.05, 0.3],
                   48^2 or 24^3 grids over [-0.1, 1.1]^d.       (seeds 4000+i)
 * ``surface3d_big`` the surface3d generator at 50,000 + 5,000 points.  (seed 5)
+* ``franke2d``    n = 2,000 uniform points in [0,1]^2 with Franke's test function
+                  and its gradient (the preconditioning experiment of App. C);
+                  96x96 grid over [-0.1, 1.1]^2.                     (seed 6)
 
 Every vector is in block order [values (n); d/dx_1 (n); ...; d/dx_d (n)].
 """
@@ -157,6 +160,31 @@ def multi_instance(i, seed_base=4000):
     m = 48 if d == 2 else 24
     return _problem(X, y, (m,) * d, (-0.1,) * d, (1.1,) * d, ell, 1.0, 1e-3, 1e-3,
                     rank=32, rtol=1e-6, name=f"multi-{i}")
+
+
+def franke(X):
+    """Franke's bivariate test function (Franke 1979) and its gradient."""
+    x, y = 9 * X[:, 0], 9 * X[:, 1]
+    t1 = 0.75 * np.exp(-((x - 2) ** 2 + (y - 2) ** 2) / 4)
+    t2 = 0.75 * np.exp(-((x + 1) ** 2) / 49 - (y + 1) / 10)
+    t3 = 0.5 * np.exp(-((x - 7) ** 2 + (y - 3) ** 2) / 4)
+    t4 = -0.2 * np.exp(-((x - 4) ** 2) - (y - 7) ** 2)
+    f = t1 + t2 + t3 + t4
+    fx = 9 * (t1 * (-(x - 2) / 2) + t2 * (-2 * (x + 1) / 49) + t3 * (-(x - 7) / 2)
+              + t4 * (-2 * (x - 4)))
+    fy = 9 * (t1 * (-(y - 2) / 2) + t2 * (-1 / 10) + t3 * (-(y - 3) / 2) + t4 * (-2 * (y - 7)))
+    return f, fx, fy
+
+
+def franke2d(n=2000, seed=6, ell=0.1, noise=1e-2, grid=96):
+    """The preconditioning experiment's 2-D workload (App. C): n points
+    uniform in [0,1]^2 with Franke's function and its gradient, SE output
+    scale 1, one length scale and noise; grid over [-0.1, 1.1]^2."""
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(0.0, 1.0, (n, 2))
+    f, fx, fy = franke(X)
+    return _problem(X, np.concatenate([f, fx, fy]), (grid, grid), (-0.1, -0.1), (1.1, 1.1),
+                    ell, 1.0, noise, noise, rank=100, rtol=1e-4, name=f"franke2d-n{n}")
 
 
 def subsample(p, n, seed=0):

@@ -51,25 +51,31 @@ def test_single_process_reduce_is_identity():
 
 
 def test_algorithmic_byte_counts():
+    """The MVM's algorithmic HBM bytes: v read by the scatter and by the noise
+    term, out written (3 N s elements), the geometry (cell id + d fractions,
+    g = 4 + b d bytes) read by scatter and gather; the grid stays in L2."""
     import bench
-    # terrain MVM in FP64: v read twice and out written (3 N), grid written and
-    # read (2 M), geometry (cell id + 8 d weights) read twice
-    n, d, M = 100_000, 2, 65_536
+    n, d = 100_000, 2
     N = n * (d + 1)
-    assert bench.mvm_bytes(n, d, M, 1, 8) == 3 * N * 8 + 2 * M * 8 + 2 * n * (4 + 8 * 8 * d)
-    assert bench.precond_bytes(N, 100, 1) == 2 * N * 100 * 8 + 3 * N * 8
+    assert bench.geometry_bytes(2, 4) == 12 and bench.geometry_bytes(3, 4) == 16
+    assert bench.mvm_bytes(n, d, 1, 4) == 3 * N * 4 + 2 * n * 12
+    assert bench.mvm_bytes(n, d, 1, 8) == 3 * N * 8 + 2 * n * (4 + 8 * d)
+    # the terrain value of the byte model: ~6 MB per FP32 MVM
+    assert abs(bench.mvm_bytes(n, d, 1, 4) - 6.0e6) < 1e3
+    # weight tables (S weights + S derivative weights per dimension) are extra traffic
+    assert bench.weight_table_bytes(d, 4) == 4 * 2 * 4 * d
 
 
 def test_scatter_byte_count():
     import bench
     n, d, M = 100_000, 2, 65_536
-    assert bench.scatter_bytes(n, d, M, 1, 8) == 3 * n * 8 + n * (4 + 16 * 8) + M * 8
+    assert bench.scatter_bytes(n, d, M, 1, 8) == 3 * n * 8 + n * (4 + 2 * 8) + M * 8
 
 
 def test_gather_byte_count():
     import bench
     n, d, M = 100_000, 2, 65_536
-    assert bench.gather_bytes(n, d, M, 1, 4) == M * 4 + 2 * 3 * n * 4 + n * (4 + 16 * 4)
+    assert bench.gather_bytes(n, d, M, 1, 4) == M * 4 + 2 * 3 * n * 4 + n * (4 + 2 * 4)
 
 
 def test_scatter_flop_count():
@@ -83,11 +89,8 @@ def test_quintic_stencil_counts_and_workload_names():
     import bench
     n, d, M = 1000, 2, 256 * 256
     assert bench.stencil_nodes("cubic") == 4 and bench.stencil_nodes("quintic") == 6
-    assert bench.scatter_bytes(n, d, M, 1, 8, 6) - bench.scatter_bytes(n, d, M, 1, 8) == \
-        n * (2 * 6 - 2 * 4) * d * 8
+    assert bench.weight_table_bytes(d, 8, 6) - bench.weight_table_bytes(d, 8) == (2 * 6 - 2 * 4) * d * 8
     assert bench.scatter_flops(n, d, 6) == n * (3 + 6 * 3 + 6 + 36 * 4)
-    assert bench.mvm_bytes(n, d, M, 1, 8, 6) - bench.mvm_bytes(n, d, M, 1, 8) == \
-        2 * n * 8 * (12 - 8) * d
     name = bench.workload_name(100_000)
     assert "interp" not in name and "kuu" not in name
     assert bench.workload_name(100_000, "quintic", "fft").endswith("interp=quintic kuu=fft")
