@@ -665,7 +665,7 @@ def main():
     ap.add_argument("--franke-maxit", type=int, default=50000)
     ap.add_argument("--multi", action="store_true",
                     help="instead of the solve step: the 256-instance uneven workload")
-    ap.add_argument("--multi-workers", type=int, default=32)
+    ap.add_argument("--multi-workers", type=int, default=8)
     ap.add_argument("--surface-maxit", type=int, default=20000)
     ap.add_argument("--kuu", default="dense", choices=["dense", "fft"],
                     help="products with K_UU: dense Kronecker factors or Toeplitz/FFT")

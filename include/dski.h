@@ -326,8 +326,8 @@ int dski_set_wait_budget(dski_handle h, int polls);
  *   - the scatter's intermediate: with the cubic stencil, d = 2 and a MIXED
  *     mode, its per-cell stencil sums, 16 floats per cell of the grid and
  *     column; in FP64 mode with d >= 2 and s <= 4, its per-point
- *     coefficients, 2 S (d = 2) or 2 S^2 (d = 3) doubles per point and
- *     column, S the stencil width (4 cubic, 6 quintic);
+ *     sum-factorised coefficients, 2 S (d = 2) or 2 S^2 (d = 3) doubles per
+ *     point and column, S the stencil width (4 cubic, 6 quintic);
  *   - in the MIXED modes, the tensor-core mode products' split-contraction
  *     partials (for m_k % 4 == 0, m_k <= 256): ceil(m_k/32) FP32 128 x 32
  *     tiles per 128 x 32 output tile and column, for the largest mode.

@@ -377,7 +377,9 @@ int ts_nn(dski_handle h, const double* X, double alpha, const double* xscale, do
           const double* A, int p, const double* C, int q, double* Y, const double* rowscale) {
   const long long N = h->N;
   const size_t smem = (size_t)p * q * sizeof(double);
-  if (smem > 96 * 1024) return set_error(DSKI_ERR_ARG, "ts_nn: p*q too large (%d x %d)", p, q);
+  // C is staged in shared memory: up to 200 KB (GB300: 227 KB per block),
+  // which holds the 128 x 128 factor of a rank-128 preconditioner
+  if (smem > 200 * 1024) return set_error(DSKI_ERR_ARG, "ts_nn: p*q too large (%d x %d)", p, q);
   const int nbx = (int)std::min<long long>((N + 255) / 256, 4LL * h->sm_count);
   StageScope sc(h, ST_PRECOND, h->stream);
   if (q <= 4) {

@@ -900,8 +900,8 @@ int scatter_fused(dski_handle h, const void* vin, void* g, int s, bool prec64, v
     if (s == 1)
       scatter_cells_d2<float, 1>(h, (float*)vin, (float*)S, (float*)g, s, 1.f, 1.f, nullptr,
                                  nullptr, st);
-    else
-      scatter_cells_d2<float, 4>(h, (float*)vin, (float*)S, (float*)g, s, 1.f, 1.f, nullptr,
+    else   // two columns per pass: 16 x 4 accumulators capped occupancy at 2 blocks per SM
+      scatter_cells_d2<float, 2>(h, (float*)vin, (float*)S, (float*)g, s, 1.f, 1.f, nullptr,
                                  nullptr, st);
     DSKI_LAUNCHED();
     return DSKI_OK;

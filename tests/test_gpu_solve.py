@@ -55,6 +55,30 @@ def test_pivoted_cholesky_parity(make, rank):
     op.close()
 
 
+def test_rank_128_preconditioner():
+    """The largest rank the boundary accepts (Sec. 3.3), in 3-D where the
+    QR form's 128 x 128 factors are staged in shared memory: log|M| equals
+    the oracle's QR form of the GPU's own factor, and PCG with it solves the
+    system against the dense direct solve."""
+    need_gpu()
+    p = W.small3d(60, m=9, seed=8, nv=1e-2, ng=1e-2)
+    op = gpu_op(p, "fp64")
+    orc = oracle_op(p)
+    pc = op.pivchol(128)
+    assert pc.rank == 128
+    Lg, _ = pc.export()
+    Lg = Lg.cpu().numpy().T
+    assert abs(pc.logdet() - _oracle_pc(orc, Lg).logdet()) <= 1e-10 * abs(pc.logdet())
+    A = orc.dense()
+    x, it, rr = op.solve(torch.tensor(p["y"], device="cuda"), pc, rtol=1e-9, maxit=20000)
+    xn = x.cpu().numpy()
+    assert rr[0] <= 1e-9
+    xd = np.linalg.solve(A, p["y"])
+    assert np.linalg.norm(A @ (xn - xd)) / np.linalg.norm(p["y"]) <= 2e-9
+    pc.close()
+    op.close()
+
+
 def test_pcg_first_iterates_equal_oracle():
     need_gpu()
     from oracle.solve import pcg, pivoted_cholesky
