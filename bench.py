@@ -23,6 +23,7 @@ CPU oracle instead (the reference arm of this project).
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -549,6 +550,76 @@ def run_precond_sweep(args):
     return 0
 
 
+def run_surface(args):
+    """The implicit-surface workloads (points on a bumpy sphere, 64^3 grid over
+    [-1.4, 1.4]^3, l = 0.2, noise 1e-4, rank-100 pivoted Cholesky):
+      * 27,500 points: the PCG solve of y to relative residual 1e-8 and the
+        SLQ log determinant with 31 probes at Lanczos depth 30;
+      * 55,000 points: the log marginal likelihood of Eq. 1 and its gradient
+        with respect to (log l_1..3, log s_f, log s_n) through the autograd
+        Function (one batched PCG of the solve and 16 probes to --surface-rtol,
+        the SLQ log determinant and the grid adjoint).
+    Each step is timed with the host clock around device-synchronised calls
+    (inputs resident on the device).  Inputs are seeded and synthetic."""
+    import torch
+    from paper_1810_12283_gb300 import DSKI, mll_function
+    from synth import workloads as W
+    dev = torch.device("cuda", 0)
+    prec = args.prec
+    out = {"mode": prec}
+
+    def build(p):
+        X = torch.tensor(p["X"], device=dev)
+        return DSKI(X, p["m"], p["lo"], p["hi"], p["ell"], p["sf"], p["noise_value"],
+                    p["noise_grad"], prec=prec)
+
+    def clock(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    p = W.surface3d()
+    op = build(p)
+    pc, t_pc = clock(lambda: op.pivchol(RANK))
+    y = torch.tensor(p["y"], device=dev)
+    (x, it, rr), t_solve = clock(lambda: op.solve(y, pc, rtol=RTOL, maxit=args.surface_solve_maxit,
+                                                  allow_not_converged=True))
+    (ld, se), t_slq = clock(lambda: op.logdet(pc, probes=31, depth=30, seed=777))
+    out["surface3d_27500"] = {"pivchol_s": t_pc, "solve": {"iters": it[0], "relres": rr[0],
+                                                           "s": t_solve, "rtol": RTOL},
+                              "slq": {"logdet": ld, "stderr": se, "probes": 31, "depth": 30,
+                                      "s": t_slq}}
+    pc.close()
+    op.close()
+    q = W.surface3d_big()
+    op = build(q)
+    d = op.d
+    theta = torch.tensor([math.log(v) for v in q["ell"]] + [math.log(q["sf"]),
+                         0.5 * math.log(q["noise_value"])], dtype=torch.float64,
+                         requires_grad=True)
+    yq = torch.tensor(q["y"], device=dev)
+
+    def grad_step():
+        L = mll_function(theta, op, yq, rank=RANK, probes=16, seed=777, rtol=args.surface_rtol,
+                         maxit=args.surface_solve_maxit)
+        (g,) = torch.autograd.grad(L, theta)
+        return float(L.detach()), g.tolist()
+
+    try:
+        (L, g), t_grad = clock(grad_step)
+        out["surface3d_55000_grad"] = {"mll": L, "grad": g, "s": t_grad, "probes": 16,
+                                       "rtol": args.surface_rtol,
+                                       "theta": "log l_1..3, log s_f, log s_n"}
+    except Exception as e:   # noqa: BLE001 -- reported
+        out["surface3d_55000_grad"] = {"error": str(e)}
+    op.close()
+    print(json.dumps({"metric": "implicit-surface workloads: solve to 1e-8, 31-probe SLQ, "
+                                "55,000-point gradient of Eq. 1", **out}), flush=True)
+    return 0
+
+
 MULTI_INSTANCES = 256
 MULTI_ORACLE_SAMPLE = 16
 
@@ -663,6 +734,11 @@ def main():
                          "(Franke, 2000 points) and a preconditioner-rank sweep on the 3-D "
                          "surface workload")
     ap.add_argument("--franke-maxit", type=int, default=50000)
+    ap.add_argument("--surface", action="store_true",
+                    help="instead of the solve step: the implicit-surface solve, SLQ and the "
+                         "55,000-point gradient")
+    ap.add_argument("--surface-rtol", type=float, default=1e-8)
+    ap.add_argument("--surface-solve-maxit", type=int, default=600000)
     ap.add_argument("--multi", action="store_true",
                     help="instead of the solve step: the 256-instance uneven workload")
     ap.add_argument("--multi-workers", type=int, default=8)
@@ -686,6 +762,8 @@ def main():
         return run_precond_sweep(args)
     if args.multi:
         return run_multi(args)
+    if args.surface:
+        return run_surface(args)
     if args.impl == "reference":
         return run_reference(args, p)
 

@@ -191,18 +191,20 @@ class DSKI:
 
     def mll_grad(self, y, pc, probes=16, seed=777, rtol=None, maxit=100000):
         """Log marginal likelihood of Eq. 1 and its gradient (log l_1..d,
-        log s_f, log s_n).  rtol: the batched PCG's stopping rule (default
-        1e-8, dski_mll_grad); given, dski_mll_grad_tol runs with it."""
+        log s_f, log s_n).  rtol, maxit: the batched PCG's stopping rule
+        (defaults 1e-8 and 100,000: dski_mll_grad; otherwise
+        dski_mll_grad_tol)."""
         Y = self._cols(y, torch.float64)
         mll = C.c_double()
         g = (C.c_double * (self.d + 2))()
-        if rtol is None:
+        if rtol is None and maxit == 100000:
             _lib.check(_lib.load().dski_mll_grad(self.h, pc.ptr, _dptr(Y), int(probes),
                                                  C.c_uint64(seed), C.byref(mll), g))
         else:
             _lib.check(_lib.load().dski_mll_grad_tol(self.h, pc.ptr, _dptr(Y), int(probes),
-                                                     C.c_uint64(seed), float(rtol), int(maxit),
-                                                     C.byref(mll), g))
+                                                     C.c_uint64(seed),
+                                                     float(1e-8 if rtol is None else rtol),
+                                                     int(maxit), C.byref(mll), g))
         return mll.value, list(g)
 
     def set_wait_budget(self, polls):

@@ -22,7 +22,7 @@ class MarginalLikelihood(torch.autograd.Function):
     operator's ratio to the value-row noise)."""
 
     @staticmethod
-    def forward(ctx, theta, op, y, rank, probes, seed):
+    def forward(ctx, theta, op, y, rank, probes, seed, rtol=None, maxit=100000):
         th = [float(v) for v in theta.detach().cpu().tolist()]
         d = op.d
         if len(th) != d + 2:
@@ -33,7 +33,7 @@ class MarginalLikelihood(torch.autograd.Function):
         op.set_hypers(ell, sf, s2, s2 * op.noise_ratio)
         pc = op.pivchol(rank)
         try:
-            mll, grad = op.mll_grad(y, pc, probes=probes, seed=seed)
+            mll, grad = op.mll_grad(y, pc, probes=probes, seed=seed, rtol=rtol, maxit=maxit)
         finally:
             pc.close()
         ctx.save_for_backward(torch.tensor(grad, dtype=theta.dtype, device=theta.device))
@@ -42,10 +42,12 @@ class MarginalLikelihood(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out):
         (g,) = ctx.saved_tensors
-        return grad_out * g, None, None, None, None, None
+        return grad_out * g, None, None, None, None, None, None, None
 
 
-def mll_function(theta, op, y, rank=100, probes=16, seed=777):
-    """Differentiable log marginal likelihood (Eq. 1) of the D-SKI model."""
+def mll_function(theta, op, y, rank=100, probes=16, seed=777, rtol=None, maxit=100000):
+    """Differentiable log marginal likelihood (Eq. 1) of the D-SKI model.
+    rtol / maxit: the batched PCG's stopping rule (default: dski_mll_grad's
+    1e-8 and 100,000 iterations)."""
     _lib.load()
-    return MarginalLikelihood.apply(theta, op, y, rank, probes, seed)
+    return MarginalLikelihood.apply(theta, op, y, rank, probes, seed, rtol, maxit)

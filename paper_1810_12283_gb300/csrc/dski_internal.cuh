@@ -182,13 +182,15 @@ int scatter_fused(dski_handle h, const void* vin, void* g, int s, bool prec64, v
 // PCG: P <- Z + beta P fused into the FP64 MVM Q = K~ P (when pcg_fusable);
 // with dpart, the gather leaves per-block partial sums of p^T q there
 bool pcg_fusable(dski_handle h, int s);
+struct CgFinish;   // a CG finisher folded into a gather (solve_internal.cuh)
 int mvm_pcg_fused(dski_handle h, double* P, const double* Z, const double* beta, double* Q,
-                  int s, double* dpart = nullptr);
+                  int s, double* dpart = nullptr, const CgFinish* fin = nullptr);
 // FP64 gather: vout^0 = av (B grid)^0 + nv vin^0, vout^p = ag (B grid)^p + ng vin^p;
 // with dpart, per-block partial sums of vin^T vout per column
 // (dpart[q nblocks + block], nblocks = ceil(n / 256))
 int gather_scaled(dski_handle h, const double* grid, const double* vin, double* vout, int s,
-                  double av, double ag, double nv, double ng, int stage, double* dpart = nullptr);
+                  double av, double ag, double nv, double ng, int stage, double* dpart = nullptr,
+                  const CgFinish* fin = nullptr);
 // tc_ws: caller memory for the MIXED modes' tensor-core partials (the
 // largest mode_tc_tf32_ws_bytes over the modes); NULL = the handle's workspace
 int kron_internal(dski_handle h, void* g, void* tmp, int s, bool prec64, int dfactor,

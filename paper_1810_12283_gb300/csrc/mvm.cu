@@ -14,6 +14,7 @@
 
 #include "dski_internal.cuh"
 #include "interp.cuh"
+#include "solve_internal.cuh"
 
 namespace dski {
 
@@ -470,7 +471,8 @@ __global__ void __launch_bounds__(256) k_gather(MvmGeo g, const int* __restrict_
                                                 const T* __restrict__ grid,
                                                 const T* __restrict__ v, T* __restrict__ out,
                                                 int s, int n, long long N, long long M, T nv,
-                                                T ng, T av, T ag, double* __restrict__ dpart) {
+                                                T ng, T av, T ag, double* __restrict__ dpart,
+                                                CgFinish fin) {
   const int jt = blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = jt < n;
   const int j = live ? jt : n - 1;   // dead threads redo the last point, write nothing
@@ -598,6 +600,22 @@ __global__ void __launch_bounds__(256) k_gather(MvmGeo g, const int* __restrict_
       for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t += red[ww][threadIdx.x];
       dpart[(long long)(q0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
     }
+    // a folded CG finisher: the last block completes the partial sums
+    // (fixed block order) and updates the device scalars
+    if (fin.kind >= 0 && last_block(fin.ticket, gridDim.x * gridDim.y)) {
+      __shared__ double sh[32];
+      __shared__ double tot[CG_MAXS];
+      if (fin.kind == 0) {
+        sum_columns(dpart, gridDim.x, fin.cs.s, 1, 0, tot, sh);
+        alpha_finish(tot, fin.cs);
+      } else {
+        sum_columns(fin.part2, gridDim.x, fin.cs.s, 1, 0, tot, sh);
+        update_finish(tot, fin.cs, sh);
+        __syncthreads();   // active flags settled before beta reads them
+        sum_columns(dpart, gridDim.x, fin.cs.s, 1, 0, tot, sh);
+        beta_finish(tot, fin.cs, 0);
+      }
+    }
   }
 }
 
@@ -699,6 +717,7 @@ struct GatherScale {
   double nv = 0.0, ng = 0.0;   // multiply v on value / gradient rows
   int stage = ST_GATHER;
   double* dpart = nullptr;     // per-block partial sums of v^T out (FP64 only)
+  CgFinish fin{};              // finisher folded into the last block (with dpart)
 };
 
 template <class T, int D, int CB, int S>
@@ -710,7 +729,7 @@ void launch_gather(dski_handle h, const MvmGeo& g, const T* wt, const T* grid, c
   StageScope sc(h, gs.stage, st);
   k_gather<T, D, CB, S><<<grd, 256, 0, st>>>(g, h->cell.as<int>(), wt, grid, v, out, s, h->n,
                                           (long long)h->N, (long long)h->M, (T)gs.nv, (T)gs.ng,
-                                          (T)gs.av, (T)gs.ag, gs.dpart);
+                                          (T)gs.av, (T)gs.ag, gs.dpart, gs.fin);
 }
 
 template <class T, int D>
@@ -1041,7 +1060,10 @@ int mvm_internal(dski_handle h, const void* vin, void* vout, int s, bool prec64)
 }
 
 int gather_scaled(dski_handle h, const double* grid, const double* vin, double* vout, int s,
-                  double av, double ag, double nv, double ng, int stage, double* dpart) {
+                  double av, double ag, double nv, double ng, int stage, double* dpart,
+                  const CgFinish* fin) {
+  if (fin && fin->kind >= 0 && !dpart)
+    return set_error(DSKI_ERR_ARG, "a folded CG finisher needs the gather's partial sums");
   const MvmGeo geo = make_geo(h);
   GatherScale gs;
   gs.av = av;
@@ -1050,6 +1072,7 @@ int gather_scaled(dski_handle h, const double* grid, const double* vin, double* 
   gs.ng = ng;
   gs.stage = stage;
   gs.dpart = dpart;
+  if (fin) gs.fin = *fin;
   const double* fr = h->W64.as<double>();
   switch (h->d) {
     case 1: gather_dispatch<double, 1>(h, geo, fr, grid, vin, vout, s, h->stream, &gs); break;
@@ -1086,7 +1109,7 @@ int gather_internal(dski_handle h, const void* grid, const void* vin, void* vout
 bool pcg_fusable(dski_handle h, int s) { return f64_vectors(h) && h->d >= 2 && s <= 4; }
 
 int mvm_pcg_fused(dski_handle h, double* P, const double* Z, const double* beta, double* Q,
-                  int s, double* dpart) {
+                  int s, double* dpart, const CgFinish* fin) {
   const size_t gbytes = (size_t)h->M * s * 8;
   if (h->gridA.ensure(gbytes) || h->gridB.ensure(gbytes))
     return set_error(DSKI_ERR_ALLOC, "grid workspace allocation failed (%zu bytes)", gbytes);
@@ -1095,7 +1118,8 @@ int mvm_pcg_fused(dski_handle h, double* P, const double* Z, const double* beta,
   DSKI_TRY(kron_internal(h, h->gridA.ptr, h->gridB.ptr, s, true, -1, nullptr, &res));
   if (!dpart) return gather_internal(h, res, P, Q, s, true);
   // the gather also leaves per-block partial sums of p^T q
-  return gather_scaled(h, (const double*)res, P, Q, s, 1.0, 1.0, h->nv, h->ng, ST_GATHER, dpart);
+  return gather_scaled(h, (const double*)res, P, Q, s, 1.0, 1.0, h->nv, h->ng, ST_GATHER, dpart,
+                       fin);
 }
 
 int permute_in(dski_handle h, const void* v_user, void* v_int, int s, bool f64, cudaStream_t st) {

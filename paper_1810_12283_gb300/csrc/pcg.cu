@@ -38,42 +38,12 @@
 namespace dski {
 namespace {
 
-struct ColState {
-  double *bn2, *rn2, *rz, *rz0, *alpha, *beta, *target;
-  int *active, *iters, *bd, *nactive;
-  double *ahist, *bhist;
-  int depth;
-  int s;
-  // the inner passes run a perturbed operator (mixed modes, FFT products):
-  // a non-positive p^T q there ends the pass instead of breaking down, and
-  // the restart from the FP64 true residual refines x against the exact
-  // operator
-  int soft;
-};
-
 constexpr int CG_THREADS = 256;
 constexpr int CG_UNROLL = 4;   // elements per thread and step in the streaming kernels
 
 __device__ __forceinline__ bool cg_last(unsigned* ticket) {
   return last_block(ticket, gridDim.x * gridDim.y);
 }
-
-// In the last block: tot[c] = sum over bx of part[(c nb + bx) stride + off]
-// for every column c < s.  The block's threads split the partials and a
-// fixed tree combines them (deterministic).  tot is shared, length >= s.
-__device__ void sum_columns(const double* part, int nb, int s, int stride, int off,
-                            double* tot, double* sh) {
-  for (int c = 0; c < s; ++c) {
-    double v = 0.0;
-    for (int bx = threadIdx.x; bx < nb; bx += blockDim.x)
-      v += part[((long long)c * nb + bx) * stride + off];
-    v = block_sum(v, sh);
-    if (threadIdx.x == 0) tot[c] = v;
-  }
-  __syncthreads();
-}
-
-constexpr int CG_MAXS = 264;   // >= 1 + the largest probe count (256)
 
 // r = b - q, y = dis .* r; ||b||^2 (first call) and ||r||^2; (re)activates
 // the columns whose residual misses the target.
@@ -119,64 +89,6 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_init(
     nact = (int)block_sum((double)nact, sh);
     if (threadIdx.x == 0) *cs.nactive = nact;
   }
-}
-
-// From the column sums tot[c] = r^T z: at (re)start rz (and rz0 once), else
-// beta = (r^T z)_new / rz for active columns (recorded), 0 for the others.
-__device__ void beta_finish(const double* tot, ColState& cs, int init) {
-  for (int cc = threadIdx.x; cc < cs.s; cc += blockDim.x) {
-    const double t = tot[cc];
-    if (init) {
-      cs.rz[cc] = t;
-      cs.beta[cc] = 0.0;
-      if (cs.rz0[cc] == 0.0) cs.rz0[cc] = t;
-    } else if (cs.active[cc]) {
-      const double be = t / cs.rz[cc];
-      cs.beta[cc] = be;
-      cs.rz[cc] = t;
-      const int k = cs.iters[cc] - 1;
-      if (cs.bhist && k >= 0 && k < cs.depth) cs.bhist[(long long)k * cs.s + cc] = be;
-    } else {
-      cs.beta[cc] = 0.0;
-    }
-  }
-}
-
-// From tot[c] = p^T q: alpha = r^T z / p^T q for active columns (recorded),
-// breakdown (non-positive or non-finite) deactivates a column.
-__device__ void alpha_finish(const double* tot, ColState& cs) {
-  for (int cc = threadIdx.x; cc < cs.s; cc += blockDim.x) {
-    double al = 0.0;
-    if (cs.active[cc]) {
-      const double t = tot[cc];
-      if (!(t > 0.0) || !isfinite(t) || !isfinite(cs.rz[cc])) {
-        if (!cs.soft || !isfinite(cs.rz[cc])) cs.bd[cc] = 1;
-        cs.active[cc] = 0;
-      } else {
-        al = cs.rz[cc] / t;
-        const int k = cs.iters[cc];
-        if (cs.ahist && k < cs.depth) cs.ahist[(long long)k * cs.s + cc] = al;
-      }
-    }
-    cs.alpha[cc] = al;
-  }
-}
-
-// From tot[c] = ||r||^2 after the update: record it, count the iteration,
-// deactivate the columns that met their target; the active count.
-__device__ void update_finish(const double* tot, ColState& cs, double* sh) {
-  int nact = 0;
-  for (int cc = threadIdx.x; cc < cs.s; cc += blockDim.x) {
-    if (cs.active[cc]) {
-      const double t = tot[cc];
-      cs.rn2[cc] = t;
-      cs.iters[cc] += 1;
-      if (!(t > cs.target[cc])) cs.active[cc] = 0;
-    }
-    nact += cs.active[cc];
-  }
-  nact = (int)block_sum((double)nact, sh);
-  if (threadIdx.x == 0) *cs.nactive = nact;
 }
 
 // z = dis .* (y - Q1 C) (preconditioned) or z = r (plain); r^T z.
@@ -373,26 +285,6 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg_update(
   }
 }
 
-// One-block finishers of the fused path: the block partials come from the
-// MVM's gather (p^T q; kind 0: alpha), and from the preconditioner's scatter
-// pass (||r||^2 after the update) with its gather (r^T z, at part2; kind 1:
-// the update's bookkeeping, then beta).
-__global__ void __launch_bounds__(CG_THREADS) k_cg_finish(const double* __restrict__ part,
-                                                          const double* __restrict__ part2,
-                                                          int nb, int kind, ColState cs) {
-  __shared__ double sh[32];
-  __shared__ double tot[CG_MAXS];
-  sum_columns(part, nb, cs.s, 1, 0, tot, sh);
-  if (kind == 0) {
-    alpha_finish(tot, cs);
-    return;
-  }
-  update_finish(tot, cs, sh);
-  __syncthreads();   // active flags settled before beta reads them
-  sum_columns(part2, nb, cs.s, 1, 0, tot, sh);
-  beta_finish(tot, cs, 0);
-}
-
 }  // namespace
 
 // ----------------------------------------------------------------- engine --
@@ -535,12 +427,12 @@ int cg_run(dski_handle h, CgRun& run) {
   double* dpZ = fusedg ? dpU + (size_t)nbp * 4 : nullptr;
   auto iteration = [&]() -> int {
     if (fusedg) {
-      DSKI_TRY(mvm_pcg_fused(h, P, Z, cs.beta, Q, s, dpA));
-      {
-        StageScope sc(h, ST_PCGVEC, st);
-        k_cg_finish<<<1, CG_THREADS, 0, st>>>(dpA, nullptr, nbp, 0, cs);
-      }
-      DSKI_LAUNCHED();
+      // alpha from p^T q in the last block of the MVM's gather
+      CgFinish fa;
+      fa.kind = 0;
+      fa.cs = cs;
+      fa.ticket = tk;
+      DSKI_TRY(mvm_pcg_fused(h, P, Z, cs.beta, Q, s, dpA, &fa));
       CgUpdate up;
       up.x = run.X;
       up.p = P;
@@ -548,12 +440,14 @@ int cg_run(dski_handle h, CgRun& run) {
       up.alpha = cs.alpha;
       up.active = cs.active;
       up.dpart = dpU;
-      DSKI_TRY(grid_precond_apply(h, run.pc, R, Z, s, &up, dpZ));
-      {
-        StageScope sc(h, ST_PCGVEC, st);
-        k_cg_finish<<<1, CG_THREADS, 0, st>>>(dpU, dpZ, nbp, 1, cs);
-      }
-      DSKI_LAUNCHED();
+      // the update's bookkeeping (||r||^2 from the scatter pass) and beta
+      // (r^T z) in the last block of the preconditioner's gather
+      CgFinish fb;
+      fb.kind = 1;
+      fb.cs = cs;
+      fb.ticket = tk;
+      fb.part2 = dpU;
+      DSKI_TRY(grid_precond_apply(h, run.pc, R, Z, s, &up, dpZ, &fb));
       return DSKI_OK;
     }
     if (mixed) {

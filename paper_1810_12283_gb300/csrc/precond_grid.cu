@@ -264,8 +264,8 @@ int grid_precond_build(dski_handle h, pivchol_handle pc, const int* piv_dev, con
 
 // Z = M^-1 R for s columns (internal layout) through the grid form.
 int grid_precond_apply(dski_handle h, pivchol_handle pc, const double* R, double* Z, int s,
-                       const CgUpdate* up, double* dpart_rz) {
-  if ((up || dpart_rz) && s > 4)
+                       const CgUpdate* up, double* dpart_rz, const CgFinish* fin) {
+  if ((up || dpart_rz || fin) && s > 4)
     return set_error(DSKI_ERR_ARG, "fused CG steps in the preconditioner need s <= 4");
   const int r = pc->rank;
   const int m0 = h->m[0], m1 = h->m[1];
@@ -337,7 +337,7 @@ int grid_precond_apply(dski_handle h, pivchol_handle pc, const double* R, double
     DSKI_LAUNCHED();
     // Z = (R - B h') ./ noise
     DSKI_TRY(gather_scaled(h, hp, R + (size_t)c0 * N, Z + (size_t)c0 * N, q, -1.0 / pc->nv,
-                           -1.0 / pc->ng, 1.0 / pc->nv, 1.0 / pc->ng, ST_PRECOND, dpart_rz));
+                           -1.0 / pc->ng, 1.0 / pc->nv, 1.0 / pc->ng, ST_PRECOND, dpart_rz, fin));
   }
   return DSKI_OK;
 }

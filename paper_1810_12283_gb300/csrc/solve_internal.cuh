@@ -146,14 +146,120 @@ int grid_precond_build(dski_handle h, pivchol_handle pc, const int* piv_dev, con
 // with up, the CG update of R runs in the scatter's point pass first (R is
 // updated in place); with dpart_rz, the final gather leaves per-block partial
 // sums of R^T Z (s <= 4 for either)
+// with fin, the final gather's last block also runs that CG finisher
 int grid_precond_apply(dski_handle h, pivchol_handle pc, const double* R, double* Z, int s,
-                       const CgUpdate* up = nullptr, double* dpart_rz = nullptr);
+                       const CgUpdate* up = nullptr, double* dpart_rz = nullptr,
+                       const CgFinish* fin = nullptr);
 // Noise diagonal of the internal layout: D[e] = nv (value rows) or ng.
 int noise_diag(dski_handle h, double nv, double ng, double* D_dev);
 // M^-1 for s columns: Z = D^-1/2 (Y - Q1 Q1^T Y), Y = D^-1/2 R.
 int precond_apply(dski_handle h, pivchol_handle pc, const double* R, double* Z, int s);
 
 // One batched PCG run on the internal layout (pcg.cu).
+// ---- per-column PCG state and the scalar steps every finisher shares ----
+// (device-resident FP64 scalars; the CG kernels and the gathers that fold a
+// finisher into their last block both use them)
+struct ColState {
+  double *bn2, *rn2, *rz, *rz0, *alpha, *beta, *target;
+  int *active, *iters, *bd, *nactive;
+  double *ahist, *bhist;
+  int depth;
+  int s;
+  // the inner passes run a perturbed operator (mixed modes, FFT products):
+  // a non-positive p^T q there ends the pass instead of breaking down, and
+  // the restart from the FP64 true residual refines x against the exact
+  // operator
+  int soft;
+};
+
+constexpr int CG_MAXS = 264;   // >= 1 + the largest probe count (256)
+
+// In the last block: tot[c] = sum over bx of part[(c nb + bx) stride + off]
+// for every column c < s.  The block's threads split the partials and a
+// fixed tree combines them (deterministic).  tot is shared, length >= s.
+__device__ inline void sum_columns(const double* part, int nb, int s, int stride, int off,
+                            double* tot, double* sh) {
+  for (int c = 0; c < s; ++c) {
+    double v = 0.0;
+    for (int bx = threadIdx.x; bx < nb; bx += blockDim.x)
+      v += part[((long long)c * nb + bx) * stride + off];
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) tot[c] = v;
+  }
+  __syncthreads();
+}
+
+// From the column sums tot[c] = r^T z: at (re)start rz (and rz0 once), else
+// beta = (r^T z)_new / rz for active columns (recorded), 0 for the others.
+__device__ inline void beta_finish(const double* tot, ColState& cs, int init) {
+  for (int cc = threadIdx.x; cc < cs.s; cc += blockDim.x) {
+    const double t = tot[cc];
+    if (init) {
+      cs.rz[cc] = t;
+      cs.beta[cc] = 0.0;
+      if (cs.rz0[cc] == 0.0) cs.rz0[cc] = t;
+    } else if (cs.active[cc]) {
+      const double be = t / cs.rz[cc];
+      cs.beta[cc] = be;
+      cs.rz[cc] = t;
+      const int k = cs.iters[cc] - 1;
+      if (cs.bhist && k >= 0 && k < cs.depth) cs.bhist[(long long)k * cs.s + cc] = be;
+    } else {
+      cs.beta[cc] = 0.0;
+    }
+  }
+}
+
+// From tot[c] = p^T q: alpha = r^T z / p^T q for active columns (recorded),
+// breakdown (non-positive or non-finite) deactivates a column.
+__device__ inline void alpha_finish(const double* tot, ColState& cs) {
+  for (int cc = threadIdx.x; cc < cs.s; cc += blockDim.x) {
+    double al = 0.0;
+    if (cs.active[cc]) {
+      const double t = tot[cc];
+      if (!(t > 0.0) || !isfinite(t) || !isfinite(cs.rz[cc])) {
+        if (!cs.soft || !isfinite(cs.rz[cc])) cs.bd[cc] = 1;
+        cs.active[cc] = 0;
+      } else {
+        al = cs.rz[cc] / t;
+        const int k = cs.iters[cc];
+        if (cs.ahist && k < cs.depth) cs.ahist[(long long)k * cs.s + cc] = al;
+      }
+    }
+    cs.alpha[cc] = al;
+  }
+}
+
+// From tot[c] = ||r||^2 after the update: record it, count the iteration,
+// deactivate the columns that met their target; the active count.
+__device__ inline void update_finish(const double* tot, ColState& cs, double* sh) {
+  int nact = 0;
+  for (int cc = threadIdx.x; cc < cs.s; cc += blockDim.x) {
+    if (cs.active[cc]) {
+      const double t = tot[cc];
+      cs.rn2[cc] = t;
+      cs.iters[cc] += 1;
+      if (!(t > cs.target[cc])) cs.active[cc] = 0;
+    }
+    nact += cs.active[cc];
+  }
+  nact = (int)block_sum((double)nact, sh);
+  if (threadIdx.x == 0) *cs.nactive = nact;
+}
+
+
+// A CG finisher folded into the last block of a gather whose per-block
+// partial sums it completes (see k_gather): kind 0 sums the gather's
+// p^T q partials and sets alpha; kind 1 sums part2 (||r||^2 after the
+// update), does the update's bookkeeping, then sums the gather's r^T z
+// partials and sets beta.  kind < 0: none.
+struct CgFinish {
+  int kind = -1;
+  ColState cs{};
+  unsigned* ticket = nullptr;
+  const double* part2 = nullptr;
+};
+
 struct CgRun {
   int s = 1;
   double rtol = 1e-8;
