@@ -867,14 +867,16 @@ namespace {
 template <class T, int CB>
 void scatter_cells_d2(dski_handle h, T* v, T* S, T* grid, int s, T sv, T sg, const double* z,
                       const double* beta, cudaStream_t st) {
-  // group size: about four points per lane, so that the butterfly over the
-  // group (16 CB values per level) stays short against the points' loads
+  // group size: about eight points per lane.  The pass is bound by
+  // instruction issue (ncu at n = 1e7: issue slots 60% busy, DRAM 25%), and
+  // the butterfly over the group costs 2 x 16 CB instructions per level and
+  // lane, so fewer lanes per cell leave more issue slots to the points
   const int ncell = h->mc[0] * h->mc[1];
   const double per = (double)h->n / std::max(1, ncell);
-  if (per <= 8.0) launch_scatter_cells<T, CB, 2>(h, v, S, s, sv, sg, z, beta, st);
-  else if (per <= 16.0) launch_scatter_cells<T, CB, 4>(h, v, S, s, sv, sg, z, beta, st);
-  else if (per <= 32.0) launch_scatter_cells<T, CB, 8>(h, v, S, s, sv, sg, z, beta, st);
-  else if (per <= 64.0) launch_scatter_cells<T, CB, 16>(h, v, S, s, sv, sg, z, beta, st);
+  if (per <= 16.0) launch_scatter_cells<T, CB, 2>(h, v, S, s, sv, sg, z, beta, st);
+  else if (per <= 32.0) launch_scatter_cells<T, CB, 4>(h, v, S, s, sv, sg, z, beta, st);
+  else if (per <= 64.0) launch_scatter_cells<T, CB, 8>(h, v, S, s, sv, sg, z, beta, st);
+  else if (per <= 128.0) launch_scatter_cells<T, CB, 16>(h, v, S, s, sv, sg, z, beta, st);
   else launch_scatter_cells<T, CB, 32>(h, v, S, s, sv, sg, z, beta, st);
   const dim3 gn((unsigned)((h->M + 255) / 256), (unsigned)((s + CB - 1) / CB));
   k_scatter_nodes<T, CB><<<gn, 256, 0, st>>>(make_geo(h), S, grid, s, h->M, ncell);

@@ -398,7 +398,9 @@ def test_mll_gradient_surface_subsample_against_dense():
     path passed the same check once; it is left out to keep the suite short,
     each gradient taking ~25 s on this system).
     The oracle forms the dense matrices factor by factor, and central
-    differences with step 1e-4 pin that gradient (test_oracle_mll)."""
+    differences with step 1e-4 pin that gradient (test_oracle_mll).  One
+    seed's gradient also equals the oracle's same-probe estimator to 1e-6 of
+    its largest component."""
     need_gpu()
     import math
     from oracle.mll import mll_grad_dense
@@ -420,6 +422,20 @@ def test_mll_gradient_surface_subsample_against_dense():
         gs = np.array(gs)
         mean, se = gs.mean(0), gs.std(0, ddof=1) / np.sqrt(len(gs))
         assert np.all(np.abs(mean - ge) <= 5 * se + 1e-6 * np.abs(ge)), (prec, mean, se, ge)
+        # the first seed's gradient against the oracle's estimator with the same
+        # probes (the GPU's pivots rebuilt in the oracle, solves from the dense
+        # Cholesky factor); the GPU's solves stop at rtol 1e-8
+        from oracle.mll import mll_grad_hutchinson_direct
+        from oracle.probes import preconditioned_probes
+        from oracle.solve import pivoted_cholesky
+        pc = op.pivchol(100)
+        _, piv = pc.export()
+        pc.close()
+        Lo, _, _ = pivoted_cholesky(orc.kgrad_diag(), orc.kgrad_row, 100, pivots=piv)
+        Pc = _oracle_pc(orc, Lo)
+        _, _, go = mll_grad_hutchinson_direct(orc, p["y"], Pc, preconditioned_probes(100, Pc, 16),
+                                              factored=True)
+        assert np.max(np.abs(gs[0] - go)) <= 1e-6 * np.abs(go).max(), (gs[0], go)
         op.close()
 
 
