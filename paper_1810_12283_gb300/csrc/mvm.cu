@@ -363,16 +363,12 @@ __global__ void __launch_bounds__(256) k_scatter_cells(const int* __restrict__ c
     for (int j = js + g; j < je; j += G) {
       // the point's weights from its two cell fractions (the 12 bytes of
       // geometry a point carries, instead of a 64-byte weight table):
-      // w[0..3] = phi, w[4..7] = phi' / h in dimension 0, w[8..15] likewise in 1
+      // w[0..3] = phi, w[4..7] = phi' in dimension 0, w[8..15] likewise in 1;
+      // the 1/h of the derivative weights scales the point's gradient values
       T w[16];
       const T2v<T> fr = ld2(frac + 2 * (long long)j);
       keys4<T>(fr.x, w, w + 4);
       keys4<T>(fr.y, w + 8, w + 12);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        w[4 + k] *= ih0;
-        w[12 + k] *= ih1;
-      }
 #pragma unroll
       for (int q = 0; q < CB; ++q) {
         if (q0 + q >= s) break;
@@ -389,8 +385,8 @@ __global__ void __launch_bounds__(256) k_scatter_cells(const int* __restrict__ c
           vj[2] = v2;
         }
         v0 *= sv;
-        v1 *= sg;
-        v2 *= sg;
+        v1 *= sg * ih0;   // dW_0 = phi'(dimension 0) / h_0
+        v2 *= sg * ih1;   // dW_1 = phi'(dimension 1) / h_1
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
           const T ca = fma(w[a], v0, w[4 + a] * v1);   // sum-factorised over dimension 0
