@@ -627,23 +627,30 @@ MULTI_ORACLE_SAMPLE = 16
 def run_multi(args):
     """The uneven multi-instance workload: 256 independent GP-with-gradient
     problems (d in {2, 3}, n log-uniform in [200, 5000], 48^2 or 24^3 grids,
-    rank-32 pivoted Cholesky, PCG to 1e-6), each on its own handle and
-    stream, driven by --multi-workers host threads.  Reports instances/s
-    over the whole batch, p50/p99 per-instance time, the convergence count,
-    and (the oracle leg, on the host cores) ||y - K~_oracle x|| / ||y|| on a
-    seeded sample of the instances.  Inputs are seeded and synthetic."""
+    rank-32 pivoted Cholesky, PCG to 1e-6).  Default: the handles and
+    preconditioners are built on --multi-workers host threads (one stream
+    each), then one persistent launch solves all 256 (a CTA per system);
+    --multi-streams: every problem also solves on its own stream.  Reports
+    instances/s over the whole batch (set-up included), the set-up and solve
+    split, p50/p99 per-instance solve time, the convergence count, and (the
+    oracle leg, on the host cores) ||y - K~_oracle x|| / ||y|| on a seeded
+    sample of the instances.  Inputs are seeded and synthetic."""
     import torch
     import numpy as np
+    from paper_1810_12283_gb300 import launch_count
     from paper_1810_12283_gb300.batch import solve_many
     from synth import workloads as W
     probs = [W.multi_instance(i) for i in range(MULTI_INSTANCES)]
+    persistent = not args.multi_streams
     # warm-up: one instance of each dimension (kernel loading, tuner)
     solve_many([probs[0], probs[1]], rank=32, rtol=1e-6, maxit=40000, prec=args.prec,
-               workers=2)
+               workers=2, persistent=persistent)
     torch.cuda.synchronize()
+    launches0 = launch_count()
+    tim = {}
     t0 = time.perf_counter()
     res = solve_many(probs, rank=32, rtol=1e-6, maxit=40000, prec=args.prec,
-                     workers=args.multi_workers)
+                     workers=args.multi_workers, persistent=persistent, timings=tim)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     secs = sorted(r["seconds"] for r in res)
@@ -652,10 +659,21 @@ def run_multi(args):
     line = {"metric": "multi-instance D-SKI PCG throughput (256 uneven problems, rtol 1e-6)",
             "unit": "instances/s", "value": MULTI_INSTANCES / wall, "wall_s": wall,
             "mode": args.prec, "workers": args.multi_workers,
+            "solver": ("one persistent launch, a CTA per system (dski_pcg_solve_batch)"
+                       if persistent else "a stream per system (dski_pcg_solve)"),
             "p50_s": secs[len(secs) // 2], "p99_s": secs[min(len(secs) - 1, int(0.99 * len(secs)))],
+            "max_s": secs[-1],
+            "per_instance_time": ("solve time inside the persistent launch (device clock)"
+                                  if persistent else "wall time of the instance on its stream"),
             "converged": conv, "instances": MULTI_INSTANCES,
             "iters_p50": its[len(its) // 2] if its else None,
+            "iters_max": its[-1] if its else None,
+            "gpu_launches": launch_count() - launches0,
             "errors": sorted({r["error"] for r in res if r["error"]})[:3]}
+    if tim:
+        line["setup_s"] = tim["setup_s"]
+        line["solve_s"] = tim["solve_s"]
+        line["solve_only_instances_per_s"] = MULTI_INSTANCES / tim["solve_s"]
     if not args.no_cpu_baseline:
         from oracle.dski import DSKI as ODSKI, Grid
         rng = np.random.default_rng(11)
@@ -742,6 +760,9 @@ def main():
     ap.add_argument("--multi", action="store_true",
                     help="instead of the solve step: the 256-instance uneven workload")
     ap.add_argument("--multi-workers", type=int, default=8)
+    ap.add_argument("--multi-streams", action="store_true",
+                    help="--multi: solve each instance on its own stream instead of in one "
+                         "persistent launch")
     ap.add_argument("--surface-maxit", type=int, default=20000)
     ap.add_argument("--kuu", default="dense", choices=["dense", "fft"],
                     help="products with K_UU: dense Kronecker factors or Toeplitz/FFT")

@@ -198,6 +198,38 @@ double pivchol_logdet(pivchol_handle pc);
 int dski_pcg_solve(dski_handle h, pivchol_handle pc, const double* b_dev, double* x_dev,
                    int s, double rtol, int maxit, int* iters_host, double* relres_host);
 
+/* Sec. 2 / Sec. 3.3: solve K~_i x_i = b_i for `count` independent systems
+ * (each its own handle: any n, d, grid and hyperparameters) in ONE
+ * persistent launch.  Each CTA solves one system at a time, start to
+ * finish, with its grid vector and Kronecker factors in shared memory, and
+ * takes the next system from a device work queue ordered by estimated cost
+ * per iteration, largest first.  The PCG is dski_pcg_solve's in FP64:
+ * restarts from the FP64 true residual, at most 64 passes, maxit MVMs.
+ *   hs[count]     handles with FP64 vectors (FP64 or FP64_TC mode; here
+ *                 the mode products always run the FP64 factors K_k on the
+ *                 FP64 units); every m_k <= 64 and (M + sum_k m_k^2)
+ *                 doubles must fit in one CTA's shared memory (~227 KB:
+ *                 a 24^3 or 48^2 grid fits, 40^3 does not).
+ *   pcs[count]    pivchol_build preconditioners of those handles (rank <=
+ *                 32), applied in their QR form; pcs or an entry NULL: none.
+ *   b[count]      device pointers, N_i FP64 each, block order (as dski_mvm).
+ *   x[count]      device pointers, N_i FP64 each: initial guess in,
+ *                 solution out.  b and x must be ready before the call.
+ *   rtol, maxit   per system, as dski_pcg_solve.
+ *   iters, relres, status, seconds  host arrays of count entries, each may
+ *                 be NULL: MVMs, the final FP64 true relative residual, the
+ *                 system's DSKI_OK / NOT_CONVERGED / BREAKDOWN, and the
+ *                 system's solve time inside the launch (device clock).
+ * The scatter adds with shared-memory atomics in no fixed order, so results
+ * may differ between runs in their last bits.  Waits for every handle's
+ * stream, runs on hs[0]'s stream, allocates its workspace (6 N_i doubles
+ * per system) for the call and returns when done.
+ * Errors: ARG (nothing runs), ALLOC, CUDA; NOT_CONVERGED or BREAKDOWN
+ * (the status of the first failing system; every output is filled). */
+int dski_pcg_solve_batch(int count, const dski_handle* hs, const pivchol_handle* pcs,
+                         const double* const* b, double* const* x, double rtol, int maxit,
+                         int* iters, double* relres, int* status, double* seconds);
+
 /* Sec. 2: stochastic Lanczos quadrature estimate of log|K~|.
  * Probe j (0-based) is z_j = D^1/2 (w1_j + L' w2_j), where w = [w1; w2] is a
  * Rademacher vector of length N + r and L' the preconditioner's low-rank

@@ -252,3 +252,38 @@ def launch_count():
 def mll_function(*args, **kwargs):
     from .autograd import mll_function as f
     return f(*args, **kwargs)
+
+
+def solve_batch(ops, pcs, bs, rtol=1e-8, maxit=10000, x0s=None, allow_failed=False):
+    """Solve K~_i x_i = b_i for many independent systems in one persistent
+    launch (dski_pcg_solve_batch): ops[i] a DSKI (FP64 or FP64_TC), pcs[i]
+    its Preconditioner or None, bs[i] its N_i right-hand side (cuda FP64).
+    Returns (xs, iters, relres, status, seconds) with per-system lists;
+    status is "OK" or the failure's name.  allow_failed: return the
+    outputs of systems that did not converge or broke down instead of
+    raising."""
+    k = len(ops)
+    if not (len(pcs) == len(bs) == k) or k == 0:
+        raise ValueError("solve_batch: ops, pcs and bs must be non-empty and of equal length")
+    Bs = [torch.as_tensor(b, dtype=torch.float64, device="cuda").contiguous() for b in bs]
+    if x0s is None:
+        Xs = [torch.zeros_like(b) for b in Bs]
+    else:
+        Xs = [torch.as_tensor(x, dtype=torch.float64, device="cuda").clone().contiguous()
+              for x in x0s]
+    vp = C.c_void_p
+    H = (vp * k)(*[op.h for op in ops])
+    P = (vp * k)(*[(pc.ptr if pc is not None else None) for pc in pcs])
+    Bp = (vp * k)(*[b.data_ptr() for b in Bs])
+    Xp = (vp * k)(*[x.data_ptr() for x in Xs])
+    it = (C.c_int * k)()
+    rr = (C.c_double * k)()
+    stt = (C.c_int * k)()
+    sec = (C.c_double * k)()
+    torch.cuda.synchronize()
+    rc = _lib.load().dski_pcg_solve_batch(k, H, P, Bp, Xp, float(rtol), int(maxit), it, rr, stt,
+                                          sec)
+    _lib.check(rc, (-4, -5) if allow_failed else ())
+    status = [_lib.STATUS.get(v, str(v)) for v in stt]
+    return Xs, list(it), list(rr), status, list(sec)
+

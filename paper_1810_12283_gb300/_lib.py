@@ -22,7 +22,7 @@ EXPORTS = ["dski_create", "dski_set_hypers", "dski_mvm", "pivchol_build", "dski_
            "dski_logdet_slq", "dski_mll_grad", "dski_destroy", "pivchol_destroy",
            "dski_last_error", "dski_profile", "dski_launch_count", "pivchol_export",
            "pivchol_logdet", "dski_mvm_noalloc", "dski_predict", "dski_predict_var_cv",
-           "dski_mll_grad_tol", "dski_set_wait_budget"]
+           "dski_mll_grad_tol", "dski_set_wait_budget", "dski_pcg_solve_batch"]
 NSTAGES = 8
 STAGES = ["permute", "scatter", "kron", "gather", "precond", "pcg_vec", "pivchol", "lanczos"]
 
@@ -68,6 +68,8 @@ def load(path=LIB_PATH):
     lib.dski_mll_grad_tol.argtypes = [vp, vp, vp, C.c_int, C.c_uint64, C.c_double, C.c_int,
                                       dp, dp]
     lib.dski_set_wait_budget.argtypes = [vp, C.c_int]
+    lib.dski_pcg_solve_batch.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
+                                         C.POINTER(vp), C.c_double, C.c_int, ip, dp, ip, dp]
     lib.dski_predict.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, vp, vp]
     lib.dski_predict_var_cv.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_uint64, C.c_double,
                                         C.c_int, vp]
