@@ -644,13 +644,14 @@ def run_multi(args):
     persistent = not args.multi_streams
     # warm-up: one instance of each dimension (kernel loading, tuner)
     solve_many([probs[0], probs[1]], rank=32, rtol=1e-6, maxit=40000, prec=args.prec,
-               workers=2, persistent=persistent)
+               workers=2, persistent=persistent, cluster=args.multi_cluster)
     torch.cuda.synchronize()
     launches0 = launch_count()
     tim = {}
     t0 = time.perf_counter()
     res = solve_many(probs, rank=32, rtol=1e-6, maxit=40000, prec=args.prec,
-                     workers=args.multi_workers, persistent=persistent, timings=tim)
+                     workers=args.multi_workers, persistent=persistent, timings=tim,
+                     cluster=args.multi_cluster)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     secs = sorted(r["seconds"] for r in res)
@@ -659,8 +660,10 @@ def run_multi(args):
     line = {"metric": "multi-instance D-SKI PCG throughput (256 uneven problems, rtol 1e-6)",
             "unit": "instances/s", "value": MULTI_INSTANCES / wall, "wall_s": wall,
             "mode": args.prec, "workers": args.multi_workers,
-            "solver": ("one persistent launch, a CTA per system (dski_pcg_solve_batch)"
-                       if persistent else "a stream per system (dski_pcg_solve)"),
+            "solver": ("one persistent launch, a cluster of CTAs per system "
+                       "(dski_pcg_solve_batch)" if persistent
+                       else "a stream per system (dski_pcg_solve)"),
+            "cluster": (args.multi_cluster or 4) if persistent else None,
             "p50_s": secs[len(secs) // 2], "p99_s": secs[min(len(secs) - 1, int(0.99 * len(secs)))],
             "max_s": secs[-1],
             "per_instance_time": ("solve time inside the persistent launch (device clock)"
@@ -760,6 +763,8 @@ def main():
     ap.add_argument("--multi", action="store_true",
                     help="instead of the solve step: the 256-instance uneven workload")
     ap.add_argument("--multi-workers", type=int, default=8)
+    ap.add_argument("--multi-cluster", type=int, default=0, choices=[0, 1, 2, 4, 8],
+                    help="--multi: CTAs per system in the persistent launch (0: default)")
     ap.add_argument("--multi-streams", action="store_true",
                     help="--multi: solve each instance on its own stream instead of in one "
                          "persistent launch")

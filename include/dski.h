@@ -200,11 +200,14 @@ int dski_pcg_solve(dski_handle h, pivchol_handle pc, const double* b_dev, double
 
 /* Sec. 2 / Sec. 3.3: solve K~_i x_i = b_i for `count` independent systems
  * (each its own handle: any n, d, grid and hyperparameters) in ONE
- * persistent launch.  Each CTA solves one system at a time, start to
- * finish, with its grid vector and Kronecker factors in shared memory, and
- * takes the next system from a device work queue ordered by estimated cost
- * per iteration, largest first.  The PCG is dski_pcg_solve's in FP64:
- * restarts from the FP64 true residual, at most 64 passes, maxit MVMs.
+ * persistent launch of thread-block clusters.  A cluster of `cluster` CTAs
+ * solves one system at a time, start to finish: its CTAs split the points,
+ * rows and grid between them, each keeping the grid vector and Kronecker
+ * factors in its shared memory and exchanging grid slices through
+ * distributed shared memory; the cluster then takes the next system from a
+ * device work queue ordered by estimated cost per iteration, largest first.
+ * The PCG is dski_pcg_solve's in FP64: restarts from the FP64 true
+ * residual, at most 64 passes, maxit MVMs.
  *   hs[count]     handles with FP64 vectors (FP64 or FP64_TC mode; here
  *                 the mode products always run the FP64 factors K_k on the
  *                 FP64 units); every m_k <= 64 and (M + sum_k m_k^2)
@@ -216,6 +219,9 @@ int dski_pcg_solve(dski_handle h, pivchol_handle pc, const double* b_dev, double
  *   x[count]      device pointers, N_i FP64 each: initial guess in,
  *                 solution out.  b and x must be ready before the call.
  *   rtol, maxit   per system, as dski_pcg_solve.
+ *   cluster       CTAs per system: 1, 2, 4 or 8; 0 picks the library's
+ *                 default (4).  More CTAs finish a large system sooner;
+ *                 fewer spend less on exchanges when systems are small.
  *   iters, relres, status, seconds  host arrays of count entries, each may
  *                 be NULL: MVMs, the final FP64 true relative residual, the
  *                 system's DSKI_OK / NOT_CONVERGED / BREAKDOWN, and the
@@ -228,7 +234,7 @@ int dski_pcg_solve(dski_handle h, pivchol_handle pc, const double* b_dev, double
  * (the status of the first failing system; every output is filled). */
 int dski_pcg_solve_batch(int count, const dski_handle* hs, const pivchol_handle* pcs,
                          const double* const* b, double* const* x, double rtol, int maxit,
-                         int* iters, double* relres, int* status, double* seconds);
+                         int cluster, int* iters, double* relres, int* status, double* seconds);
 
 /* Sec. 2: stochastic Lanczos quadrature estimate of log|K~|.
  * Probe j (0-based) is z_j = D^1/2 (w1_j + L' w2_j), where w = [w1; w2] is a

@@ -254,14 +254,14 @@ def mll_function(*args, **kwargs):
     return f(*args, **kwargs)
 
 
-def solve_batch(ops, pcs, bs, rtol=1e-8, maxit=10000, x0s=None, allow_failed=False):
+def solve_batch(ops, pcs, bs, rtol=1e-8, maxit=10000, x0s=None, allow_failed=False, cluster=0):
     """Solve K~_i x_i = b_i for many independent systems in one persistent
     launch (dski_pcg_solve_batch): ops[i] a DSKI (FP64 or FP64_TC), pcs[i]
     its Preconditioner or None, bs[i] its N_i right-hand side (cuda FP64).
     Returns (xs, iters, relres, status, seconds) with per-system lists;
     status is "OK" or the failure's name.  allow_failed: return the
     outputs of systems that did not converge or broke down instead of
-    raising."""
+    raising.  cluster: CTAs per system (1, 2, 4 or 8; 0: the default)."""
     k = len(ops)
     if not (len(pcs) == len(bs) == k) or k == 0:
         raise ValueError("solve_batch: ops, pcs and bs must be non-empty and of equal length")
@@ -281,8 +281,8 @@ def solve_batch(ops, pcs, bs, rtol=1e-8, maxit=10000, x0s=None, allow_failed=Fal
     stt = (C.c_int * k)()
     sec = (C.c_double * k)()
     torch.cuda.synchronize()
-    rc = _lib.load().dski_pcg_solve_batch(k, H, P, Bp, Xp, float(rtol), int(maxit), it, rr, stt,
-                                          sec)
+    rc = _lib.load().dski_pcg_solve_batch(k, H, P, Bp, Xp, float(rtol), int(maxit), int(cluster),
+                                          it, rr, stt, sec)
     _lib.check(rc, (-4, -5) if allow_failed else ())
     status = [_lib.STATUS.get(v, str(v)) for v in stt]
     return Xs, list(it), list(rr), status, list(sec)

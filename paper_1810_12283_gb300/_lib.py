@@ -69,7 +69,8 @@ def load(path=LIB_PATH):
                                       dp, dp]
     lib.dski_set_wait_budget.argtypes = [vp, C.c_int]
     lib.dski_pcg_solve_batch.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
-                                         C.POINTER(vp), C.c_double, C.c_int, ip, dp, ip, dp]
+                                         C.POINTER(vp), C.c_double, C.c_int, C.c_int, ip, dp, ip,
+                                         dp]
     lib.dski_predict.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, vp, vp]
     lib.dski_predict_var_cv.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_uint64, C.c_double,
                                         C.c_int, vp]

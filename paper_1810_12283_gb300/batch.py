@@ -32,14 +32,15 @@ def _setup(p, rank, prec, device):
 
 
 def solve_many(problems, rank=32, rtol=1e-6, maxit=20000, prec="fp64", workers=8,
-               device="cuda", persistent=True, timings=None):
+               device="cuda", persistent=True, timings=None, cluster=0):
     """Solve K~_i x_i = y_i for every problem dict (X, y, m, lo, hi, ell, sf,
     noise_value, noise_grad).  Returns a list of dicts with x (CPU tensor),
     iters, relres, error (None, or the message / status of a solve that
     failed) and seconds: the problem's solve time inside the persistent
     launch (device clock), or its wall time on its stream.  timings (a
     dict, persistent mode): receives the wall seconds of the set-up
-    ("setup_s") and of the persistent launch ("solve_s")."""
+    ("setup_s") and of the persistent launch ("solve_s").  cluster: CTAs
+    per system in the persistent launch (1, 2, 4 or 8; 0: the default)."""
     if persistent:
         t0 = time.perf_counter()
         with cf.ThreadPoolExecutor(max_workers=max(1, workers)) as ex:
@@ -49,7 +50,8 @@ def solve_many(problems, rank=32, rtol=1e-6, maxit=20000, prec="fp64", workers=8
         try:
             t1 = time.perf_counter()
             xs, its, rrs, status, secs = solve_batch(ops, pcs, [b[2] for b in built], rtol=rtol,
-                                                     maxit=maxit, allow_failed=True)
+                                                     maxit=maxit, allow_failed=True,
+                                                     cluster=cluster)
             if timings is not None:
                 timings["setup_s"] = t1 - t0
                 timings["solve_s"] = time.perf_counter() - t1

@@ -53,17 +53,20 @@ def _persistent_cases():
     return probs
 
 
-def test_persistent_batch_meets_the_oracle_system():
+@pytest.mark.parametrize("cluster", [1, 2, 4, 8])
+def test_persistent_batch_meets_the_oracle_system(cluster):
     """Every system of one persistent launch -- 2-D and 3-D, cubic and
     quintic, with and without a preconditioner -- reaches the FP64 tolerance
-    by its own true residual and satisfies the oracle's system."""
+    by its own true residual and satisfies the oracle's system, whether one
+    CTA or a cluster of 2, 4 or 8 CTAs solves each system."""
     need_gpu()
     from paper_1810_12283_gb300 import solve_batch
     probs = _persistent_cases()
     ops = [gpu_op(p, "fp64") for p in probs]
     pcs = [op.pivchol(16) if i < len(probs) - 1 else None for i, op in enumerate(ops)]
     bs = [torch.tensor(p["y"], device="cuda") for p in probs]
-    xs, its, rrs, status, secs = solve_batch(ops, pcs, bs, rtol=1e-8, maxit=50000)
+    xs, its, rrs, status, secs = solve_batch(ops, pcs, bs, rtol=1e-8, maxit=50000,
+                                             cluster=cluster)
     assert status == ["OK"] * len(probs)
     for p, x, it, rr, sec in zip(probs, xs, its, rrs, secs):
         assert 0 < it < 50000 and rr <= 1e-8 and sec > 0
@@ -104,7 +107,7 @@ def test_persistent_batch_edge_cases():
     assert its2[0] > 0 and all(i == 0 for i in its2[1:]) and max(rrs2[1:]) <= 1.01e-8
     # too few iterations
     xs3, its3, rrs3, status3, _ = solve_batch(ops, pcs, bs, rtol=1e-12, maxit=3,
-                                              allow_failed=True)
+                                              allow_failed=True, cluster=2)
     assert status3 == ["NOT_CONVERGED"] * 3 and its3 == [3, 3, 3]
     assert all(np.isfinite(r) and r > 1e-12 for r in rrs3)
     assert all(bool(torch.isfinite(x).all()) for x in xs3)
@@ -123,6 +126,9 @@ def test_persistent_batch_edge_cases():
         solve_batch([opb], [None], [torch.tensor(big["y"], device="cuda")], rtol=1e-6)
     assert e.value.status == "ARG" and "shared" in str(e.value)
     opb.close()
+    with pytest.raises(DskiError) as e:
+        solve_batch(ops, pcs, bs, rtol=1e-6, cluster=3)
+    assert e.value.status == "ARG"
     for pc in pcs:
         pc.close()
     for op in ops:
