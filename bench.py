@@ -104,6 +104,30 @@ def scatter_flops(n, d, S=4):
     return n * (3 + S * 3 + S + S * S * 4)
 
 
+def batch_iter_flops(n, d, M, msum, rank, S=4):
+    """FP64 flops of one PCG iteration of the persistent batched solver for
+    one system (n points in d dimensions, M grid nodes, sum of m_k msum, a
+    rank-`rank` QR-form preconditioner), counting an FMA as 2 flops, in the
+    sum-factorised form the kernel evaluates:
+      scatter per point   d = 2: S (3 + 1) + S^2 (3 + 1 atomic add)
+                          d = 3: S (3 + 1 + 1) + S^2 (3 + 1) + S^3 (3 + 1)
+      gather per point    d = 2: 4 S^2 + 6 S;  d = 3: 4 S^3 + 6 S^2 + 8 S
+      per row             noise and p^T q 4, p update 2, x and r updates 4,
+                          ||r||^2 2, D^-1/2 r 1, c = Q1^T y 2 rank,
+                          z 2 + 2 rank, r^T z 2
+      mode products       2 M sum_k m_k."""
+    if d == 1:
+        scat, gath = S * 4, S * 4
+    elif d == 2:
+        scat, gath = S * 4 + S * S * 4, 4 * S * S + 6 * S
+    elif d == 3:
+        scat, gath = S * 5 + S * S * 4 + S ** 3 * 4, 4 * S ** 3 + 6 * S * S + 8 * S
+    else:
+        raise ValueError("d must be 1, 2 or 3")
+    N = n * (d + 1)
+    return n * (scat + gath) + 2 * M * msum + N * (17 + 4 * rank)
+
+
 def measure_peaks(dev):
     """Dense-GEMM rates of this GPU measured in the run (CUDA events, best of
     3 after a warm-up): FP64 (cuBLAS DGEMM, 8192^3) and TF32 (cuBLAS FP32
@@ -677,6 +701,25 @@ def run_multi(args):
         line["setup_s"] = tim["setup_s"]
         line["solve_s"] = tim["solve_s"]
         line["solve_only_instances_per_s"] = MULTI_INSTANCES / tim["solve_s"]
+        # the persistent kernel is bound by the FP64 units: its algorithmic
+        # FP64 flops (batch_iter_flops x iterations, summed over the systems)
+        # over the launch's wall time, against this GPU's measured DGEMM rate
+        flops = 0.0
+        for q, r in zip(probs, res):
+            n, d = q["X"].shape
+            flops += r["iters"] * batch_iter_flops(n, d, int(np.prod(q["m"])), int(sum(q["m"])), 32)
+        fp64 = measure_peaks("cuda")["fp64_tflops"]
+        ach = flops / tim["solve_s"] / 1e12
+        C = line["cluster"]
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        line["roofline"] = {"bound": "alu", "achieved": ach, "peak": fp64, "unit": "TFLOP/s",
+                            "frac": ach / fp64, "traffic": None,
+                            "kernel": "k_batch_pcg (FP64 SIMT; one launch)",
+                            "peak_source": "measured in this run: cuBLAS DGEMM 8192^3, best of 3",
+                            "flops": flops}
+        # share of the launch's SM-time spent inside solves (a cluster of C
+        # CTAs holds C SMs while it solves a system)
+        line["sm_busy_fraction"] = sum(r["seconds"] for r in res) * C / (tim["solve_s"] * sms)
     if not args.no_cpu_baseline:
         from oracle.dski import DSKI as ODSKI, Grid
         rng = np.random.default_rng(11)

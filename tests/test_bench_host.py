@@ -94,3 +94,12 @@ def test_quintic_stencil_counts_and_workload_names():
     name = bench.workload_name(100_000)
     assert "interp" not in name and "kuu" not in name
     assert bench.workload_name(100_000, "quintic", "fft").endswith("interp=quintic kuu=fft")
+
+
+def test_batch_iteration_flop_count():
+    import bench
+    # d = 2, cubic: scatter 4 (3 + 1) + 16 (3 + 1) = 80 and gather
+    # 4 * 16 + 6 * 4 = 88 flops per point; 48^2 grid: 2 M (48 + 48)
+    assert bench.batch_iter_flops(10, 2, 48 * 48, 96, 32) == 10 * 168 + 2 * 2304 * 96 + 30 * 145
+    # d = 3: scatter 20 + 64 + 256 = 340, gather 256 + 96 + 32 = 384
+    assert bench.batch_iter_flops(5, 3, 24 ** 3, 72, 0) == 5 * 724 + 2 * 13824 * 72 + 20 * 17
