@@ -664,7 +664,8 @@ def run_multi(args):
     from paper_1810_12283_gb300 import launch_count
     from paper_1810_12283_gb300.batch import solve_many
     from synth import workloads as W
-    probs = [W.multi_instance(i) for i in range(MULTI_INSTANCES)]
+    count = args.multi_instances
+    probs = [W.multi_instance(i) for i in range(count)]
     persistent = not args.multi_streams
     # warm-up: one instance of each dimension (kernel loading, tuner)
     solve_many([probs[0], probs[1]], rank=32, rtol=1e-6, maxit=40000, prec=args.prec,
@@ -673,7 +674,7 @@ def run_multi(args):
     launches0 = launch_count()
     tim = {}
     t0 = time.perf_counter()
-    res = solve_many(probs, rank=32, rtol=1e-6, maxit=40000, prec=args.prec,
+    res = solve_many(probs, rank=32, rtol=1e-6, maxit=args.multi_maxit, prec=args.prec,
                      workers=args.multi_workers, persistent=persistent, timings=tim,
                      cluster=args.multi_cluster)
     torch.cuda.synchronize()
@@ -681,8 +682,8 @@ def run_multi(args):
     secs = sorted(r["seconds"] for r in res)
     conv = sum(1 for r in res if r["error"] is None and r["relres"] <= 1e-6)
     its = sorted(r["iters"] for r in res if r["error"] is None)
-    line = {"metric": "multi-instance D-SKI PCG throughput (256 uneven problems, rtol 1e-6)",
-            "unit": "instances/s", "value": MULTI_INSTANCES / wall, "wall_s": wall,
+    line = {"metric": f"multi-instance D-SKI PCG throughput ({count} uneven problems, rtol 1e-6)",
+            "unit": "instances/s", "value": count / wall, "wall_s": wall,
             "mode": args.prec, "workers": args.multi_workers,
             "solver": ("one persistent launch, a cluster of CTAs per system "
                        "(dski_pcg_solve_batch)" if persistent
@@ -692,7 +693,7 @@ def run_multi(args):
             "max_s": secs[-1],
             "per_instance_time": ("solve time inside the persistent launch (device clock)"
                                   if persistent else "wall time of the instance on its stream"),
-            "converged": conv, "instances": MULTI_INSTANCES,
+            "converged": conv, "instances": count, "maxit": args.multi_maxit,
             "iters_p50": its[len(its) // 2] if its else None,
             "iters_max": its[-1] if its else None,
             "gpu_launches": launch_count() - launches0,
@@ -700,7 +701,7 @@ def run_multi(args):
     if tim:
         line["setup_s"] = tim["setup_s"]
         line["solve_s"] = tim["solve_s"]
-        line["solve_only_instances_per_s"] = MULTI_INSTANCES / tim["solve_s"]
+        line["solve_only_instances_per_s"] = count / tim["solve_s"]
         # the persistent kernel is bound by the FP64 units: its algorithmic
         # FP64 flops (batch_iter_flops x iterations, summed over the systems)
         # over the launch's wall time, against this GPU's measured DGEMM rate
@@ -723,7 +724,7 @@ def run_multi(args):
     if not args.no_cpu_baseline:
         from oracle.dski import DSKI as ODSKI, Grid
         rng = np.random.default_rng(11)
-        sample = sorted(rng.choice(MULTI_INSTANCES, MULTI_ORACLE_SAMPLE, replace=False).tolist())
+        sample = sorted(rng.choice(count, min(count, MULTI_ORACLE_SAMPLE), replace=False).tolist())
         errs = []
         for i in sample:
             q, r = probs[i], res[i]
@@ -806,6 +807,10 @@ def main():
     ap.add_argument("--multi", action="store_true",
                     help="instead of the solve step: the 256-instance uneven workload")
     ap.add_argument("--multi-workers", type=int, default=8)
+    ap.add_argument("--multi-instances", type=int, default=MULTI_INSTANCES,
+                    help="--multi: the first K instances of the workload (default 256)")
+    ap.add_argument("--multi-maxit", type=int, default=40000,
+                    help="--multi: iteration cap per system (a small cap bounds a profiling run)")
     ap.add_argument("--multi-cluster", type=int, default=0, choices=[0, 1, 2, 4, 8],
                     help="--multi: CTAs per system in the persistent launch (0: default)")
     ap.add_argument("--multi-streams", action="store_true",
