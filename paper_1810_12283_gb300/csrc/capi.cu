@@ -141,6 +141,7 @@ static void release_all(dski_handle h) {
   h->frac32.release();
   h->W64.release();
   h->W32.release();
+  h->Wdf.release();
   for (int k = 0; k < DSKI_MAXD; ++k) {
     h->K64[k].release();
     h->K32[k].release();

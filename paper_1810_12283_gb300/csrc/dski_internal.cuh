@@ -110,6 +110,10 @@ struct dski_handle_ {
   // geometry (sorted order); W64/W32: per point and dimension the sw
   // stencil weights then the sw derivative weights (already divided by h_k)
   dski::DevBuf perm, inv_perm, cell, cell_start, frac64, frac32, W64, W32;
+  // FP64_TC, d = 2, cubic stencil: the W64 table as double-float pairs
+  // (float2 {hi, lo}, hi = fl32(w), lo = fl32(w - hi)) for the scatter's
+  // stencil products on the FP32 units
+  dski::DevBuf Wdf;
   // Kronecker factors K_k (m_k x m_k, row-major, symmetric): FP64, FP32 and
   // the TF32 hi/lo split of the FP64 value (hi = rna_tf32(K), lo = rna_tf32(K - hi)).
   dski::DevBuf K64[DSKI_MAXD], K32[DSKI_MAXD], Khi[DSKI_MAXD], Klo[DSKI_MAXD];
@@ -160,6 +164,13 @@ int scatter_internal(dski_handle h, const void* vin, void* g, int s, bool prec64
 // `ws` (scatter_ws_bytes bytes; NULL = the handle's workspace)
 int scatter_internal_ws(dski_handle h, const void* vin, void* g, int s, bool prec64, void* ws);
 size_t scatter_ws_bytes(dski_handle h, int s, bool prec64);
+// FP64_TC (d = 2, cubic, outside the true residuals): the scatter forms its
+// stencil products in double-float arithmetic on the FP32 units (~2^-48
+// relative) per cell, then adds the cells per node
+bool df_scatter_path(dski_handle h, bool prec64);
+// number of per-block partial sums of ||r||^2 (per column) that a scatter
+// fused with a CG update (CgUpdate) writes
+int scatter_update_blocks(dski_handle h);
 // A CG update fused into the scatter's point pass (FP64, d >= 2, s <= 4):
 // for every active column q, x += alpha_q p and r -= alpha_q q on the scattered
 // vector r (written back) before it is scattered, and per-block partial sums

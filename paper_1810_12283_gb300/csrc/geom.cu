@@ -201,6 +201,17 @@ __global__ void k_weights(const double* __restrict__ f64, int n, int d, GeoParam
   }
 }
 
+// Double-float copy of the FP64 weight table: Wdf[i] = {hi, lo} with
+// hi = fl32(W[i]) and lo = fl32(W[i] - hi) (hi + lo = W[i] to ~2^-48).
+__global__ void k_split_weights(const double* __restrict__ W, long long count,
+                                float2* __restrict__ Wdf) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const double w = W[i];
+  const float hi = __double2float_rn(w);
+  Wdf[i] = make_float2(hi, __double2float_rn(w - (double)hi));
+}
+
 // cell_start[c] = first sorted position whose cell is >= c (CSR over cells).
 __global__ void k_cell_start(const uint32_t* __restrict__ skey, int n, int ncell,
                              int* __restrict__ start) {
@@ -319,6 +330,16 @@ int build_geometry(dski_handle h, const double* X_dev) {
                                                       h->W64.as<double>(), h->W32.as<float>());
     });
     count_launches(3);
+    if (h->prec == DSKI_FP64_TC && d == 2 && h->sw == 4) {
+      const long long cnt = (long long)n * d * 2 * h->sw;
+      if (h->Wdf.ensure((size_t)cnt * sizeof(float2))) {
+        rc = DSKI_ERR_ALLOC;
+        break;
+      }
+      k_split_weights<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(h->W64.as<double>(), cnt,
+                                                                    h->Wdf.as<float2>());
+      count_launches(1);
+    }
     if (cudaGetLastError() != cudaSuccess) { rc = DSKI_ERR_CUDA; break; }
     if (cudaStreamSynchronize(st) != cudaSuccess) { rc = DSKI_ERR_CUDA; break; }
   } while (0);

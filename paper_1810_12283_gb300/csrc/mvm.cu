@@ -444,6 +444,158 @@ __global__ void __launch_bounds__(256) k_scatter_nodes(MvmGeo geo, const T* __re
     if (q0 + q < s) grid[(long long)(q0 + q) * M + u] = acc[q];
 }
 
+// ------------------------------- FP64_TC scatter, d = 2, double-float ----
+// k_scatter_cells' per-cell pass at FP64-class accuracy on the FP32 units
+// (GB300 runs FP32 ~60x faster than FP64): each point's three values are
+// split into double-float pairs (hi + lo), the stencil weights arrive as
+// pairs (Wdf), and every product and sum is an error-free transformation
+// (FMA exact product, TwoSum), so a cell's 16 sums carry ~2^-48 relative
+// error of the magnitudes they add (FP64: 2^-53).  Before that, in FP64,
+// the CG steps a pass may carry: p = z + beta p (written back), or
+// x += alpha p, r -= alpha q (r written back) with per-block partial sums of
+// ||r||^2 (column q at dpart[q gridDim.x + block]); then v^0 scaled by sv,
+// v^1, v^2 by sg.  Column q = blockIdx.y; G lanes per cell, each a
+// stride-G subset of the cell's points; a fixed butterfly adds the lanes.
+__device__ __forceinline__ void df_prod(float ah, float al, float bh, float bl, float& ph,
+                                        float& pl) {
+  const float p = ah * bh;
+  const float e = fmaf(ah, bh, -p);
+  const float t = fmaf(ah, bl, fmaf(al, bh, e));
+  ph = p + t;              // |t| << |p|: Fast2Sum renormalises exactly
+  pl = t - (ph - p);
+}
+
+template <int G>
+__global__ void __launch_bounds__(256) k_scatter_cells_df(
+    const int* __restrict__ cell_start, const float2* __restrict__ Wdf, double* __restrict__ v,
+    float2* __restrict__ S, long long N, int ncell, double sv, double sg,
+    const double* __restrict__ z, const double* __restrict__ beta, CgUpdate up) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = (int)(t / G), g = (int)(t % G);
+  const bool live = c < ncell;   // whole groups: G | 32
+  const int q = blockIdx.y;
+  const bool upd = up.x != nullptr && up.active[q] != 0;
+  float ah[16], al[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    ah[k] = 0.f;
+    al[k] = 0.f;
+  }
+  double rs = 0.0;
+  if (live) {
+    const int js = cell_start[c], je = cell_start[c + 1];
+    for (int j = js + g; j < je; j += G) {
+      const long long o = (long long)q * N + (long long)j * 3;
+      double* vj = v + o;
+      double vv[3] = {vj[0], vj[1], vj[2]};
+      if (z) {
+        const double be = beta[q];
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+          vv[cc] = fma(be, vv[cc], z[o + cc]);
+          vj[cc] = vv[cc];
+        }
+      }
+      if (upd) {
+        const double alpha = up.alpha[q];
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+          up.x[o + cc] = fma(alpha, up.p[o + cc], up.x[o + cc]);
+          vv[cc] = fma(-alpha, up.q[o + cc], vv[cc]);
+          vj[cc] = vv[cc];
+          rs = fma(vv[cc], vv[cc], rs);
+        }
+      }
+      float vh[3], vl[3];
+      split_d(sv * vv[0], vh[0], vl[0]);
+      split_d(sg * vv[1], vh[1], vl[1]);
+      split_d(sg * vv[2], vh[2], vl[2]);
+      float2 w[16];   // w0[0..3], dw0[0..3] (dimension 0), w1, dw1 (dimension 1)
+      const float4* w4 = reinterpret_cast<const float4*>(Wdf + (long long)j * 16);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float4 x = __ldg(w4 + k);
+        w[2 * k] = make_float2(x.x, x.y);
+        w[2 * k + 1] = make_float2(x.z, x.w);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        // A = w0_a v0 + dw0_a v1, B = w0_a v2 (sum-factorised over dimension 0)
+        float Ah, Al, Bh, Bl;
+        df_prod(w[a].x, w[a].y, vh[0], vl[0], Ah, Al);
+        df_fma(w[4 + a].x, w[4 + a].y, vh[1], vl[1], Ah, Al);
+        {
+          float sh, se;
+          two_sum(Ah, Al, sh, se);
+          Ah = sh;
+          Al = se;
+        }
+        df_prod(w[a].x, w[a].y, vh[2], vl[2], Bh, Bl);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          df_fma(w[8 + b].x, w[8 + b].y, Ah, Al, ah[a * 4 + b], al[a * 4 + b]);
+          df_fma(w[12 + b].x, w[12 + b].y, Bh, Bl, ah[a * 4 + b], al[a * 4 + b]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const float oh = __shfl_xor_sync(0xffffffffu, ah[k], o);
+      const float ol = __shfl_xor_sync(0xffffffffu, al[k], o);
+      df_add(ah[k], al[k], oh, ol);
+    }
+  if (up.x) {
+    __shared__ double red[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double tsum = rs;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
+    if (lane == 0) red[w] = tsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b = 0.0;
+      for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) b += red[ww];
+      up.dpart[(long long)q * gridDim.x + blockIdx.x] = b;
+    }
+  }
+  if (!live) return;
+#pragma unroll
+  for (int k = 0; k < 16; ++k)
+    if (k % G == g) {
+      float sh, se;
+      two_sum(ah[k], al[k], sh, se);
+      S[((long long)q * 16 + k) * ncell + c] = make_float2(sh, se);
+    }
+}
+
+// Per node: the 16 cells whose stencils hold it, added in double-float in
+// a fixed order, rounded once to FP64.  Column q = blockIdx.y.
+__global__ void __launch_bounds__(256) k_scatter_nodes_df(MvmGeo geo, const float2* __restrict__ S,
+                                                          double* __restrict__ grid, long long M,
+                                                          int ncell) {
+  const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= M) return;
+  const int q = blockIdx.y;
+  const int u0 = (int)(u / geo.m[1]), u1 = (int)(u % geo.m[1]);
+  float sh = 0.f, sl = 0.f;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int c0 = u0 - a;
+    if (c0 < 0 || c0 >= geo.mc[0]) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int c1 = u1 - b;
+      if (c1 < 0 || c1 >= geo.mc[1]) continue;
+      const float2 x = S[((long long)q * 16 + a * 4 + b) * ncell + (long long)c0 * geo.mc[1] + c1];
+      df_add(sh, sl, x.x, x.y);
+    }
+  }
+  grid[(long long)q * M + u] = (double)sh + (double)sl;
+}
+
 template <class T, int CB, int G>
 void launch_scatter_cells(dski_handle h, T* v, T* S, int s, T sv, T sg, const double* z,
                           const double* beta, cudaStream_t st) {
@@ -605,7 +757,7 @@ __global__ void __launch_bounds__(256) k_gather(MvmGeo g, const int* __restrict_
         sum_columns(dpart, gridDim.x, fin.cs.s, 1, 0, tot, sh);
         alpha_finish(tot, fin.cs);
       } else {
-        sum_columns(fin.part2, gridDim.x, fin.cs.s, 1, 0, tot, sh);
+        sum_columns(fin.part2, fin.nb2 > 0 ? fin.nb2 : (int)gridDim.x, fin.cs.s, 1, 0, tot, sh);
         update_finish(tot, fin.cs, sh);
         __syncthreads();   // active flags settled before beta reads them
         sum_columns(dpart, gridDim.x, fin.cs.s, 1, 0, tot, sh);
@@ -850,8 +1002,27 @@ void set_no_tune(bool on) { g_no_tune = on; }
 // the FP32 d = 2 scatter takes the per-cell passes for cubic stencils
 static bool cells_path(dski_handle h, bool prec64) { return h->d == 2 && !prec64 && h->sw == 4; }
 
+bool df_scatter_path(dski_handle h, bool prec64) {
+  return prec64 && h->prec == DSKI_FP64_TC && !h->kron_exact && h->d == 2 && h->sw == 4 &&
+         h->Wdf.ptr != nullptr;
+}
+
+// lanes per cell of the double-float per-cell pass: about eight points per
+// lane, as the FP32 pass
+static int df_group(dski_handle h) {
+  const double per = (double)h->n / std::max(1, h->mc[0] * h->mc[1]);
+  return per <= 16.0 ? 2 : per <= 32.0 ? 4 : per <= 64.0 ? 8 : per <= 128.0 ? 16 : 32;
+}
+
+int scatter_update_blocks(dski_handle h) {
+  if (df_scatter_path(h, true))
+    return (int)(((long long)h->mc[0] * h->mc[1] * df_group(h) + 255) / 256);
+  return (h->n + 255) / 256;
+}
+
 size_t scatter_ws_bytes(dski_handle h, int s, bool prec64) {
   if (cells_path(h, prec64)) return (size_t)s * 16 * h->mc[0] * h->mc[1] * 4;
+  if (df_scatter_path(h, prec64)) return (size_t)s * 16 * h->mc[0] * h->mc[1] * sizeof(float2);
   if (!(prec64 && h->d >= 2 && s <= 4)) return 0;
   const size_t S = (size_t)h->sw;
   return (size_t)s * h->n * (h->d == 2 ? 2 * S : 2 * S * S) * 8;
@@ -920,6 +1091,33 @@ int scatter_fused(dski_handle h, const void* vin, void* g, int s, bool prec64, v
     else   // two columns per pass: 16 x 4 accumulators capped occupancy at 2 blocks per SM
       scatter_cells_d2<float, 2>(h, (float*)vin, (float*)S, (float*)g, s, 1.f, 1.f, nullptr,
                                  nullptr, st);
+    DSKI_LAUNCHED();
+    return DSKI_OK;
+  }
+  if (df_scatter_path(h, prec64)) {
+    if (up && s > 4) return set_error(DSKI_ERR_ARG, "fused CG update needs s <= 4");
+    float2* S = static_cast<float2*>(ws);
+    if (!S) {
+      if (h->scat_ab.ensure(scatter_ws_bytes(h, s, prec64)))
+        return set_error(DSKI_ERR_ALLOC, "scatter workspace allocation failed");
+      S = h->scat_ab.as<float2>();
+    }
+    const int ncell = h->mc[0] * h->mc[1];
+    const int G = df_group(h);
+    const dim3 gc((unsigned)(((long long)ncell * G + 255) / 256), (unsigned)s);
+    const float2* W = h->Wdf.as<float2>();
+    const int* cs = h->cell_start.as<int>();
+    double* v = (double*)vin;
+    StageScope sc(h, ST_SCATTER, st, 2);
+    switch (G) {
+      case 2: k_scatter_cells_df<2><<<gc, 256, 0, st>>>(cs, W, v, S, h->N, ncell, sv, sg, z, beta, upd); break;
+      case 4: k_scatter_cells_df<4><<<gc, 256, 0, st>>>(cs, W, v, S, h->N, ncell, sv, sg, z, beta, upd); break;
+      case 8: k_scatter_cells_df<8><<<gc, 256, 0, st>>>(cs, W, v, S, h->N, ncell, sv, sg, z, beta, upd); break;
+      case 16: k_scatter_cells_df<16><<<gc, 256, 0, st>>>(cs, W, v, S, h->N, ncell, sv, sg, z, beta, upd); break;
+      default: k_scatter_cells_df<32><<<gc, 256, 0, st>>>(cs, W, v, S, h->N, ncell, sv, sg, z, beta, upd); break;
+    }
+    const dim3 gn((unsigned)((h->M + 255) / 256), (unsigned)s);
+    k_scatter_nodes_df<<<gn, 256, 0, st>>>(geo, S, (double*)g, h->M, ncell);
     DSKI_LAUNCHED();
     return DSKI_OK;
   }

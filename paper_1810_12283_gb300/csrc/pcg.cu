@@ -420,7 +420,9 @@ int cg_run(dski_handle h, CgRun& run) {
   // and ||r||^2 into the preconditioner's scatter pass, r^T z into its
   // gather); one-block kernels finish the sums
   const bool fusedg = fused && gridf && s <= 4;
-  const int nbp = (h->n + 255) / 256;
+  // partial sums per column: the gathers write ceil(n / 256), the fused
+  // scatter of the preconditioner scatter_update_blocks
+  const int nbp = std::max((h->n + 255) / 256, scatter_update_blocks(h));
   double* dpA = fusedg ? wbuf(h->s_dpart, (size_t)3 * nbp * 4 + 16) : nullptr;
   if (fusedg && !dpA) return set_error(DSKI_ERR_ALLOC, "dski_pcg_solve: workspace allocation failed");
   double* dpU = fusedg ? dpA + (size_t)nbp * 4 : nullptr;
@@ -447,6 +449,7 @@ int cg_run(dski_handle h, CgRun& run) {
       fb.cs = cs;
       fb.ticket = tk;
       fb.part2 = dpU;
+      fb.nb2 = scatter_update_blocks(h);
       DSKI_TRY(grid_precond_apply(h, run.pc, R, Z, s, &up, dpZ, &fb));
       return DSKI_OK;
     }

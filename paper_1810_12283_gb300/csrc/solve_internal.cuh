@@ -258,6 +258,7 @@ struct CgFinish {
   ColState cs{};
   unsigned* ticket = nullptr;
   const double* part2 = nullptr;
+  int nb2 = 0;   // partial sums per column in part2 (0: as many as the gather's blocks)
 };
 
 struct CgRun {
