@@ -465,34 +465,6 @@ __device__ __forceinline__ void df_prod(float ah, float al, float bh, float bl, 
   pl = t - (ph - p);
 }
 
-// x = hi + lo with hi = x rounded to a 24-bit significand and lo = fl32(x -
-// hi) (|lo| <= 2^-24 |hi|, lo's rounding <= 2^-48 |x|), from the bit pattern
-// with integer and FP32 operations only: on GB300 every FP64-pipe
-// instruction, conversions included, holds a sub-partition for ~64 cycles.
-// Rounding the pattern (add half an ulp of the 24-bit significand, clear the
-// 29 low bits) carries into the exponent where it must; x - hi is then the
-// integer difference of the patterns in units of x's last place (also
-// across that carry), at most 2^28 in magnitude.  Outside 2^-74 <= |x| <
-// 2^127 (where hi or lo would leave FP32's normal range) the FP64 split.
-__device__ __forceinline__ void split_bits(double x, float& hi, float& lo) {
-  const long long b = __double_as_longlong(x);
-  const int E = (int)((b >> 52) & 0x7FF);
-  if (E < 949 || E > 1149) {
-    split_d(x, hi, lo);
-    return;
-  }
-  const long long mag = b & 0x7FFFFFFFFFFFFFFFLL;
-  const long long r = (mag + (1LL << 28)) & ~((1LL << 29) - 1);   // |hi| as a double pattern
-  const int Er = (int)(r >> 52);
-  const unsigned hb = ((unsigned)(b >> 32) & 0x80000000u) |
-                      ((unsigned)(Er - 1023 + 127) << 23) | (unsigned)((r >> 29) & 0x7FFFFF);
-  hi = __uint_as_float(hb);
-  const int diff = (int)(mag - r);                                   // |x| - |hi| in ulps of x
-  const float scale = __uint_as_float((unsigned)(E - 1075 + 127) << 23);   // 2^(E - 1075)
-  const float l = (float)diff * scale;
-  lo = b < 0 ? -l : l;
-}
-
 template <int G>
 __global__ void __launch_bounds__(256) k_scatter_cells_df(
     const int* __restrict__ cell_start, const float2* __restrict__ Wdf, double* __restrict__ v,
@@ -510,12 +482,6 @@ __global__ void __launch_bounds__(256) k_scatter_cells_df(
     al[k] = 0.f;
   }
   double rs = 0.0;
-  const bool scaled = sv != 1.0 || sg != 1.0;
-  float svh = 1.f, svl = 0.f, sgh = 1.f, sgl = 0.f;
-  if (scaled) {
-    split_d(sv, svh, svl);
-    split_d(sg, sgh, sgl);
-  }
   if (live) {
     const int js = cell_start[c], je = cell_start[c + 1];
     for (int j = js + g; j < je; j += G) {
@@ -541,13 +507,9 @@ __global__ void __launch_bounds__(256) k_scatter_cells_df(
         }
       }
       float vh[3], vl[3];
-#pragma unroll
-      for (int cc = 0; cc < 3; ++cc) split_bits(vv[cc], vh[cc], vl[cc]);
-      if (scaled) {   // v^0 sv, v^1..2 sg in double-float
-        df_prod(vh[0], vl[0], svh, svl, vh[0], vl[0]);
-        df_prod(vh[1], vl[1], sgh, sgl, vh[1], vl[1]);
-        df_prod(vh[2], vl[2], sgh, sgl, vh[2], vl[2]);
-      }
+      split_d(sv * vv[0], vh[0], vl[0]);
+      split_d(sg * vv[1], vh[1], vl[1]);
+      split_d(sg * vv[2], vh[2], vl[2]);
       float2 w[16];   // w0[0..3], dw0[0..3] (dimension 0), w1, dw1 (dimension 1)
       const float4* w4 = reinterpret_cast<const float4*>(Wdf + (long long)j * 16);
 #pragma unroll
