@@ -445,17 +445,22 @@ __global__ void __launch_bounds__(256) k_scatter_nodes(MvmGeo geo, const T* __re
 }
 
 // ------------------------------- FP64_TC scatter, d = 2, double-float ----
-// k_scatter_cells' per-cell pass at FP64-class accuracy on the FP32 units
-// (GB300 runs FP32 ~60x faster than FP64): each point's three values are
-// split into double-float pairs (hi + lo), the stencil weights arrive as
-// pairs (Wdf), and every product and sum is an error-free transformation
-// (FMA exact product, TwoSum), so a cell's 16 sums carry ~2^-48 relative
-// error of the magnitudes they add (FP64: 2^-53).  Before that, in FP64,
-// the CG steps a pass may carry: p = z + beta p (written back), or
-// x += alpha p, r -= alpha q (r written back) with per-block partial sums of
-// ||r||^2 (column q at dpart[q gridDim.x + block]); then v^0 scaled by sv,
-// v^1, v^2 by sg.  Column q = blockIdx.y; G lanes per cell, each a
-// stride-G subset of the cell's points; a fixed butterfly adds the lanes.
+// k_scatter_cells' two passes at FP64-class accuracy on the FP32 units
+// (GB300 runs FP32 ~60x faster than FP64), after a point-parallel pass that
+// does each point's FP64 work with every lane busy:
+//   0. per point (k_scatter_split_df): the CG steps a pass may carry, in
+//      FP64 -- p = z + beta p (written back), or x += alpha p, r -= alpha q
+//      (r written back) with per-block partial sums of ||r||^2 (column q at
+//      dpart[q gridDim.x + block]) -- then v^0 sv, v^1..2 sg, split into
+//      double-float pairs hi + lo (hi = fl32(v), lo = fl32(v - hi));
+//   1. per cell (k_scatter_cells_df): the 16 stencil sums of the cell's
+//      points with the weights as pairs (Wdf), every product and sum an
+//      error-free transformation (FMA exact product, TwoSum), so each sum
+//      carries ~2^-48 relative error of the magnitudes it adds (FP64:
+//      2^-53); G lanes per cell, a fixed butterfly adds the lanes;
+//   2. per node (k_scatter_nodes_df): the 16 cells' sums in a fixed order,
+//      rounded once to FP64.
+// Column q = blockIdx.y in every pass.
 __device__ __forceinline__ void df_prod(float ah, float al, float bh, float bl, float& ph,
                                         float& pl) {
   const float p = ah * bh;
@@ -465,51 +470,79 @@ __device__ __forceinline__ void df_prod(float ah, float al, float bh, float bl, 
   pl = t - (ph - p);
 }
 
-template <int G>
-__global__ void __launch_bounds__(256) k_scatter_cells_df(
-    const int* __restrict__ cell_start, const float2* __restrict__ Wdf, double* __restrict__ v,
-    float2* __restrict__ S, long long N, int ncell, double sv, double sg,
+__global__ void __launch_bounds__(256) k_scatter_split_df(
+    double* __restrict__ v, float2* __restrict__ Vdf, int n, long long N, double sv, double sg,
     const double* __restrict__ z, const double* __restrict__ beta, CgUpdate up) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.y;
+  const bool live = j < n;
+  const bool upd = up.x != nullptr && up.active[q] != 0;
+  double rs = 0.0;
+  if (live) {
+    const long long o = (long long)q * N + (long long)j * 3;
+    double vv[3] = {v[o], v[o + 1], v[o + 2]};
+    if (z) {
+      const double be = beta[q];
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        vv[cc] = fma(be, vv[cc], z[o + cc]);
+        v[o + cc] = vv[cc];
+      }
+    }
+    if (upd) {
+      const double alpha = up.alpha[q];
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        up.x[o + cc] = fma(alpha, up.p[o + cc], up.x[o + cc]);
+        vv[cc] = fma(-alpha, up.q[o + cc], vv[cc]);
+        v[o + cc] = vv[cc];
+        rs = fma(vv[cc], vv[cc], rs);
+      }
+    }
+    float2* out = Vdf + ((long long)q * n + j) * 3;
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      float hi, lo;
+      split_d((cc == 0 ? sv : sg) * vv[cc], hi, lo);
+      out[cc] = make_float2(hi, lo);
+    }
+  }
+  if (up.x) {
+    __shared__ double red[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double t = rs;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) red[w] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b = 0.0;
+      for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) b += red[ww];
+      up.dpart[(long long)q * gridDim.x + blockIdx.x] = b;
+    }
+  }
+}
+
+template <int G>
+__global__ void __launch_bounds__(256) k_scatter_cells_df(const int* __restrict__ cell_start,
+                                                          const float2* __restrict__ Wdf,
+                                                          const float2* __restrict__ Vdf, int n,
+                                                          float2* __restrict__ S, int ncell) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int c = (int)(t / G), g = (int)(t % G);
   const bool live = c < ncell;   // whole groups: G | 32
   const int q = blockIdx.y;
-  const bool upd = up.x != nullptr && up.active[q] != 0;
   float ah[16], al[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
     ah[k] = 0.f;
     al[k] = 0.f;
   }
-  double rs = 0.0;
   if (live) {
     const int js = cell_start[c], je = cell_start[c + 1];
     for (int j = js + g; j < je; j += G) {
-      const long long o = (long long)q * N + (long long)j * 3;
-      double* vj = v + o;
-      double vv[3] = {vj[0], vj[1], vj[2]};
-      if (z) {
-        const double be = beta[q];
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc) {
-          vv[cc] = fma(be, vv[cc], z[o + cc]);
-          vj[cc] = vv[cc];
-        }
-      }
-      if (upd) {
-        const double alpha = up.alpha[q];
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc) {
-          up.x[o + cc] = fma(alpha, up.p[o + cc], up.x[o + cc]);
-          vv[cc] = fma(-alpha, up.q[o + cc], vv[cc]);
-          vj[cc] = vv[cc];
-          rs = fma(vv[cc], vv[cc], rs);
-        }
-      }
-      float vh[3], vl[3];
-      split_d(sv * vv[0], vh[0], vl[0]);
-      split_d(sg * vv[1], vh[1], vl[1]);
-      split_d(sg * vv[2], vh[2], vl[2]);
+      const float2* vj = Vdf + ((long long)q * n + j) * 3;
+      const float2 v0 = vj[0], v1 = vj[1], v2 = vj[2];
       float2 w[16];   // w0[0..3], dw0[0..3] (dimension 0), w1, dw1 (dimension 1)
       const float4* w4 = reinterpret_cast<const float4*>(Wdf + (long long)j * 16);
 #pragma unroll
@@ -522,15 +555,15 @@ __global__ void __launch_bounds__(256) k_scatter_cells_df(
       for (int a = 0; a < 4; ++a) {
         // A = w0_a v0 + dw0_a v1, B = w0_a v2 (sum-factorised over dimension 0)
         float Ah, Al, Bh, Bl;
-        df_prod(w[a].x, w[a].y, vh[0], vl[0], Ah, Al);
-        df_fma(w[4 + a].x, w[4 + a].y, vh[1], vl[1], Ah, Al);
+        df_prod(w[a].x, w[a].y, v0.x, v0.y, Ah, Al);
+        df_fma(w[4 + a].x, w[4 + a].y, v1.x, v1.y, Ah, Al);
         {
           float sh, se;
           two_sum(Ah, Al, sh, se);
           Ah = sh;
           Al = se;
         }
-        df_prod(w[a].x, w[a].y, vh[2], vl[2], Bh, Bl);
+        df_prod(w[a].x, w[a].y, v2.x, v2.y, Bh, Bl);
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
           df_fma(w[8 + b].x, w[8 + b].y, Ah, Al, ah[a * 4 + b], al[a * 4 + b]);
@@ -547,20 +580,6 @@ __global__ void __launch_bounds__(256) k_scatter_cells_df(
       const float ol = __shfl_xor_sync(0xffffffffu, al[k], o);
       df_add(ah[k], al[k], oh, ol);
     }
-  if (up.x) {
-    __shared__ double red[8];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    double tsum = rs;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tsum += __shfl_xor_sync(0xffffffffu, tsum, o);
-    if (lane == 0) red[w] = tsum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double b = 0.0;
-      for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) b += red[ww];
-      up.dpart[(long long)q * gridDim.x + blockIdx.x] = b;
-    }
-  }
   if (!live) return;
 #pragma unroll
   for (int k = 0; k < 16; ++k)
@@ -1014,15 +1033,12 @@ static int df_group(dski_handle h) {
   return per <= 16.0 ? 2 : per <= 32.0 ? 4 : per <= 64.0 ? 8 : per <= 128.0 ? 16 : 32;
 }
 
-int scatter_update_blocks(dski_handle h) {
-  if (df_scatter_path(h, true))
-    return (int)(((long long)h->mc[0] * h->mc[1] * df_group(h) + 255) / 256);
-  return (h->n + 255) / 256;
-}
+int scatter_update_blocks(dski_handle h) { return (h->n + 255) / 256; }
 
 size_t scatter_ws_bytes(dski_handle h, int s, bool prec64) {
   if (cells_path(h, prec64)) return (size_t)s * 16 * h->mc[0] * h->mc[1] * 4;
-  if (df_scatter_path(h, prec64)) return (size_t)s * 16 * h->mc[0] * h->mc[1] * sizeof(float2);
+  if (df_scatter_path(h, prec64))   // cell planes, then the points' double-float values
+    return (size_t)s * (16 * (size_t)h->mc[0] * h->mc[1] + 3 * (size_t)h->n) * sizeof(float2);
   if (!(prec64 && h->d >= 2 && s <= 4)) return 0;
   const size_t S = (size_t)h->sw;
   return (size_t)s * h->n * (h->d == 2 ? 2 * S : 2 * S * S) * 8;
@@ -1103,18 +1119,20 @@ int scatter_fused(dski_handle h, const void* vin, void* g, int s, bool prec64, v
       S = h->scat_ab.as<float2>();
     }
     const int ncell = h->mc[0] * h->mc[1];
+    float2* Vdf = S + (size_t)s * 16 * ncell;   // s x n x 3 pairs after the cell planes
     const int G = df_group(h);
-    const dim3 gc((unsigned)(((long long)ncell * G + 255) / 256), (unsigned)s);
     const float2* W = h->Wdf.as<float2>();
     const int* cs = h->cell_start.as<int>();
-    double* v = (double*)vin;
-    StageScope sc(h, ST_SCATTER, st, 2);
+    StageScope sc(h, ST_SCATTER, st, 3);
+    k_scatter_split_df<<<dim3((unsigned)((h->n + 255) / 256), (unsigned)s), 256, 0, st>>>(
+        (double*)vin, Vdf, h->n, h->N, sv, sg, z, beta, upd);
+    const dim3 gc((unsigned)(((long long)ncell * G + 255) / 256), (unsigned)s);
     switch (G) {
-      case 2: k_scatter_cells_df<2><<<gc, 256, 0, st>>>(cs, W, v, S, h->N, ncell, sv, sg, z, beta, upd); break;
-      case 4: k_scatter_cells_df<4><<<gc, 256, 0, st>>>(cs, W, v, S, h->N, ncell, sv, sg, z, beta, upd); break;
-      case 8: k_scatter_cells_df<8><<<gc, 256, 0, st>>>(cs, W, v, S, h->N, ncell, sv, sg, z, beta, upd); break;
-      case 16: k_scatter_cells_df<16><<<gc, 256, 0, st>>>(cs, W, v, S, h->N, ncell, sv, sg, z, beta, upd); break;
-      default: k_scatter_cells_df<32><<<gc, 256, 0, st>>>(cs, W, v, S, h->N, ncell, sv, sg, z, beta, upd); break;
+      case 2: k_scatter_cells_df<2><<<gc, 256, 0, st>>>(cs, W, Vdf, h->n, S, ncell); break;
+      case 4: k_scatter_cells_df<4><<<gc, 256, 0, st>>>(cs, W, Vdf, h->n, S, ncell); break;
+      case 8: k_scatter_cells_df<8><<<gc, 256, 0, st>>>(cs, W, Vdf, h->n, S, ncell); break;
+      case 16: k_scatter_cells_df<16><<<gc, 256, 0, st>>>(cs, W, Vdf, h->n, S, ncell); break;
+      default: k_scatter_cells_df<32><<<gc, 256, 0, st>>>(cs, W, Vdf, h->n, S, ncell); break;
     }
     const dim3 gn((unsigned)((h->M + 255) / 256), (unsigned)s);
     k_scatter_nodes_df<<<gn, 256, 0, st>>>(geo, S, (double*)g, h->M, ncell);
