@@ -199,9 +199,11 @@ int mvm_pcg_fused(dski_handle h, double* P, const double* Z, const double* beta,
 // FP64 gather: vout^0 = av (B grid)^0 + nv vin^0, vout^p = ag (B grid)^p + ng vin^p;
 // with dpart, per-block partial sums of vin^T vout per column
 // (dpart[q nblocks + block], nblocks = ceil(n / 256))
+// grid_scratch: the grid is the caller's scratch, which FP64_TC (d = 2,
+// cubic) may overwrite with its double-float split for the FP32-unit gather
 int gather_scaled(dski_handle h, const double* grid, const double* vin, double* vout, int s,
                   double av, double ag, double nv, double ng, int stage, double* dpart = nullptr,
-                  const CgFinish* fin = nullptr);
+                  const CgFinish* fin = nullptr, bool grid_scratch = false);
 // tc_ws: caller memory for the MIXED modes' tensor-core partials (the
 // largest mode_tc_tf32_ws_bytes over the modes); NULL = the handle's workspace
 int kron_internal(dski_handle h, void* g, void* tmp, int s, bool prec64, int dfactor,

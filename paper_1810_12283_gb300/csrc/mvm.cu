@@ -627,6 +627,45 @@ void launch_scatter_cells(dski_handle h, T* v, T* S, int s, T sv, T sg, const do
                                                   s, h->N, ncell, sv, sg, z, beta);
 }
 
+// The gather's optional CG work: per-block partial sums of v^T out per
+// column (fixed tree) to dpart[q gridDim.x + block], and a folded CG
+// finisher: the last block completes the partial sums (fixed block order)
+// and updates the device scalars.  All threads of every block call it.
+template <int CB>
+__device__ __forceinline__ void gather_partials(const double (&dsum)[CB], double* dpart, int q0,
+                                                int s, CgFinish fin) {
+  if (!dpart) return;
+  __shared__ double red[8][CB];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < CB; ++q) {
+    double t = dsum[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) red[w][q] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < CB && q0 + (int)threadIdx.x < s) {
+    double t = 0.0;
+    for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t += red[ww][threadIdx.x];
+    dpart[(long long)(q0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+  }
+  if (fin.kind >= 0 && last_block(fin.ticket, gridDim.x * gridDim.y)) {
+    __shared__ double sh[32];
+    __shared__ double tot[CG_MAXS];
+    if (fin.kind == 0) {
+      sum_columns(dpart, gridDim.x, fin.cs.s, 1, 0, tot, sh);
+      alpha_finish(tot, fin.cs);
+    } else {
+      sum_columns(fin.part2, fin.nb2 > 0 ? fin.nb2 : (int)gridDim.x, fin.cs.s, 1, 0, tot, sh);
+      update_finish(tot, fin.cs, sh);
+      __syncthreads();   // active flags settled before beta reads them
+      sum_columns(dpart, gridDim.x, fin.cs.s, 1, 0, tot, sh);
+      beta_finish(tot, fin.cs, 0);
+    }
+  }
+}
+
 // -------------------------------------------------------------- gather ----
 // out_j^0 = av sum_u w_j(u) h(u) + nv v_j^0,
 // out_j^p = ag sum_u dw_{j,p}(u) h(u) + ng v_j^p,
@@ -749,41 +788,85 @@ __global__ void __launch_bounds__(256) k_gather(MvmGeo g, const int* __restrict_
         for (int cc = 0; cc <= D; ++cc) dsum[q] = fma((double)vq[cc], (double)o[cc], dsum[q]);
     }
   }
-  // optional: per-block partial sums of v^T out per column (fixed tree),
-  // dpart[q gridDim.x + block] -- the CG dot fused into the gather
-  if (dpart) {
-    __shared__ double red[8][CB];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  gather_partials<CB>(dsum, dpart, q0, s, fin);
+}
+
+// ------------------------------- FP64_TC gather, d = 2, double-float ----
+// The gather's stencil sums on the FP32 units at FP64-class accuracy: the
+// grid (FP64) is first split in place into double-float pairs (hi =
+// fl32(x), lo = fl32(x - hi); 8 bytes per node either way), then each point
+// forms its value and two derivative sums from the pairs and its weights
+// (Wdf) with error-free products and TwoSum sums (~2^-48 of the magnitudes
+// added), rounds each once to FP64 and finishes in FP64 exactly as k_gather:
+// out^0 = av r^0 + nv v^0, out^p = ag r^p + ng v^p, the partial sums of
+// v^T out and the folded CG finisher.  Column q = blockIdx.y.
+__global__ void __launch_bounds__(256) k_grid_split_df(double* __restrict__ grid, long long count) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  float hi, lo;
+  split_d(grid[i], hi, lo);
+  reinterpret_cast<float2*>(grid)[i] = make_float2(hi, lo);
+}
+
+__global__ void __launch_bounds__(256) k_gather_df(MvmGeo g, const int* __restrict__ cell,
+                                                   const float2* __restrict__ Wdf,
+                                                   const float2* __restrict__ G,
+                                                   const double* __restrict__ v,
+                                                   double* __restrict__ out, int s, int n,
+                                                   long long N, long long M, double nv, double ng,
+                                                   double av, double ag, double* __restrict__ dpart,
+                                                   CgFinish fin) {
+  const int jt = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = jt < n;
+  const int j = live ? jt : n - 1;   // dead threads redo the last point, write nothing
+  const int q = blockIdx.y;
+  double dsum[1] = {0.0};
+  const int t = cell[j];
+  const int f0 = t / g.mc[1], f1 = t - f0 * g.mc[1];
+  const int m1 = g.m[1];
+  const float2* hq = G + (long long)q * M + (long long)f0 * m1 + f1;
+  float2 w[16];   // w0[0..3], dw0[0..3], w1[0..3], dw1[0..3]
+  const float4* w4 = reinterpret_cast<const float4*>(Wdf + (long long)j * 16);
 #pragma unroll
-    for (int q = 0; q < CB; ++q) {
-      double t = dsum[q];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) red[w][q] = t;
-    }
-    __syncthreads();
-    if (threadIdx.x < CB && q0 + (int)threadIdx.x < s) {
-      double t = 0.0;
-      for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t += red[ww][threadIdx.x];
-      dpart[(long long)(q0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
-    }
-    // a folded CG finisher: the last block completes the partial sums
-    // (fixed block order) and updates the device scalars
-    if (fin.kind >= 0 && last_block(fin.ticket, gridDim.x * gridDim.y)) {
-      __shared__ double sh[32];
-      __shared__ double tot[CG_MAXS];
-      if (fin.kind == 0) {
-        sum_columns(dpart, gridDim.x, fin.cs.s, 1, 0, tot, sh);
-        alpha_finish(tot, fin.cs);
-      } else {
-        sum_columns(fin.part2, fin.nb2 > 0 ? fin.nb2 : (int)gridDim.x, fin.cs.s, 1, 0, tot, sh);
-        update_finish(tot, fin.cs, sh);
-        __syncthreads();   // active flags settled before beta reads them
-        sum_columns(dpart, gridDim.x, fin.cs.s, 1, 0, tot, sh);
-        beta_finish(tot, fin.cs, 0);
-      }
-    }
+  for (int k = 0; k < 8; ++k) {
+    const float4 x = __ldg(w4 + k);
+    w[2 * k] = make_float2(x.x, x.y);
+    w[2 * k + 1] = make_float2(x.z, x.w);
   }
+  float r0h = 0.f, r0l = 0.f, r1h = 0.f, r1l = 0.f, r2h = 0.f, r2l = 0.f;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    float th = 0.f, tl = 0.f, uh = 0.f, ul = 0.f;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const float2 x = hq[(long long)a * m1 + b];
+      df_fma(w[8 + b].x, w[8 + b].y, x.x, x.y, th, tl);
+      df_fma(w[12 + b].x, w[12 + b].y, x.x, x.y, uh, ul);
+    }
+    float sh, se;
+    two_sum(th, tl, sh, se);
+    th = sh;
+    tl = se;
+    two_sum(uh, ul, sh, se);
+    uh = sh;
+    ul = se;
+    df_fma(w[a].x, w[a].y, th, tl, r0h, r0l);
+    df_fma(w[4 + a].x, w[4 + a].y, th, tl, r1h, r1l);
+    df_fma(w[a].x, w[a].y, uh, ul, r2h, r2l);
+  }
+  const double r[3] = {(double)r0h + (double)r0l, (double)r1h + (double)r1l,
+                       (double)r2h + (double)r2l};
+  const long long e = (long long)q * N + (long long)j * 3;
+  const double o0 = av * r[0] + nv * v[e];
+  const double o1 = ag * r[1] + ng * v[e + 1];
+  const double o2 = ag * r[2] + ng * v[e + 2];
+  if (live) {
+    out[e] = o0;
+    out[e + 1] = o1;
+    out[e + 2] = o2;
+    if (dpart) dsum[0] = fma(v[e], o0, fma(v[e + 1], o1, v[e + 2] * o2));
+  }
+  gather_partials<1>(dsum, dpart, q, s, fin);
 }
 
 // --------------------------------------------------- SIMT mode product ----
@@ -885,6 +968,9 @@ struct GatherScale {
   int stage = ST_GATHER;
   double* dpart = nullptr;     // per-block partial sums of v^T out (FP64 only)
   CgFinish fin{};              // finisher folded into the last block (with dpart)
+  // the grid is the caller's scratch: FP64_TC (d = 2, cubic) may split it
+  // in place and take the double-float gather
+  bool grid_scratch = false;
 };
 
 template <class T, int D, int CB, int S>
@@ -892,6 +978,19 @@ void launch_gather(dski_handle h, const MvmGeo& g, const T* wt, const T* grid, c
                    T* out, int s, cudaStream_t st, const GatherScale& gs) {
   // FP32 gathers evaluate the weights from the FP32 fractions
   if constexpr (std::is_same<T, float>::value) wt = h->frac32.as<float>();
+  if constexpr (std::is_same<T, double>::value && D == 2 && S == 4) {
+    if (gs.grid_scratch && df_scatter_path(h, true)) {
+      StageScope sc(h, gs.stage, st, 2);
+      const long long cnt = (long long)h->M * s;
+      double* gw = const_cast<double*>(grid);
+      k_grid_split_df<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(gw, cnt);
+      k_gather_df<<<dim3((unsigned)((h->n + 255) / 256), (unsigned)s), 256, 0, st>>>(
+          g, h->cell.as<int>(), h->Wdf.as<float2>(), reinterpret_cast<const float2*>(gw), v, out,
+          s, h->n, (long long)h->N, (long long)h->M, gs.nv, gs.ng, gs.av, gs.ag, gs.dpart,
+          gs.fin);
+      return;
+    }
+  }
   dim3 grd((unsigned)((h->n + 255) / 256), (unsigned)((s + CB - 1) / CB));
   StageScope sc(h, gs.stage, st);
   k_gather<T, D, CB, S><<<grd, 256, 0, st>>>(g, h->cell.as<int>(), wt, grid, v, out, s, h->n,
@@ -1275,7 +1374,7 @@ int mvm_internal(dski_handle h, const void* vin, void* vout, int s, bool prec64)
 
 int gather_scaled(dski_handle h, const double* grid, const double* vin, double* vout, int s,
                   double av, double ag, double nv, double ng, int stage, double* dpart,
-                  const CgFinish* fin) {
+                  const CgFinish* fin, bool grid_scratch) {
   if (fin && fin->kind >= 0 && !dpart)
     return set_error(DSKI_ERR_ARG, "a folded CG finisher needs the gather's partial sums");
   const MvmGeo geo = make_geo(h);
@@ -1287,6 +1386,7 @@ int gather_scaled(dski_handle h, const double* grid, const double* vin, double* 
   gs.stage = stage;
   gs.dpart = dpart;
   if (fin) gs.fin = *fin;
+  gs.grid_scratch = grid_scratch;
   const double* fr = h->W64.as<double>();
   switch (h->d) {
     case 1: gather_dispatch<double, 1>(h, geo, fr, grid, vin, vout, s, h->stream, &gs); break;
@@ -1332,8 +1432,9 @@ int mvm_pcg_fused(dski_handle h, double* P, const double* Z, const double* beta,
   DSKI_TRY(kron_internal(h, h->gridA.ptr, h->gridB.ptr, s, true, -1, nullptr, &res));
   if (!dpart) return gather_internal(h, res, P, Q, s, true);
   // the gather also leaves per-block partial sums of p^T q
+  // (the product grid is this call's scratch)
   return gather_scaled(h, (const double*)res, P, Q, s, 1.0, 1.0, h->nv, h->ng, ST_GATHER, dpart,
-                       fin);
+                       fin, true);
 }
 
 int permute_in(dski_handle h, const void* v_user, void* v_int, int s, bool f64, cudaStream_t st) {

@@ -336,8 +336,10 @@ int grid_precond_apply(dski_handle h, pivchol_handle pc, const double* R, double
     }
     DSKI_LAUNCHED();
     // Z = (R - B h') ./ noise
+    // (hp is this call's scratch)
     DSKI_TRY(gather_scaled(h, hp, R + (size_t)c0 * N, Z + (size_t)c0 * N, q, -1.0 / pc->nv,
-                           -1.0 / pc->ng, 1.0 / pc->nv, 1.0 / pc->ng, ST_PRECOND, dpart_rz, fin));
+                           -1.0 / pc->ng, 1.0 / pc->nv, 1.0 / pc->ng, ST_PRECOND, dpart_rz, fin,
+                           true));
   }
   return DSKI_OK;
 }
