@@ -451,8 +451,9 @@ __global__ void __launch_bounds__(256) k_scatter_nodes(MvmGeo geo, const T* __re
 //   0. per point (k_scatter_split_df): the CG steps a pass may carry, in
 //      FP64 -- p = z + beta p (written back), or x += alpha p, r -= alpha q
 //      (r written back) with per-block partial sums of ||r||^2 (column q at
-//      dpart[q gridDim.x + block]) -- then v^0 sv, v^1..2 sg, split into
-//      double-float pairs hi + lo (hi = fl32(v), lo = fl32(v - hi));
+//      dpart[q gridDim.x + block]) -- then each value split into a
+//      double-float pair hi + lo (split_trunc, < 2^-47) and v^0 scaled by
+//      sv, v^1..2 by sg in double-float;
 //   1. per cell (k_scatter_cells_df): the 16 stencil sums of the cell's
 //      points with the weights as pairs (Wdf), every product and sum an
 //      error-free transformation (FMA exact product, TwoSum), so each sum
@@ -470,9 +471,34 @@ __device__ __forceinline__ void df_prod(float ah, float al, float bh, float bl, 
   pl = t - (ph - p);
 }
 
+// x = hi + lo + e with |e| < 2^-47 |x|: hi is x truncated to a 24-bit
+// significand and lo the next 24 bits of x's significand (truncated), both
+// assembled from the bit pattern with integer operations.  split_d's
+// conversions and subtraction run on GB300's FP64 pipe, which bound the
+// point pass (ncu: 64% busy); these need none.  Outside 2^-79 <= |x| <
+// 2^128 (where hi or lo would leave FP32's normal range): split_d.
+__device__ __forceinline__ void split_trunc(double x, float& hi, float& lo) {
+  const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+  const int E = (int)((hw >> 20) & 0x7FF);
+  if (E < 944 || E > 1150) {
+    split_d(x, hi, lo);
+    return;
+  }
+  const unsigned sign = hw & 0x80000000u;
+  hi = __uint_as_float(sign | ((unsigned)(E - 896) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
+  const unsigned r24 = (lw & 0x1FFFFFFFu) >> 5;
+  if (r24 == 0) {
+    lo = 0.f;
+    return;
+  }
+  const int lz = __clz(r24) - 8;   // leading zeros within the 24 bits
+  lo = __uint_as_float(sign | ((unsigned)(E - 920 - lz) << 23) | ((r24 << lz) & 0x7FFFFFu));
+}
+
+// sv, sg as double-float pairs (split on the host); scaled: apply them
 __global__ void __launch_bounds__(256) k_scatter_split_df(
-    double* __restrict__ v, float2* __restrict__ Vdf, int n, long long N, double sv, double sg,
-    const double* __restrict__ z, const double* __restrict__ beta, CgUpdate up) {
+    double* __restrict__ v, float2* __restrict__ Vdf, int n, long long N, bool scaled, float2 svp,
+    float2 sgp, const double* __restrict__ z, const double* __restrict__ beta, CgUpdate up) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int q = blockIdx.y;
   const bool live = j < n;
@@ -503,7 +529,11 @@ __global__ void __launch_bounds__(256) k_scatter_split_df(
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {
       float hi, lo;
-      split_d((cc == 0 ? sv : sg) * vv[cc], hi, lo);
+      split_trunc(vv[cc], hi, lo);
+      if (scaled) {   // v^0 sv, v^1..2 sg, in double-float
+        const float2 sc = cc == 0 ? svp : sgp;
+        df_prod(hi, lo, sc.x, sc.y, hi, lo);
+      }
       out[cc] = make_float2(hi, lo);
     }
   }
@@ -793,8 +823,8 @@ __global__ void __launch_bounds__(256) k_gather(MvmGeo g, const int* __restrict_
 
 // ------------------------------- FP64_TC gather, d = 2, double-float ----
 // The gather's stencil sums on the FP32 units at FP64-class accuracy: the
-// grid (FP64) is first split in place into double-float pairs (hi =
-// fl32(x), lo = fl32(x - hi); 8 bytes per node either way), then each point
+// grid (FP64) is first split in place into double-float pairs (split_trunc;
+// 8 bytes per node either way), then each point
 // forms its value and two derivative sums from the pairs and its weights
 // (Wdf) with error-free products and TwoSum sums (~2^-48 of the magnitudes
 // added), rounds each once to FP64 and finishes in FP64 exactly as k_gather:
@@ -804,7 +834,7 @@ __global__ void __launch_bounds__(256) k_grid_split_df(double* __restrict__ grid
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
   float hi, lo;
-  split_d(grid[i], hi, lo);
+  split_trunc(grid[i], hi, lo);
   reinterpret_cast<float2*>(grid)[i] = make_float2(hi, lo);
 }
 
@@ -1223,8 +1253,12 @@ int scatter_fused(dski_handle h, const void* vin, void* g, int s, bool prec64, v
     const float2* W = h->Wdf.as<float2>();
     const int* cs = h->cell_start.as<int>();
     StageScope sc(h, ST_SCATTER, st, 3);
+    auto pair = [](double x) {
+      const float hi = (float)x;
+      return make_float2(hi, (float)(x - (double)hi));
+    };
     k_scatter_split_df<<<dim3((unsigned)((h->n + 255) / 256), (unsigned)s), 256, 0, st>>>(
-        (double*)vin, Vdf, h->n, h->N, sv, sg, z, beta, upd);
+        (double*)vin, Vdf, h->n, h->N, sv != 1.0 || sg != 1.0, pair(sv), pair(sg), z, beta, upd);
     const dim3 gc((unsigned)(((long long)ncell * G + 255) / 256), (unsigned)s);
     switch (G) {
       case 2: k_scatter_cells_df<2><<<gc, 256, 0, st>>>(cs, W, Vdf, h->n, S, ncell); break;
