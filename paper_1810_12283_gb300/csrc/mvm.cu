@@ -358,7 +358,60 @@ __global__ void __launch_bounds__(256) k_scatter_cells(const int* __restrict__ c
   for (int q = 0; q < CB; ++q)
 #pragma unroll
     for (int k = 0; k < 16; ++k) acc[q][k] = T(0);
-  if (live) {
+  // one point's contribution, its values already loaded: the weights from
+  // its two cell fractions, the scalings, the sum-factorised stencil
+  auto add_point = [&](const T2v<T>& fr, T (&vp)[CB][3]) {
+    T w[16];
+    keys4<T>(fr.x, w, w + 4);
+    keys4<T>(fr.y, w + 8, w + 12);
+#pragma unroll
+    for (int q = 0; q < CB; ++q) {
+      const T v0 = vp[q][0] * sv, v1 = vp[q][1] * (sg * ih0), v2 = vp[q][2] * (sg * ih1);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const T ca = fma(w[a], v0, w[4 + a] * v1);
+        const T ea = w[a] * v2;
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          acc[q][a * 4 + b] = fma(w[8 + b], ca, fma(w[12 + b], ea, acc[q][a * 4 + b]));
+      }
+    }
+  };
+  if (live && !z) {
+    // two points per lane and trip, both points' loads issued before either
+    // is used: one point per trip left too few loads in flight for HBM
+    const int js = cell_start[c], je = cell_start[c + 1];
+    int j = js + g;
+    for (; j + G < je; j += 2 * G) {
+      const T2v<T> fa = ld2(frac + 2 * (long long)j), fb = ld2(frac + 2 * (long long)(j + G));
+      T va[CB][3], vb[CB][3];
+#pragma unroll
+      for (int q = 0; q < CB; ++q) {
+        const bool on = q0 + q < s;
+        const T* pa = v + (long long)(q0 + q) * N + (long long)j * 3;
+        const T* pb = pa + 3 * (long long)G;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+          va[q][cc] = on ? pa[cc] : T(0);
+          vb[q][cc] = on ? pb[cc] : T(0);
+        }
+      }
+      add_point(fa, va);
+      add_point(fb, vb);
+    }
+    if (j < je) {
+      const T2v<T> fa = ld2(frac + 2 * (long long)j);
+      T va[CB][3];
+#pragma unroll
+      for (int q = 0; q < CB; ++q) {
+        const bool on = q0 + q < s;
+        const T* pa = v + (long long)(q0 + q) * N + (long long)j * 3;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) va[q][cc] = on ? pa[cc] : T(0);
+      }
+      add_point(fa, va);
+    }
+  } else if (live) {
     const int js = cell_start[c], je = cell_start[c + 1];
     for (int j = js + g; j < je; j += G) {
       // the point's weights from its two cell fractions (the 12 bytes of
