@@ -874,6 +874,70 @@ __global__ void __launch_bounds__(256) k_gather(MvmGeo g, const int* __restrict_
   gather_partials<CB>(dsum, dpart, q0, s, fin);
 }
 
+// ----------------------------------------------- FP32 gather, d = 2 ----
+// The MIXED modes' gather without partial sums (cubic stencil): two
+// consecutive points per thread, every load of both points (cells,
+// fractions, the 2 x 16 grid values, v) issued before either point's sums,
+// since one point per thread left too few loads in flight for HBM.  The
+// weights come from the FP32 fractions; the sums are k_gather's.  Column
+// q = blockIdx.y.
+__global__ void __launch_bounds__(256) k_gather2_f32(MvmGeo g, const int* __restrict__ cell,
+                                                     const float* __restrict__ frac,
+                                                     const float* __restrict__ grid,
+                                                     const float* __restrict__ v,
+                                                     float* __restrict__ out, int n, long long N,
+                                                     long long M, float nv, float ng, float av,
+                                                     float ag) {
+  const int j0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (j0 >= n) return;
+  const bool two = j0 + 1 < n;
+  const int jp[2] = {j0, two ? j0 + 1 : j0};
+  const int q = blockIdx.y;
+  const int m1 = g.m[1], mc1 = g.mc[1];
+  float x[2][16], fr[2][2], vv[2][3];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int c = __ldg(cell + jp[u]);
+    const T2v<float> f = ld2(frac + 2 * (long long)jp[u]);
+    fr[u][0] = f.x;
+    fr[u][1] = f.y;
+    const int f0 = c / mc1, f1 = c - f0 * mc1;
+    const float* hq = grid + (long long)q * M + (long long)f0 * m1 + f1;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) x[u][a * 4 + b] = __ldg(hq + (long long)a * m1 + b);
+    const float* vq = v + (long long)q * N + (long long)jp[u] * 3;
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) vv[u][cc] = vq[cc];
+  }
+  const float ih0 = (float)g.invh[0], ih1 = (float)g.invh[1];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    if (u == 1 && !two) break;
+    float w0[4], dw0[4], w1[4], dw1[4];
+    stencil_weights<4, float>(fr[u][0], w0, dw0);
+    stencil_weights<4, float>(fr[u][1], w1, dw1);
+    float r0 = 0.f, r1 = 0.f, r2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      float rw = 0.f, rd = 0.f;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        rw += w1[b] * x[u][a * 4 + b];
+        rd += dw1[b] * x[u][a * 4 + b];
+      }
+      r0 += w0[a] * rw;
+      r1 += dw0[a] * rw;
+      r2 += w0[a] * rd;
+    }
+    float* oq = out + (long long)q * N + (long long)jp[u] * 3;
+    oq[0] = av * r0 + nv * vv[u][0];
+    oq[1] = ag * (r1 * ih0) + ng * vv[u][1];
+    oq[2] = ag * (r2 * ih1) + ng * vv[u][2];
+  }
+}
+
 // ------------------------------- FP64_TC gather, d = 2, double-float ----
 // The gather's stencil sums on the FP32 units at FP64-class accuracy: the
 // grid (FP64) is first split in place into double-float pairs (split_trunc;
@@ -1061,6 +1125,16 @@ void launch_gather(dski_handle h, const MvmGeo& g, const T* wt, const T* grid, c
                    T* out, int s, cudaStream_t st, const GatherScale& gs) {
   // FP32 gathers evaluate the weights from the FP32 fractions
   if constexpr (std::is_same<T, float>::value) wt = h->frac32.as<float>();
+  if constexpr (std::is_same<T, float>::value && D == 2 && S == 4) {
+    if (!gs.dpart) {
+      StageScope sc(h, gs.stage, st);
+      const unsigned nt = (unsigned)((h->n + 1) / 2);
+      k_gather2_f32<<<dim3((nt + 255) / 256, (unsigned)s), 256, 0, st>>>(
+          g, h->cell.as<int>(), wt, grid, v, out, h->n, (long long)h->N, (long long)h->M,
+          (float)gs.nv, (float)gs.ng, (float)gs.av, (float)gs.ag);
+      return;
+    }
+  }
   if constexpr (std::is_same<T, double>::value && D == 2 && S == 4) {
     if (gs.grid_scratch && df_scatter_path(h, true)) {
       StageScope sc(h, gs.stage, st, 2);
