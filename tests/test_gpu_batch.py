@@ -46,16 +46,18 @@ def test_solve_many_matches_single_solves():
 # ---- the persistent launch (dski_pcg_solve_batch) -------------------------
 
 def _persistent_cases():
+    from tests._gpu_helpers import problem_1d
     probs = _small_instances(7)
     q = dict(W.small2d(300, m=21, seed=5))   # quintic stencil, no preconditioner
     q["interp"] = "quintic"
+    probs.insert(3, problem_1d(300, m=40, seed=2))   # d = 1
     probs.append(q)
     return probs
 
 
 @pytest.mark.parametrize("cluster", [1, 2, 4, 8])
 def test_persistent_batch_meets_the_oracle_system(cluster):
-    """Every system of one persistent launch -- 2-D and 3-D, cubic and
+    """Every system of one persistent launch -- 1-D, 2-D and 3-D, cubic and
     quintic, with and without a preconditioner -- reaches the FP64 tolerance
     by its own true residual and satisfies the oracle's system, whether one
     CTA or a cluster of 2, 4 or 8 CTAs solves each system."""
