@@ -649,6 +649,12 @@ MULTI_ORACLE_SAMPLE = 16
 
 
 def run_multi(args):
+    """--multi: print multi_instance_result's line."""
+    print(json.dumps(multi_instance_result(args)), flush=True)
+    return 0
+
+
+def multi_instance_result(args):
     """The uneven multi-instance workload: 256 independent GP-with-gradient
     problems (d in {2, 3}, n log-uniform in [200, 5000], 48^2 or 24^3 grids,
     rank-32 pivoted Cholesky, PCG to 1e-6).  Default: the handles and
@@ -737,8 +743,7 @@ def run_multi(args):
                               np.linalg.norm(q["y"])))
         line["oracle_check"] = {"sample": sample, "relres_oracle": errs,
                                 "max": max(e for e in errs if e is not None)}
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def run_reference(args, p):
@@ -813,6 +818,8 @@ def main():
                     help="--multi: iteration cap per system (a small cap bounds a profiling run)")
     ap.add_argument("--multi-cluster", type=int, default=0, choices=[0, 1, 2, 4, 8],
                     help="--multi: CTAs per system in the persistent launch (0: default)")
+    ap.add_argument("--no-multi", action="store_true",
+                    help="default step: leave out the nested 256-instance measurement")
     ap.add_argument("--multi-streams", action="store_true",
                     help="--multi: solve each instance on its own stream instead of in one "
                          "persistent launch")
@@ -1111,6 +1118,13 @@ def main():
             ref_it, ref_src = it_last, f"this run's {args.prec} PCG iteration count"
         line["cpu_baseline"] = cpu_baseline(p, ref_it, ref_src, built=built)
         line["oracle_check"] = oracle_check(p, built, xs, subs)
+    if rank == 0 and not args.no_multi and args.interp == "cubic" and args.kuu == "dense":
+        # the many-instance workload (256 uneven systems in one persistent
+        # launch), after the timed region: its own line's fields, nested
+        try:
+            line["multi_instance"] = multi_instance_result(args)
+        except Exception as e:   # noqa: BLE001 -- reported, never fatal to the line
+            line["multi_instance"] = {"error": str(e)[:300]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
