@@ -103,3 +103,26 @@ def test_batch_iteration_flop_count():
     assert bench.batch_iter_flops(10, 2, 48 * 48, 96, 32) == 10 * 168 + 2 * 2304 * 96 + 30 * 145
     # d = 3: scatter 20 + 64 + 256 = 340, gather 256 + 96 + 32 = 384
     assert bench.batch_iter_flops(5, 3, 24 ** 3, 72, 0) == 5 * 724 + 2 * 13824 * 72 + 20 * 17
+
+
+def test_multi_instance_workload_recipe():
+    # the 256-system workload: d in {2, 3}, n log-uniform in [200, 5000], points
+    # in the unit box, 48^2 or 24^3 grids over [-0.1, 1.1]^d, rank 32, rtol 1e-6,
+    # values then the d gradient blocks as the target; seeded (same i, same system)
+    import numpy as np
+    from synth import workloads as W
+    seen = set()
+    for i in range(64):
+        p = W.multi_instance(i)
+        n, d = p["X"].shape
+        seen.add(d)
+        assert d in (2, 3) and 200 <= n <= 5000
+        assert tuple(p["m"]) == ((48, 48) if d == 2 else (24, 24, 24))
+        assert tuple(p["lo"]) == (-0.1,) * d and tuple(p["hi"]) == (1.1,) * d
+        assert p["X"].min() >= 0.0 and p["X"].max() <= 1.0
+        assert p["y"].shape == (n * (d + 1),) and np.all(np.isfinite(p["y"]))
+        assert p["rank"] == 32 and p["rtol"] == 1e-6
+        assert 0.05 <= float(np.atleast_1d(p["ell"])[0]) <= 0.3
+    assert seen == {2, 3}
+    q = W.multi_instance(5)
+    assert np.array_equal(q["X"], W.multi_instance(5)["X"])
